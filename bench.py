@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput benchmark: forward + adjoint backward of a 20-qubit, 64-sample batch.
+
+Workload (``C3``): RX angle encoding of 20 inputs, then 10 layers of (RY, RZ on every qubit) +
+CNOT ring; complex64 state (512 MiB per batch, larger than L2), float64 <Z_i> and gradients.
+One step = qsim_forward (angle -> coefficients, fused passes, <Z> reduction) + qsim_backward
+(adjoint passes, gradient reductions) on device-resident inputs. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode fused|per_gate]
+
+For N > 1 launch under torchrun: every rank runs its own replica (the method has no exchange
+step on one circuit batch), rank 0 prints the line, ``value`` sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+adjoint-bwd samples/s"
+UNIT = "samples/s"
+WORKLOAD = "C3: 20 qubits, batch 64, complex64, RX encoding + 10 x (RY,RZ per qubit + CNOT ring), fwd+bwd"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
+    ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--contiguous-bits", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--json-out", default="")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_init(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"qsim_clocks_{os.getpid()}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={','.join(self.FIELDS)}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle (bounded sample)
+def oracle_rate(wl, gate_budget_s=12.0, max_gates=None):
+    """Oracle-S forward of one sample over a prefix of the circuit, timed, extrapolated to the
+    fwd+bwd samples/s of the full workload (backward = parameter shift: 2 forwards per rotation)."""
+    import oracle
+    gates = wl.gates
+    n = wl.n
+    t0 = time.perf_counter()
+    done = 0
+    psi = None
+    chunk = 10
+    while done < len(gates) and (max_gates is None or done < max_gates):
+        nxt = min(len(gates), done + chunk)
+        psi = oracle.simulate_strided(gates[done:nxt], n, wl.params, wl.inputs[:1], init=psi)
+        done = nxt
+        if time.perf_counter() - t0 > gate_budget_s:
+            break
+    dt = time.perf_counter() - t0
+    per_gate = dt / done
+    n_rot = sum(1 for g in gates if g[0] <= 2)
+    per_sample = per_gate * len(gates) * (1 + 2 * n_rot)
+    sample = (f"Oracle-S (numpy FP64, strided) forward of 1 sample through {done} of {len(gates)} gates in "
+              f"{dt:.2f} s; extrapolated to fwd+bwd per sample = {1 + 2 * n_rot} full forwards "
+              f"(1 + parameter shift of {n_rot} rotations)")
+    return 1.0 / per_sample, sample, dt
+
+
+# ------------------------------------------------------------------ our arm
+def algorithmic_bytes(plan_desc, B, n, direction):
+    """Bytes each fused pass must move (complex64): forward 16 B/amp (8 B for the |0> start), backward
+    32 B/amp (24 for the first pass, which forms lambda, 16 for the last, which stores nothing)."""
+    P = len(plan_desc["passes"])
+    amps = B * (1 << n)
+    if direction == "fwd":
+        return [amps * (8 if q == 0 else 16) for q in range(P)]
+    out = []
+    for q in range(P):
+        if P == 1:
+            out.append(amps * 8)
+        elif q == P - 1:
+            out.append(amps * 24)
+        elif q == 0:
+            out.append(amps * 16)
+        else:
+            out.append(amps * 32)
+    return out
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_record(kernel):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    rec = d.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2404_09213_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh", ".h", ".hpp")):
+            h.update(open(os.path.join(src, f), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import workloads as W
+    from paper_2404_09213_gb300 import build as qbuild
+    qbuild.build()
+    import paper_2404_09213_gb300 as q
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.config(3)
+    plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=args.k, contiguous_bits=args.contiguous_bits)
+    desc = plan.describe()
+    p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
+    x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
+    g = torch.tensor(wl.grad_out, dtype=torch.float64, device=dev)
+    B = wl.batch
+    states = torch.empty((B, 1 << wl.n), dtype=torch.complex64, device=dev)
+    z = torch.empty((B, wl.n), dtype=torch.float64, device=dev)
+    dp = torch.empty((wl.n_params,), dtype=torch.float64, device=dev)
+    di = torch.empty((B, wl.n_inputs), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.forward(p, x, states=states, z=z, stream=stream)
+        plan.backward(g, dparams=dp, dinputs=di, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    plan.set_profiling(args.steps)
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    launches0 = q.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = q.kernel_launches() - launches0
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    fwd_ms, bwd_ms, nf, nb = plan.read_profile()
+    plan.set_profiling(0)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * B * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (fused backward pass kernel in fused mode)
+    peak, peak_kind = load_peaks()
+    fb = algorithmic_bytes(desc, B, wl.n, "fwd")
+    bb = algorithmic_bytes(desc, B, wl.n, "bwd")
+    kern = "bwd_pass_kernel" if args.mode == "fused" else "pg_bwd_kernel"
+    if fwd_ms.sum() > bwd_ms.sum():
+        kern = "fwd_pass_kernel" if args.mode == "fused" else "pg_gate_kernel"
+        tot_b, tot_ms, n_l = sum(fb) * nf, float(fwd_ms.sum()), len(fb) * nf
+    else:
+        tot_b, tot_ms, n_l = sum(bb) * nb, float(bwd_ms.sum()), len(bb) * nb
+    achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1e3) / 1e9 if tot_ms > 0 else None
+    traffic = traffic_record(kern)
+    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "algorithmic_bytes_per_launch": tot_b / n_l if n_l else None,
+                "avg_launch_ms": tot_ms / n_l if n_l else None, "launches_timed": n_l,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+                "fwd_ms_per_step": float(fwd_ms.sum()) / max(nf, 1), "bwd_ms_per_step": float(bwd_ms.sum()) / max(nb, 1),
+                "passes": len(desc["passes"])}
+
+    # end to end: host inputs -> device, forward + backward, results -> host, every step
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.tensor(wl.params, dtype=torch.float32).pin_memory()
+        hx = torch.tensor(wl.inputs, dtype=torch.float32).pin_memory()
+        hg = torch.tensor(wl.grad_out, dtype=torch.float64).pin_memory()
+        hz = torch.empty((B, wl.n), dtype=torch.float64).pin_memory()
+        hdp = torch.empty((wl.n_params,), dtype=torch.float64).pin_memory()
+        hdi = torch.empty((B, wl.n_inputs), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            p.copy_(hp, non_blocking=True)
+            x.copy_(hx, non_blocking=True)
+            g.copy_(hg, non_blocking=True)
+            step()
+            hz.copy_(z, non_blocking=True)
+            hdp.copy_(dp, non_blocking=True)
+            hdi.copy_(di, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        barrier(world)
+        sec = max_over_ranks(t1 - t0, world, dev)
+        h2d = hp.numel() * 4 + hx.numel() * 4 + hg.numel() * 8
+        d2h = hz.numel() * 8 + hdp.numel() * 8 + hdi.numel() * 8
+        e2e = {"value": world * B * args.steps / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 state, fp64 reductions)",
+           "data": "synthetic (seeded splitmix64 angles and loss weights)",
+           "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": B, "gates": len(wl.gates),
+                      "params": wl.n_params, "mode": args.mode, "k": desc["k"], "contiguous_bits": desc["c"],
+                      "l2": "inputs larger than L2: 512 MiB state per step (L2 129 MB), no flush needed",
+                      "parallelism": f"replicas x{world}"},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    return out, wl
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import workloads as W
+        wl = W.config(3)
+        for _ in range(args.warmup):
+            oracle_rate(wl, gate_budget_s=0.0, max_gates=1)
+        rates = []
+        samples = None
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            r, samples, _ = oracle_rate(wl, gate_budget_s=1.0, max_gates=60)
+            rates.append(r)
+        dt = time.perf_counter() - t0
+        v = statistics.median(rates)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": wl.batch},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": dt}
+        print(json.dumps(line))
+        return
+    out, wl = run_ours(args, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, sample, _ = oracle_rate(wl, gate_budget_s=12.0)
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        line = json.dumps(out)
+        print(line)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(line + "\n")
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * qsim.h — C ABI of the batched state-vector simulator (GB300, sm_103a).
+ *
+ * What it computes (arXiv 2404.09213, "Qandle"):
+ *   - a batch of B states of n qubits, psi_b in C^(2^n), stored (B, 2^n) row-major with interleaved
+ *     (re, im) — the batched shape (B, 2^W) of Section II-D;
+ *   - qubit q is the q-th MOST significant index bit (MSb-0, Section II-A): bit (n-1-q) of x;
+ *   - a gate list (Section II-B: embedding layers, trainable layers) applied in order, each gate one
+ *     of RX, RY, RZ (R_P(theta) = exp(-i theta P / 2); RX written as in Eq. 1), H, X, CNOT, CZ;
+ *   - the measurement layer <Z_i>_b = sum_x |psi_b[x]|^2 (1 - 2 bit_i(x)) for every qubit i;
+ *   - gradients of L = sum_{b,i} g_{b,i} <Z_i>_b by the adjoint method (Section II-B: backpropagation
+ *     through the simulator); shared parameters sum over the batch, inputs are per sample.
+ *
+ * Gates are never expanded to 2^n x 2^n matrices (the paper's Eq. 2 caching): the planner groups
+ * consecutive gates touching at most k qubits into one pass over the state (the circuit splitting
+ * of Section III-B), and each 2x2 is formed on the device from the angle.
+ *
+ * Conventions for every call below:
+ *   - status: 0 = QSIM_OK, negative = error; the message is in qsim_last_error() (thread-local).
+ *   - "d_" pointers are DEVICE pointers owned by the caller; host pointers are marked "h_".
+ *   - all device work is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and is
+ *     asynchronous; the status only reports validation and enqueue errors. Device-side failures
+ *     (a bounded wait that timed out) are reported by qsim_sync_status().
+ *   - scalar type: QSIM_C64 -> state complex64, params/inputs float32; QSIM_C128 -> complex128,
+ *     params/inputs float64. <Z>, grad_out and all gradients are float64 in both modes.
+ */
+#ifndef QSIM_PUBLIC_API_H_
+#define QSIM_PUBLIC_API_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Gate types (Section III-A names R_x; RY/RZ/H/X/CNOT/CZ follow the textbook definitions). */
+enum { QSIM_RX = 0, QSIM_RY = 1, QSIM_RZ = 2, QSIM_H = 3, QSIM_X = 4, QSIM_CNOT = 5, QSIM_CZ = 6 };
+
+/* One gate: {type, targets, controls, param index}.
+ *   single-qubit gates: targets[0] = qubit, others -1.
+ *   CNOT: controls[0] = control, targets[0] = target.   CZ: controls[0], targets[0] (symmetric).
+ *   param >= 0: index into the trainable parameter vector (shared by the batch);
+ *   param == -1: no parameter (H, X, CNOT, CZ);
+ *   param <= -2: encoded input, column (-2 - param) of the (B, n_inputs) input matrix. */
+typedef struct {
+  int32_t type;
+  int32_t targets[2];
+  int32_t controls[2];
+  int32_t param;
+} qsim_gate;
+
+enum {
+  QSIM_OK = 0,
+  QSIM_ERR_ARG = -1,        /* null pointer, bad size or option                       */
+  QSIM_ERR_QUBIT = -2,      /* qubit index out of range or control == target          */
+  QSIM_ERR_PARAM = -3,      /* parameter field inconsistent with the gate type        */
+  QSIM_ERR_GATE = -4,       /* unknown gate type                                      */
+  QSIM_ERR_NO_FORWARD = -5, /* backward without a preceding forward on this plan      */
+  QSIM_ERR_OOM = -6,        /* workspace allocation failed or exceeds the budget      */
+  QSIM_ERR_CUDA = -7,       /* a CUDA call failed (message has the CUDA error string) */
+  QSIM_ERR_TIMEOUT = -8,    /* a bounded device-side wait gave up                     */
+  QSIM_ERR_UNSUPPORTED = -9 /* size outside what this build supports                  */
+};
+
+enum { QSIM_C64 = 0, QSIM_C128 = 1 };
+enum { QSIM_FUSED = 0, QSIM_PER_GATE = 1 };
+
+typedef struct {
+  int32_t k;                 /* max qubits local to one fused pass (tile = 2^k amplitudes); 0 = default (12) */
+  int32_t dtype;             /* QSIM_C64 or QSIM_C128 */
+  int32_t mode;              /* QSIM_FUSED (default) or QSIM_PER_GATE (one kernel per gate: the plain baseline) */
+  int32_t contiguous_bits;   /* low index bits local in every pass (runs of 2^c amplitudes); 0 = default (4) */
+  int32_t checkpoint_passes; /* >0: backward restarts psi from a stored forward state every this many passes;
+                                0: no checkpoints; -1: choose from mem_budget_bytes */
+  int32_t reserved;
+  int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
+} qsim_plan_opts;
+
+typedef struct {
+  int32_t n_qubits, n_gates, n_params, n_inputs;
+  int32_t n_passes, k, dtype, mode;
+  int32_t n_checkpoints;     /* stored forward states the backward restarts from (0 = none) */
+  int32_t reserved;
+  int64_t workspace_bytes;   /* device bytes held by the plan for the last batch size used */
+} qsim_plan_info;
+
+typedef struct qsim_plan_s* qsim_plan_t;
+
+/* Fill `opts` with the defaults (k = 12, complex64, fused, c = 4, no checkpoints). */
+void qsim_default_opts(qsim_plan_opts* opts);
+
+/* Build a plan (host only; no device memory is touched until the first forward).
+ *   h_gates: n_gates gate records (host memory, copied); n_qubits in [1, 34].
+ *   opts: NULL for defaults. On success *out owns the plan (free with qsim_plan_destroy).
+ *   Errors: QSIM_ERR_ARG / _QUBIT / _PARAM / _GATE with a message naming the first bad gate. */
+int qsim_plan(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits,
+              const qsim_plan_opts* opts, qsim_plan_t* out);
+
+/* Sizes and schedule summary of a plan. */
+int qsim_plan_info_get(qsim_plan_t plan, qsim_plan_info* info);
+
+/* JSON description of the pass schedule (local qubits, tile-bit positions, register phases and
+ * the gate indices of every op), for inspection and tests. Writes at most `cap` bytes including
+ * the terminating NUL into h_buf (which may be NULL when cap == 0) and the full length + 1 into
+ * *needed. */
+int qsim_plan_describe(qsim_plan_t plan, char* h_buf, size_t cap, size_t* needed);
+
+/* Physical amplitude indices (within one sample) of the 2^k elements of tile `tile` of pass
+ * `pass`, in tile order (tile bit j <-> physical bit L_j): the gather/scatter map of that pass.
+ * h_out must hold 2^k int64 values. Host only. */
+int qsim_tile_index_map(qsim_plan_t plan, int32_t pass, int64_t tile, int64_t* h_out);
+
+/* Forward pass.
+ *   d_params:  (n_params,) float32/float64 trainable angles (may be NULL if n_params == 0)
+ *   d_inputs:  (batch, n_inputs) float32/float64 encoded inputs (NULL if n_inputs == 0)
+ *   d_init:    (batch, 2^n) complex initial states, or NULL for |0...0> in every sample
+ *   d_states:  (batch, 2^n) complex output: the final states (may equal d_init)
+ *   d_z:       (batch, n) float64 output <Z_i>_b
+ * The plan remembers d_params, d_inputs and d_states for the backward: they must stay unchanged
+ * until qsim_backward has been enqueued. Workspace is (re)allocated on `stream` when batch grows. */
+int qsim_forward(qsim_plan_t plan, const void* d_params, const void* d_inputs, int32_t batch,
+                 const void* d_init, void* d_states, double* d_z, void* stream);
+
+/* Adjoint backward of the last forward on this plan.
+ *   d_grad_out: (batch, n) float64 dL/d<Z_i>_b
+ *   d_dparams:  (n_params,) float64 output dL/dparams (summed over the batch), may be NULL
+ *   d_dinputs:  (batch, n_inputs) float64 output dL/dinputs, may be NULL
+ * Reads the saved final states (not modified); uses the plan's own workspace for psi and lambda. */
+int qsim_backward(qsim_plan_t plan, const double* d_grad_out, double* d_dparams, double* d_dinputs,
+                  void* stream);
+
+/* Synchronize `plan`'s last stream and return the device-side status (QSIM_OK or QSIM_ERR_TIMEOUT). */
+int qsim_sync_status(qsim_plan_t plan);
+
+/* Standalone measurement layer: <Z_i>_b of arbitrary states (the same reduction the fused path
+ * runs in its last pass). d_states (batch, 2^n) complex of `dtype`; d_z (batch, n) float64.
+ * Allocates its partial-sum scratch on `stream` (stream-ordered) and frees it after use. */
+int qsim_expval_z(const void* d_states, int32_t batch, int32_t n_qubits, int32_t dtype, double* d_z,
+                  void* stream);
+
+/* Per-pass timing: from now on CUDA events are recorded on the launch stream around every pass of
+ * the next `depth` forward and backward calls (a ring of `depth` event sets); depth == 0 turns it
+ * off. Synchronizes the plan's last stream and clears earlier records. */
+int qsim_set_profiling(qsim_plan_t plan, int32_t depth);
+
+/* Per-pass durations in milliseconds, SUMMED over the recorded calls (at most `depth`): h_fwd_ms and
+ * h_bwd_ms hold `cap` floats each, indexed by pass (either may be NULL). h_n_calls[0..1] receives
+ * the number of forward and backward calls summed (may be NULL). Waits for the recorded events. */
+int qsim_read_profile(qsim_plan_t plan, float* h_fwd_ms, float* h_bwd_ms, int32_t cap, int32_t* n_passes,
+                      int32_t* h_n_calls);
+
+/* Number of CUDA kernels this library has launched in the calling process so far. */
+int64_t qsim_kernel_launches(void);
+
+/* Free the plan and its device workspace (synchronizes the plan's last stream). NULL is a no-op. */
+void qsim_plan_destroy(qsim_plan_t plan);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* qsim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_PUBLIC_API_H_ */

@@ -1,0 +1,214 @@
+"""Batched parameterised-circuit simulation on GB300 (arXiv 2404.09213, "Qandle", hot path).
+
+The Python layer only marshals arguments: every step (angle -> 2x2 coefficients, fused passes,
+<Z_i> reduction, adjoint backward and gradient reductions) runs in the CUDA library behind the C ABI
+of ``include/qsim.h``.
+
+* :class:`Plan`           — a planned circuit; ``forward`` / ``backward`` on CUDA tensors.
+* :class:`QSimFunction`   — ``torch.autograd.Function`` over a plan (Section IV-A: circuits as
+                            modules whose weights are ordinary parameters).
+* :class:`QSimLayer`      — ``torch.nn.Module`` holding the trainable angles.
+* :func:`expval_z`        — the standalone measurement layer.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import QsimError, QSIM_C64, QSIM_C128, QSIM_FUSED, QSIM_PER_GATE  # noqa: F401
+
+__all__ = ["Plan", "QSimFunction", "QSimLayer", "expval_z", "QsimError", "gate_structs"]
+
+_DT = {"c64": (QSIM_C64, torch.complex64, torch.float32), "c128": (QSIM_C128, torch.complex128, torch.float64)}
+
+
+def gate_structs(gates):
+    """Gate tuples ``(type, targets, controls, param)`` -> ctypes array of ``qsim_gate``."""
+    arr = (_lib.QsimGate * max(1, len(gates)))()
+    for i, (k, t, c, p) in enumerate(gates):
+        arr[i].type = k
+        arr[i].targets[0], arr[i].targets[1] = t
+        arr[i].controls[0], arr[i].controls[1] = c
+        arr[i].param = p
+    return arr
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(None)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Plan:
+    """A planned circuit (``qsim_plan``): gate list + qubit count + options.
+
+    ``dtype`` "c64" (complex64 state, float32 angles) or "c128"; ``mode`` "fused" or "per_gate";
+    ``k`` qubits per fused pass (default 12 for c64, 11 for c128); ``checkpoint_passes`` > 0 stores
+    the forward state every that many passes for the backward to restart from.
+    """
+
+    def __init__(self, gates, n_qubits, *, dtype="c64", mode="fused", k=0, contiguous_bits=0,
+                 checkpoint_passes=0, mem_budget_bytes=0):
+        L = _lib.lib()
+        self.gates = list(gates)
+        self.n = int(n_qubits)
+        self.dtype = dtype
+        self._code, self.cdtype, self.rdtype = _DT[dtype]
+        opts = _lib.QsimPlanOpts()
+        L.qsim_default_opts(ctypes.byref(opts))
+        opts.k = k
+        opts.dtype = self._code
+        opts.mode = {"fused": QSIM_FUSED, "per_gate": QSIM_PER_GATE}[mode]
+        opts.contiguous_bits = contiguous_bits
+        opts.checkpoint_passes = checkpoint_passes
+        opts.mem_budget_bytes = mem_budget_bytes
+        h = ctypes.c_void_p()
+        arr = gate_structs(self.gates)
+        _lib.check(L.qsim_plan(arr, len(self.gates), self.n, ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        inf = self.info()
+        self.n_params, self.n_inputs = inf["n_params"], inf["n_inputs"]
+        self._saved = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.lib().qsim_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def info(self):
+        inf = _lib.QsimPlanInfo()
+        _lib.check(_lib.lib().qsim_plan_info_get(self._h, ctypes.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in inf._fields_ if f != "reserved"}
+
+    def describe(self):
+        need = ctypes.c_size_t()
+        L = _lib.lib()
+        _lib.check(L.qsim_plan_describe(self._h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _lib.check(L.qsim_plan_describe(self._h, buf, need.value, ctypes.byref(need)))
+        return json.loads(buf.value.decode())
+
+    def tile_index_map(self, pass_index, tile):
+        k = self.describe()["k"]
+        out = np.zeros(1 << k, dtype=np.int64)
+        _lib.check(_lib.lib().qsim_tile_index_map(self._h, pass_index, tile,
+                                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return out
+
+    def forward(self, params, inputs, init=None, states=None, z=None, stream=None):
+        """Run the circuit on a batch. ``params`` (P,), ``inputs`` (B, n_inputs) real CUDA tensors of the
+        plan's real dtype; ``init`` optional (B, 2^n) complex initial states. Returns (states, z)."""
+        B = int(inputs.shape[0]) if inputs is not None and inputs.dim() == 2 else (
+            int(init.shape[0]) if init is not None else 1)
+        dev = (params if params is not None and params.numel() else inputs).device if (
+            params is not None or inputs is not None) else torch.device("cuda")
+        params = self._prep(params, (self.n_params,))
+        inputs = self._prep(inputs, (B, self.n_inputs))
+        if init is not None:
+            init = init.contiguous()
+            assert init.dtype == self.cdtype and init.shape == (B, 1 << self.n)
+        if states is None:
+            states = torch.empty((B, 1 << self.n), dtype=self.cdtype, device=dev)
+        if z is None:
+            z = torch.empty((B, self.n), dtype=torch.float64, device=dev)
+        _lib.check(_lib.lib().qsim_forward(self._h, _ptr(params), _ptr(inputs), B, _ptr(init), _ptr(states),
+                                           _ptr(z), _stream(stream)))
+        self._saved = (params, inputs, states, B)   # the plan reads these again in backward
+        return states, z
+
+    def backward(self, grad_z, dparams=None, dinputs=None, stream=None):
+        """Adjoint backward of the last forward: returns (dL/dparams (P,), dL/dinputs (B, n_inputs)) float64."""
+        if self._saved is None:
+            raise QsimError(-5, "backward called without a preceding forward")
+        _, _, states, B = self._saved
+        grad_z = grad_z.to(torch.float64).contiguous()
+        assert grad_z.shape == (B, self.n)
+        if dparams is None:
+            dparams = torch.empty((self.n_params,), dtype=torch.float64, device=states.device)
+        if dinputs is None:
+            dinputs = torch.empty((B, self.n_inputs), dtype=torch.float64, device=states.device)
+        _lib.check(_lib.lib().qsim_backward(self._h, _ptr(grad_z), _ptr(dparams) if self.n_params else None,
+                                            _ptr(dinputs) if self.n_inputs else None, _stream(stream)))
+        return dparams, dinputs
+
+    def set_profiling(self, depth=1):
+        """Record per-pass CUDA events for the next ``depth`` forward/backward calls (0 = off)."""
+        _lib.check(_lib.lib().qsim_set_profiling(self._h, int(depth)))
+
+    def read_profile(self):
+        """Per-pass event times (ms) summed over the recorded calls: (fwd[P], bwd[P], n_fwd, n_bwd)."""
+        P = self.info()["n_passes"]
+        f = (ctypes.c_float * max(P, 1))()
+        b = (ctypes.c_float * max(P, 1))()
+        n = ctypes.c_int32()
+        nc = (ctypes.c_int32 * 2)()
+        _lib.check(_lib.lib().qsim_read_profile(self._h, f, b, P, ctypes.byref(n), nc))
+        return np.array(f[:P]), np.array(b[:P]), int(nc[0]), int(nc[1])
+
+    def sync_status(self):
+        return _lib.lib().qsim_sync_status(self._h)
+
+    def _prep(self, t, shape):
+        if t is None or (shape[-1] == 0):
+            return None
+        if t.dtype != self.rdtype:
+            t = t.to(self.rdtype)
+        t = t.contiguous()
+        assert tuple(t.shape) == tuple(shape), (t.shape, shape)
+        return t
+
+
+def kernel_launches():
+    """Kernels launched by the library in this process so far."""
+    return int(_lib.lib().qsim_kernel_launches())
+
+
+def expval_z(states, n_qubits, stream=None):
+    """<Z_i> of a batch of states (B, 2^n) complex64/complex128 -> (B, n) float64."""
+    code = QSIM_C128 if states.dtype == torch.complex128 else QSIM_C64
+    states = states.contiguous()
+    B = states.shape[0]
+    z = torch.empty((B, n_qubits), dtype=torch.float64, device=states.device)
+    _lib.check(_lib.lib().qsim_expval_z(_ptr(states), B, n_qubits, code, _ptr(z), _stream(stream)))
+    return z
+
+
+class QSimFunction(torch.autograd.Function):
+    """z = circuit(params, inputs) with the adjoint-method backward of the C library."""
+
+    @staticmethod
+    def forward(ctx, plan, params, inputs):
+        _, z = plan.forward(params.detach(), inputs.detach())
+        ctx.plan = plan
+        ctx.dtypes = (params.dtype, inputs.dtype)
+        return z
+
+    @staticmethod
+    def backward(ctx, grad_z):
+        dp, di = ctx.plan.backward(grad_z)
+        return None, dp.to(ctx.dtypes[0]), di.to(ctx.dtypes[1])
+
+
+class QSimLayer(torch.nn.Module):
+    """A circuit as a module: its rotation angles are an ``nn.Parameter`` (Section IV-A)."""
+
+    def __init__(self, gates, n_qubits, init_params=None, **plan_kw):
+        super().__init__()
+        self.plan = Plan(gates, n_qubits, **plan_kw)
+        p = torch.zeros(self.plan.n_params, dtype=self.plan.rdtype) if init_params is None else \
+            torch.as_tensor(init_params, dtype=self.plan.rdtype)
+        self.weight = torch.nn.Parameter(p)
+
+    def forward(self, inputs):
+        return QSimFunction.apply(self.plan, self.weight, inputs)

@@ -1,0 +1,635 @@
+// C ABI: plan objects, workspace management and the launch sequences of forward / backward.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+#include "launch.hpp"
+#include "planner.hpp"
+
+using namespace qsim;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return QSIM_ERR_CUDA;
+}
+
+template <typename T>
+cudaError_t upload(T** dptr, const std::vector<T>& v) {
+  *dptr = nullptr;
+  if (v.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dptr), v.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+}  // namespace
+
+struct qsim_plan_s {
+  Schedule s;
+  qsim_plan_opts opts{};
+  int el = 8, sc = 4;
+  // device copy of the schedule
+  bool uploaded = false;
+  DevPass* d_passes = nullptr;
+  DevPhase* d_phases = nullptr;
+  DevOp* d_ops = nullptr;
+  DevLayout* d_layouts = nullptr;
+  int32_t* d_gate_type = nullptr;
+  int32_t* d_gate_param = nullptr;
+  int32_t* d_exec_gates = nullptr;
+  int32_t* d_exec_begin = nullptr;
+  int32_t* d_occ_gate = nullptr;
+  int64_t* d_occ_slot = nullptr;
+  int32_t *d_p_ptr = nullptr, *d_p_occ = nullptr, *d_i_ptr = nullptr, *d_i_occ = nullptr;
+  uint8_t* d_Lnl_last = nullptr;
+  int n_occ = 0;
+  // batch workspace
+  int B_cap = -1;
+  int n_segments = 1;
+  std::vector<int> seg_begin;   // pass index where each checkpoint segment starts (+ end sentinel)
+  void* coef = nullptr;
+  uint8_t* form = nullptr;
+  void* scale_f = nullptr;
+  void* scale_b = nullptr;
+  double* gm = nullptr;
+  double* zpart = nullptr;
+  double* gpart = nullptr;
+  double* G = nullptr;
+  void* W = nullptr;
+  void* Lam = nullptr;
+  std::vector<void*> ckpt;
+  int64_t ws_bytes = 0;
+  // saved forward context
+  bool has_fwd = false;
+  const void* params = nullptr;
+  const void* inputs = nullptr;
+  void* states = nullptr;
+  int B = 0;
+  cudaStream_t last_stream = nullptr;
+  // optional per-pass event timing
+  int prof_depth = 0;            // 0 = off; else event sets kept for this many calls
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_f0, ev_f1, ev_b0, ev_b1;   // [depth][P]
+  int64_t n_fwd_calls = 0, n_bwd_calls = 0;
+  int fslot(int q) const { return (int)((n_fwd_calls % prof_depth) * P() + q); }
+  int bslot(int q) const { return (int)((n_bwd_calls % prof_depth) * P() + q); }
+
+  int ensure_events() {
+    const size_t n = (size_t)P() * prof_depth;
+    auto mk = [&](std::vector<cudaEvent_t>& v) -> cudaError_t {
+      while (v.size() < n) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        v.push_back(e);
+      }
+      return cudaSuccess;
+    };
+    cudaError_t e = mk(ev_f0);
+    if (e == cudaSuccess) e = mk(ev_f1);
+    if (e == cudaSuccess) e = mk(ev_b0);
+    if (e == cudaSuccess) e = mk(ev_b1);
+    if (e != cudaSuccess) return cuda_fail(e, "creating profiling events");
+    return QSIM_OK;
+  }
+  void destroy_events() {
+    for (auto* v : {&ev_f0, &ev_f1, &ev_b0, &ev_b1}) {
+      for (auto e : *v) cudaEventDestroy(e);
+      v->clear();
+    }
+  }
+
+  int P() const { return (int)s.passes.size(); }
+  int64_t tps() const {
+    return s.mode == QSIM_PER_GATE ? pg_blocks_per_sample(s.n) : s.passes.empty() ? 1 : s.passes[0].dev.tiles_per_sample;
+  }
+  int64_t state_bytes(int B_) const { return (int64_t)B_ * ((int64_t)1 << s.n) * el; }
+
+  void free_ws() {
+    void* ptrs[] = {coef, form, scale_f, scale_b, gm, zpart, gpart, G, W, Lam};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    for (void* p : ckpt)
+      if (p) cudaFree(p);
+    coef = form = nullptr;
+    scale_f = scale_b = nullptr;
+    gm = zpart = gpart = G = nullptr;
+    W = Lam = nullptr;
+    ckpt.clear();
+    ws_bytes = 0;
+    B_cap = -1;
+  }
+  void free_all() {
+    free_ws();
+    destroy_events();
+    void* ptrs[] = {d_passes, d_phases, d_ops, d_layouts, d_gate_type, d_gate_param, d_exec_gates, d_exec_begin,
+                    d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Lnl_last};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    uploaded = false;
+  }
+
+  int upload_schedule() {
+    if (uploaded) return QSIM_OK;
+    cudaError_t e = cudaSuccess;
+    std::vector<DevPass> passes;
+    std::vector<int32_t> gtype, gparam, exec, exec_begin;
+    for (auto& g : s.gates) {
+      gtype.push_back(g.type);
+      gparam.push_back(g.param);
+    }
+    for (auto& pp : s.passes) {
+      passes.push_back(pp.dev);
+      exec_begin.push_back((int32_t)exec.size());
+      if (s.mode == QSIM_PER_GATE) {
+        exec.push_back(pp.gates[0]);
+      } else {
+        for (int i = 0; i < pp.dev.n_ops; i++) exec.push_back(s.ops[pp.dev.op0 + i].gate);
+      }
+    }
+    exec_begin.push_back((int32_t)exec.size());
+    n_occ = (int)s.grad_gate.size();
+    std::vector<int32_t> occ_gate(s.grad_gate.begin(), s.grad_gate.end());
+    std::vector<int64_t> occ_slot(n_occ);
+    for (int j = 0; j < n_occ; j++) occ_slot[j] = s.passes[s.grad_pass[j]].dev.gpart_offset + s.grad_slot[j];
+    std::vector<int32_t> p_ptr(s.n_params + 1, 0), i_ptr(s.n_inputs + 1, 0), p_occ, i_occ;
+    for (int p = 0; p < s.n_params; p++) {
+      for (int j = 0; j < n_occ; j++)
+        if (s.gates[occ_gate[j]].param == p) p_occ.push_back(j);
+      p_ptr[p + 1] = (int32_t)p_occ.size();
+    }
+    for (int c = 0; c < s.n_inputs; c++) {
+      for (int j = 0; j < n_occ; j++)
+        if (s.gates[occ_gate[j]].param == -2 - c) i_occ.push_back(j);
+      i_ptr[c + 1] = (int32_t)i_occ.size();
+    }
+    std::vector<uint8_t> lnl;
+    if (s.mode == QSIM_FUSED && !s.passes.empty()) {
+      const DevPass& d = s.passes.back().dev;
+      for (int j = 0; j < d.k; j++) lnl.push_back(d.L[j]);
+      for (int j = 0; j < d.n_nonlocal; j++) lnl.push_back(d.nonlocal[j]);
+      lnl.push_back(0);
+    }
+#define QSIM_UP(PTR, VEC) \
+  if (e == cudaSuccess) e = upload(&PTR, VEC);
+    QSIM_UP(d_passes, passes)
+    QSIM_UP(d_phases, s.phases)
+    QSIM_UP(d_ops, s.ops)
+    QSIM_UP(d_layouts, s.layouts)
+    QSIM_UP(d_gate_type, gtype)
+    QSIM_UP(d_gate_param, gparam)
+    QSIM_UP(d_exec_gates, exec)
+    QSIM_UP(d_exec_begin, exec_begin)
+    QSIM_UP(d_occ_gate, occ_gate)
+    QSIM_UP(d_occ_slot, occ_slot)
+    QSIM_UP(d_p_ptr, p_ptr)
+    QSIM_UP(d_p_occ, p_occ)
+    QSIM_UP(d_i_ptr, i_ptr)
+    QSIM_UP(d_i_occ, i_occ)
+    QSIM_UP(d_Lnl_last, lnl)
+#undef QSIM_UP
+    if (e != cudaSuccess) return cuda_fail(e, "uploading the plan");
+    if (s.mode == QSIM_FUSED) {
+      size_t mf = 0, mb = 0;
+      for (auto& pp : s.passes) {
+        const int Rf = fwd_R_for(pp.dev.k, s.dtype), Rb = bwd_R_for(pp.dev.k, s.dtype);
+        mf = std::max(mf, fwd_pass_smem(pp.dev, s.dtype, 1 << (pp.dev.k - Rf)));
+        mb = std::max(mb, bwd_pass_smem(pp.dev, s.dtype, 1 << (pp.dev.k - Rb)));
+      }
+      int dev = 0, optin = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if ((int64_t)mf > optin || (int64_t)mb > optin)
+        return fail(QSIM_ERR_UNSUPPORTED, "tile does not fit in shared memory: lower k");
+      e = prepare_pass_kernels(s.dtype, mf, mb);
+      if (e != cudaSuccess) return cuda_fail(e, "setting kernel attributes");
+    }
+    uploaded = true;
+    return QSIM_OK;
+  }
+
+  int ensure_ws(int B_) {
+    if (B_ == B_cap) return QSIM_OK;
+    free_ws();
+    const int64_t G_ = (int64_t)s.gates.size(), P_ = P();
+    const int64_t sb = state_bytes(B_);
+    int64_t zcount = s.mode == QSIM_PER_GATE ? z_partials_count(s.n, B_)
+                                             : (int64_t)B_ * tps() * (s.k + 1);
+    struct Item {
+      void** p;
+      int64_t bytes;
+    } items[] = {
+        {&coef, G_ * B_ * sc}, {reinterpret_cast<void**>(&form), G_ * B_},
+        {&scale_f, P_ * B_ * sc}, {&scale_b, P_ * B_ * sc},
+        {reinterpret_cast<void**>(&gm), G_ * B_ * 8}, {reinterpret_cast<void**>(&zpart), zcount * 8},
+        {reinterpret_cast<void**>(&gpart), s.total_gslots * B_ * tps() * 8},
+        {reinterpret_cast<void**>(&G), (int64_t)n_occ * B_ * 8},
+        {&W, sb}, {&Lam, sb},
+    };
+    for (auto& it : items) {
+      if (it.bytes <= 0) continue;
+      cudaError_t e = cudaMalloc(it.p, (size_t)it.bytes);
+      if (e != cudaSuccess) {
+        free_ws();
+        return fail(QSIM_ERR_OOM, std::string("workspace allocation failed: ") + cudaGetErrorString(e));
+      }
+      ws_bytes += it.bytes;
+    }
+    // checkpoint segments (fused path only)
+    n_segments = 1;
+    if (s.mode == QSIM_FUSED && P_ > 1) {
+      int m = 0;
+      if (opts.checkpoint_passes > 0) {
+        m = opts.checkpoint_passes;
+      } else if (opts.checkpoint_passes < 0 && opts.mem_budget_bytes > 0 && sb > 0) {
+        const int64_t avail = opts.mem_budget_bytes - ws_bytes;
+        const int64_t nck = std::max<int64_t>(0, std::min<int64_t>(avail / sb, P_ - 1));
+        if (nck > 0) m = (int)((P_ + nck) / (nck + 1));
+      }
+      if (m > 0 && m < P_) n_segments = (int)((P_ + m - 1) / m);
+      seg_begin.clear();
+      for (int j = 0; j < n_segments; j++) seg_begin.push_back(j * (m > 0 ? m : (int)P_));
+      seg_begin.push_back((int)P_);
+      for (int j = 0; j + 1 < n_segments; j++) {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, (size_t)sb);
+        if (e != cudaSuccess) {
+          free_ws();
+          return fail(QSIM_ERR_OOM, std::string("checkpoint allocation failed: ") + cudaGetErrorString(e));
+        }
+        ckpt.push_back(p);
+        ws_bytes += sb;
+      }
+    } else {
+      seg_begin = {0, (int)P_};
+    }
+    B_cap = B_;
+    return QSIM_OK;
+  }
+
+  int seg_of(int p) const {
+    for (int j = 0; j < n_segments; j++)
+      if (p < seg_begin[j + 1]) return j;
+    return n_segments - 1;
+  }
+
+  PassLaunch pass_launch(int p, const void* scale) const {
+    PassLaunch L{};
+    L.h_pass = &s.passes[p].dev;
+    L.d_pass = d_passes + p;
+    L.d_phases = d_phases;
+    L.d_ops = d_ops;
+    L.d_layouts = d_layouts;
+    L.n = s.n;
+    L.B = B;
+    L.coef = coef;
+    L.form = form;
+    L.scale = scale;
+    return L;
+  }
+
+  PerGateArgs pg_args(int g, const void* scale) const {
+    PerGateArgs a{};
+    const Gate& x = s.gates[g];
+    a.n = s.n;
+    a.B = B;
+    a.dtype = s.dtype;
+    a.type = x.type;
+    a.pos_t = s.n - 1 - x.t0;
+    a.pos_c = x.c0 >= 0 ? s.n - 1 - x.c0 : 0;
+    a.gate = g;
+    a.coef = coef;
+    a.form = form;
+    a.scale = scale;
+    return a;
+  }
+};
+
+extern "C" {
+
+void qsim_default_opts(qsim_plan_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->k = 12;
+  o->dtype = QSIM_C64;
+  o->mode = QSIM_FUSED;
+  o->contiguous_bits = 4;
+  o->checkpoint_passes = 0;
+  o->mem_budget_bytes = 0;
+}
+
+const char* qsim_last_error(void) { return g_err.c_str(); }
+
+int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const qsim_plan_opts* opts,
+              qsim_plan_t* out) {
+  g_err.clear();
+  if (!out) return fail(QSIM_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  qsim_plan_opts o;
+  qsim_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "dtype must be QSIM_C64 or QSIM_C128");
+  if (o.mode != QSIM_FUSED && o.mode != QSIM_PER_GATE) return fail(QSIM_ERR_ARG, "mode must be QSIM_FUSED or QSIM_PER_GATE");
+  if (o.k < 0 || o.contiguous_bits < 0 || o.checkpoint_passes < -1 || o.mem_budget_bytes < 0)
+    return fail(QSIM_ERR_ARG, "negative option value");
+  std::vector<Gate> gv;
+  int np = 0, ni = 0;
+  std::string err;
+  int rc = validate_gates(gates, n_gates, n_qubits, gv, np, ni, err);
+  if (rc) return fail(rc, err);
+  auto* p = new qsim_plan_s();
+  p->opts = o;
+  p->el = o.dtype == QSIM_C128 ? 16 : 8;
+  p->sc = o.dtype == QSIM_C128 ? 8 : 4;
+  if (o.mode == QSIM_FUSED) {
+    if (o.k == 0) o.k = max_k_for(o.dtype);
+    if (o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
+  }
+  p->opts = o;
+  rc = build_schedule(gv, n_qubits, o, fwd_R_for(o.k > 0 ? o.k : 12, o.dtype), p->s, err);
+  if (rc) {
+    delete p;
+    return fail(rc, err);
+  }
+  p->s.n_params = np;
+  p->s.n_inputs = ni;
+  *out = p;
+  return QSIM_OK;
+}
+
+int qsim_plan_info_get(qsim_plan_t p, qsim_plan_info* info) {
+  if (!p || !info) return fail(QSIM_ERR_ARG, "NULL argument");
+  std::memset(info, 0, sizeof *info);
+  info->n_qubits = p->s.n;
+  info->n_gates = (int32_t)p->s.gates.size();
+  info->n_params = p->s.n_params;
+  info->n_inputs = p->s.n_inputs;
+  info->n_passes = p->P();
+  info->k = p->s.k;
+  info->dtype = p->s.dtype;
+  info->mode = p->s.mode;
+  info->n_checkpoints = (int32_t)p->ckpt.size();
+  info->workspace_bytes = p->ws_bytes;
+  return QSIM_OK;
+}
+
+int qsim_plan_describe(qsim_plan_t p, char* buf, size_t cap, size_t* needed) {
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  std::string d = describe_schedule(p->s);
+  if (needed) *needed = d.size() + 1;
+  if (buf && cap > 0) {
+    size_t m = std::min(cap - 1, d.size());
+    std::memcpy(buf, d.data(), m);
+    buf[m] = 0;
+  }
+  return QSIM_OK;
+}
+
+int qsim_tile_index_map(qsim_plan_t p, int32_t pass, int64_t tile, int64_t* out) {
+  if (!p || !out) return fail(QSIM_ERR_ARG, "NULL argument");
+  if (p->s.mode != QSIM_FUSED) return fail(QSIM_ERR_ARG, "index maps exist only for fused plans");
+  if (pass < 0 || pass >= p->P()) return fail(QSIM_ERR_ARG, "pass out of range");
+  const DevPass& d = p->s.passes[pass].dev;
+  if (tile < 0 || tile >= d.tiles_per_sample) return fail(QSIM_ERR_ARG, "tile out of range");
+  for (int64_t e = 0; e < ((int64_t)1 << d.k); e++) out[e] = tile_element_index(d, tile, e);
+  return QSIM_OK;
+}
+
+int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int32_t batch, const void* d_init,
+                 void* d_states, double* d_z, void* stream) {
+  g_err.clear();
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  if (batch < 0) return fail(QSIM_ERR_ARG, "batch < 0");
+  if (batch > 0 && (!d_states || !d_z)) return fail(QSIM_ERR_ARG, "d_states and d_z are required");
+  if (p->s.n_params > 0 && !d_params) return fail(QSIM_ERR_ARG, "d_params is NULL but the circuit has parameters");
+  if (p->s.n_inputs > 0 && batch > 0 && !d_inputs) return fail(QSIM_ERR_ARG, "d_inputs is NULL but the circuit has inputs");
+  if (((uintptr_t)d_states & 15) || ((uintptr_t)d_init & 15)) return fail(QSIM_ERR_ARG, "state buffers must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = p->upload_schedule();
+  if (rc) return rc;
+  p->has_fwd = false;
+  if (batch == 0) return QSIM_OK;
+  rc = p->ensure_ws(batch);
+  if (rc) return rc;
+  p->B = batch;
+  p->params = d_params;
+  p->inputs = d_inputs;
+  p->states = d_states;
+  p->last_stream = st;
+  const Schedule& s = p->s;
+  cudaError_t e;
+  CoefArgs ca{};
+  ca.gate_type = p->d_gate_type;
+  ca.gate_param = p->d_gate_param;
+  ca.exec_gates = p->d_exec_gates;
+  ca.exec_begin = p->d_exec_begin;
+  ca.params = d_params;
+  ca.inputs = d_inputs;
+  ca.n_inputs = s.n_inputs;
+  ca.B = batch;
+  ca.P = p->P();
+  ca.coef = p->coef;
+  ca.form = p->form;
+  ca.scale_f = p->scale_f;
+  ca.scale_b = p->scale_b;
+  ca.gm = p->gm;
+  if (s.gates.size() > 0 && ca.P > 0) {
+    e = launch_coef(ca, s.dtype, st);
+    if (e != cudaSuccess) return cuda_fail(e, "coefficient kernel");
+  }
+  const char* sf = reinterpret_cast<const char*>(p->scale_f);
+  if (s.mode == QSIM_PER_GATE) {
+    e = launch_pg_init(d_states, d_init, s.n, batch, s.dtype, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init kernel");
+    for (int g = 0; g < (int)s.gates.size(); g++) {
+      if (p->profiling) cudaEventRecord(p->ev_f0[p->fslot(g)], st);
+      e = launch_pg_gate(p->pg_args(g, sf + (size_t)g * batch * p->sc), d_states, false, st);
+      if (e != cudaSuccess) return cuda_fail(e, "per-gate kernel");
+      if (p->profiling) cudaEventRecord(p->ev_f1[p->fslot(g)], st);
+    }
+    e = launch_expval_z(d_states, s.n, batch, s.dtype, p->zpart, d_z, st);
+    if (e != cudaSuccess) return cuda_fail(e, "<Z> kernel");
+  } else {
+    const int P_ = p->P();
+    for (int q = 0; q < P_; q++) {
+      const int seg = p->seg_of(q);
+      void* out = (seg == p->n_segments - 1) ? d_states : p->ckpt[seg];
+      const void* in;
+      if (q == p->seg_begin[seg]) in = (seg == 0) ? d_init : p->ckpt[seg - 1];
+      else in = out;
+      double* zp = (q == P_ - 1) ? p->zpart : nullptr;
+      if (p->profiling) cudaEventRecord(p->ev_f0[p->fslot(q)], st);
+      e = launch_fwd_pass(p->pass_launch(q, sf + (size_t)q * batch * p->sc), s.dtype, in, out, zp, st);
+      if (e != cudaSuccess) return cuda_fail(e, "fused forward pass");
+      if (p->profiling) cudaEventRecord(p->ev_f1[p->fslot(q)], st);
+    }
+    const DevPass& last = s.passes.back().dev;
+    e = launch_z_final(p->zpart, last.k, p->d_Lnl_last, last.n_nonlocal, last.tiles_per_sample, s.n, batch, d_z, st);
+    if (e != cudaSuccess) return cuda_fail(e, "<Z> reduction");
+  }
+  p->has_fwd = true;
+  if (p->profiling) p->n_fwd_calls++;
+  return QSIM_OK;
+}
+
+int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, double* d_dinputs, void* stream) {
+  g_err.clear();
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  if (!p->has_fwd) return fail(QSIM_ERR_NO_FORWARD, "backward called without a preceding forward on this plan");
+  const int B = p->B;
+  if (!d_grad_out) return fail(QSIM_ERR_ARG, "d_grad_out is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  p->last_stream = st;
+  const Schedule& s = p->s;
+  cudaError_t e;
+  const char* sbk = reinterpret_cast<const char*>(p->scale_b);
+  if (s.mode == QSIM_PER_GATE) {
+    e = launch_pg_lambda_init(p->states, p->W, p->Lam, d_grad_out, s.n, B, s.dtype, st);
+    if (e != cudaSuccess) return cuda_fail(e, "lambda init");
+    const int bps = pg_blocks_per_sample(s.n);
+    for (int g = (int)s.gates.size() - 1; g >= 0; g--) {
+      double* gp = p->gpart + s.passes[g].dev.gpart_offset * (int64_t)B * bps;
+      if (p->profiling) cudaEventRecord(p->ev_b0[p->bslot(g)], st);
+      e = launch_pg_bwd_gate(p->pg_args(g, sbk + (size_t)g * B * p->sc), p->W, p->Lam, gp, bps, st);
+      if (e != cudaSuccess) return cuda_fail(e, "per-gate backward kernel");
+      if (p->profiling) cudaEventRecord(p->ev_b1[p->bslot(g)], st);
+    }
+  } else {
+    const int P_ = p->P();
+    for (int q = P_ - 1; q >= 0; q--) {
+      const int seg = p->seg_of(q);
+      const bool seg_last = (q == p->seg_begin[seg + 1] - 1);
+      const void* pin = seg_last ? ((seg == p->n_segments - 1) ? p->states : p->ckpt[seg]) : p->W;
+      const void* lin = (q == P_ - 1) ? nullptr : p->Lam;
+      void* pout = q == 0 ? nullptr : p->W;
+      void* lout = q == 0 ? nullptr : p->Lam;
+      if (p->profiling) cudaEventRecord(p->ev_b0[p->bslot(q)], st);
+      e = launch_bwd_pass(p->pass_launch(q, sbk + (size_t)q * B * p->sc), s.dtype, pin, pout, lin, lout, d_grad_out,
+                          p->gpart, st);
+      if (e != cudaSuccess) return cuda_fail(e, "fused backward pass");
+      if (p->profiling) cudaEventRecord(p->ev_b1[p->bslot(q)], st);
+    }
+  }
+  GradReduceArgs ga{};
+  ga.gpart = p->gpart;
+  ga.tiles_per_sample = p->tps();
+  ga.n_occ = p->n_occ;
+  ga.occ_gate = p->d_occ_gate;
+  ga.occ_slot = p->d_occ_slot;
+  ga.gm = p->gm;
+  ga.G = p->G;
+  ga.B = B;
+  ga.n_params = s.n_params;
+  ga.n_inputs = s.n_inputs;
+  ga.p_ptr = p->d_p_ptr;
+  ga.p_occ = p->d_p_occ;
+  ga.i_ptr = p->d_i_ptr;
+  ga.i_occ = p->d_i_occ;
+  ga.dparams = d_dparams;
+  ga.dinputs = d_dinputs;
+  e = launch_grad_reduce(ga, st);
+  if (e != cudaSuccess) return cuda_fail(e, "gradient reduction");
+  if (p->profiling) p->n_bwd_calls++;
+  return QSIM_OK;
+}
+
+int qsim_set_profiling(qsim_plan_t p, int32_t depth) {
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  if (depth < 0) return fail(QSIM_ERR_ARG, "depth < 0");
+  if (p->last_stream || p->n_fwd_calls || p->n_bwd_calls) cudaStreamSynchronize(p->last_stream);
+  p->destroy_events();
+  p->n_fwd_calls = p->n_bwd_calls = 0;
+  p->prof_depth = depth;
+  p->profiling = depth > 0;
+  if (depth > 0) {
+    int rc = p->ensure_events();
+    if (rc) {
+      p->profiling = false;
+      p->prof_depth = 0;
+      return rc;
+    }
+  }
+  return QSIM_OK;
+}
+
+int qsim_read_profile(qsim_plan_t p, float* fwd, float* bwd, int32_t cap, int32_t* n_passes, int32_t* n_calls) {
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  const int P_ = p->P();
+  if (n_passes) *n_passes = P_;
+  const int64_t nf = p->prof_depth ? std::min<int64_t>(p->n_fwd_calls, p->prof_depth) : 0;
+  const int64_t nb = p->prof_depth ? std::min<int64_t>(p->n_bwd_calls, p->prof_depth) : 0;
+  if (n_calls) {
+    n_calls[0] = (int32_t)nf;
+    n_calls[1] = (int32_t)nb;
+  }
+  for (int q = 0; q < P_ && q < cap; q++) {
+    if (fwd) fwd[q] = 0.f;
+    if (bwd) bwd[q] = 0.f;
+    for (int64_t c = 0; c < nf && fwd; c++) {
+      float ms = 0.f;
+      const int i = (int)(c * P_ + q);
+      cudaError_t e = cudaEventSynchronize(p->ev_f1[i]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev_f0[i], p->ev_f1[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "reading forward events");
+      fwd[q] += ms;
+    }
+    for (int64_t c = 0; c < nb && bwd; c++) {
+      float ms = 0.f;
+      const int i = (int)(c * P_ + q);
+      cudaError_t e = cudaEventSynchronize(p->ev_b1[i]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev_b0[i], p->ev_b1[i]);
+      if (e != cudaSuccess) return cuda_fail(e, "reading backward events");
+      bwd[q] += ms;
+    }
+  }
+  return QSIM_OK;
+}
+
+int64_t qsim_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
+
+int qsim_sync_status(qsim_plan_t p) {
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(p->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+  return QSIM_OK;
+}
+
+int qsim_expval_z(const void* d_states, int32_t batch, int32_t n, int32_t dtype, double* d_z, void* stream) {
+  g_err.clear();
+  if (n < 1 || n > kMaxQubits) return fail(QSIM_ERR_UNSUPPORTED, "n_qubits outside [1, 34]");
+  if (batch < 0) return fail(QSIM_ERR_ARG, "batch < 0");
+  if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "bad dtype");
+  if (batch == 0) return QSIM_OK;
+  if (!d_states || !d_z) return fail(QSIM_ERR_ARG, "NULL buffer");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  double* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&scratch), (size_t)z_partials_count(n, batch) * 8, st);
+  if (e != cudaSuccess) return fail(QSIM_ERR_OOM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+  e = launch_expval_z(d_states, n, batch, dtype, scratch, d_z, st);
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return cuda_fail(e, "<Z> kernels");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "scratch free");
+  return QSIM_OK;
+}
+
+void qsim_plan_destroy(qsim_plan_t p) {
+  if (!p) return;
+  if (p->uploaded || p->B_cap >= 0) {
+    cudaStreamSynchronize(p->last_stream);
+    p->free_all();
+  }
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// Angle -> coefficient formation, and the deterministic FP64 reductions (<Z>, gradients).
+#include <cuda_runtime.h>
+
+#include "launch.hpp"
+
+namespace qsim {
+
+std::atomic<long long> g_kernel_launches{0};
+
+// ------------------------------------------------------------------ coefficients
+// Gate-matrix caching (Section III-A, Eq. 1) writes R_x(theta) = cos(theta/2) R_xa + (-i sin(theta/2)) R_xb
+// with fixed partial matrices and two angle-dependent scalars. Here the scalars are formed once per
+// forward for every (gate, sample) and stored as one coefficient per rotation (tan or cot of theta/2,
+// whichever is at most 1 in magnitude) plus the factored-out cos / sin, accumulated per pass.
+template <typename T>
+__global__ void coef_kernel(CoefArgs a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)a.P * a.B) return;
+  const int p = (int)(id / a.B), b = (int)(id - (int64_t)p * a.B);
+  const T* params = reinterpret_cast<const T*>(a.params);
+  const T* inputs = reinterpret_cast<const T*>(a.inputs);
+  T* coef = reinterpret_cast<T*>(a.coef);
+  const int e0 = a.exec_begin[p], e1 = a.exec_begin[p + 1];
+  double fs = 1.0;
+  for (int e = e0; e < e1; e++) {
+    const int g = a.exec_gates[e];
+    const int ty = a.gate_type[g];
+    if (ty <= QSIM_RZ) {
+      const int pr = a.gate_param[g];
+      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * a.n_inputs + (-2 - pr)];
+      double s, c;
+      sincos(0.5 * th, &s, &c);
+      const int64_t gi = (int64_t)g * a.B + b;
+      if (fabs(s) <= fabs(c)) {
+        coef[gi] = (T)(s / c);
+        a.form[gi] = 0;
+        fs *= c;
+      } else {
+        coef[gi] = (T)(c / s);
+        a.form[gi] = 1;
+        fs *= s;
+      }
+    } else if (ty == QSIM_H) {
+      fs *= 0.70710678118654752440;
+    }
+  }
+  reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)fs;
+  // backward: ops undone in reverse execution order; gm = (product of inverse scales so far)^2
+  double bs = 1.0;
+  for (int e = e1 - 1; e >= e0; e--) {
+    const int g = a.exec_gates[e];
+    const int ty = a.gate_type[g];
+    if (ty <= QSIM_RZ) {
+      const int64_t gi = (int64_t)g * a.B + b;
+      a.gm[gi] = bs * bs;
+      const int pr = a.gate_param[g];
+      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * a.n_inputs + (-2 - pr)];
+      double s, c;
+      sincos(0.5 * th, &s, &c);
+      bs *= (a.form[gi] == 0) ? c : -s;
+    } else if (ty == QSIM_H) {
+      bs *= 0.70710678118654752440;
+    }
+  }
+  reinterpret_cast<T*>(a.scale_b)[(int64_t)p * a.B + b] = (T)bs;
+}
+
+cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
+  const int64_t n = (int64_t)a.P * a.B;
+  if (n == 0) return cudaSuccess;
+  const int thr = 128;
+  const unsigned blocks = (unsigned)((n + thr - 1) / thr);
+  if (dtype == QSIM_C128) coef_kernel<double><<<blocks, thr, 0, st>>>(a);
+  else coef_kernel<float><<<blocks, thr, 0, st>>>(a);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ fixed-order block reduction
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  // fixed tree: warp butterflies, then warp 0 over the warp totals -> same order every run
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (warp == 0) {
+    r = lane < nw ? sh[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+  }
+  __syncthreads();
+  return r;   // valid in thread 0
+}
+
+// z[b][q] from per-tile partials: block per (b, q).
+__global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Lnl, int n_nonlocal, int64_t tps,
+                               int n, int B, double* z) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x / n, q = blockIdx.x - (blockIdx.x / n) * n;
+  const int pos = n - 1 - q;
+  int tbit = -1, nlbit = -1;
+  for (int j = 0; j < k; j++)
+    if (Lnl[j] == pos) tbit = j;
+  for (int j = 0; j < n_nonlocal; j++)
+    if (Lnl[k + j] == pos) nlbit = j;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < tps; t += blockDim.x) {
+    const double* row = zpart + ((int64_t)b * tps + t) * (k + 1);
+    if (tbit >= 0) acc += row[tbit];
+    else acc += ((t >> nlbit) & 1) ? -row[k] : row[k];
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) z[(int64_t)b * n + q] = acc;
+}
+
+cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Lnl, int n_nonlocal, int64_t tps, int n,
+                           int B, double* z, cudaStream_t st) {
+  if ((int64_t)B * n == 0) return cudaSuccess;
+  z_final_kernel<<<(unsigned)(B * n), 256, 0, st>>>(zpart, k, d_Lnl, n_nonlocal, tps, n, B, z);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ gradients
+// G[j][b] = gm[g_j][b] * sum over the sample's tiles of the slot's partials (block per (j, b)).
+__global__ void grad_gather_kernel(GradReduceArgs a) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x / a.B, b = blockIdx.x - (blockIdx.x / a.B) * a.B;
+  const double* src = a.gpart + (a.occ_slot[j] * a.B + b) * a.tiles_per_sample;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < a.tiles_per_sample; t += blockDim.x) acc += src[t];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) a.G[(int64_t)j * a.B + b] = acc * a.gm[(int64_t)a.occ_gate[j] * a.B + b];
+}
+
+// dparams[p] = sum over occurrences (fixed order) of sum_b G[j][b]; dinputs[b][c] likewise per sample.
+__global__ void grad_scatter_kernel(GradReduceArgs a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t np = a.dparams ? a.n_params : 0;
+  const int64_t ni = a.dinputs ? (int64_t)a.B * a.n_inputs : 0;
+  if (id < np) {
+    double acc = 0.0;
+    for (int o = a.p_ptr[id]; o < a.p_ptr[id + 1]; o++) {
+      const double* row = a.G + (int64_t)a.p_occ[o] * a.B;
+      for (int b = 0; b < a.B; b++) acc += row[b];
+    }
+    a.dparams[id] = acc;
+  } else if (id < np + ni) {
+    const int64_t r = id - np;
+    const int b = (int)(r / a.n_inputs), c = (int)(r - (r / a.n_inputs) * a.n_inputs);
+    double acc = 0.0;
+    for (int o = a.i_ptr[c]; o < a.i_ptr[c + 1]; o++) acc += a.G[(int64_t)a.i_occ[o] * a.B + b];
+    a.dinputs[r] = acc;
+  }
+}
+
+cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st) {
+  if (a.n_occ > 0 && a.B > 0) {
+    grad_gather_kernel<<<(unsigned)(a.n_occ * a.B), 256, 0, st>>>(a);
+    g_kernel_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t total = (a.dparams ? a.n_params : 0) + (a.dinputs ? (int64_t)a.B * a.n_inputs : 0);
+  if (total > 0) {
+    grad_scatter_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
+    g_kernel_launches++;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ standalone <Z>
+// Block = 2^ZB consecutive amplitudes of one sample (ZB = min(n, 12)); each thread accumulates
+// its elements' |psi|^2 and signed sums over the index bits that vary inside its own elements,
+// the block turns those into (ZB + 1) partials, a final pass maps bits to qubits.
+constexpr int kZBits = 12;
+constexpr int kZThreads = 256;
+
+template <typename T>
+__global__ void z_partials_kernel(const T* states, int n, int zb, double* part) {
+  __shared__ double sred[kZThreads * 6];
+  const int64_t blocks_per_sample = (int64_t)1 << (n - zb);
+  const int64_t blk = blockIdx.x;
+  const int b = (int)(blk / blocks_per_sample);
+  const int64_t base = ((int64_t)b << n) + ((blk - (int64_t)b * blocks_per_sample) << zb);
+  const int nthr = blockDim.x;
+  int lg = 0;
+  while ((1 << lg) < nthr) lg++;
+  const int per = (1 << zb) >> lg;          // elements per thread (>= 1), stride nthr
+  int nb = 0;
+  while ((1 << nb) < per) nb++;
+  double tot = 0.0, sg[5] = {0, 0, 0, 0, 0};
+  for (int i = 0; i < per; i++) {
+    const int64_t x = base + threadIdx.x + (int64_t)i * nthr;
+    const double re = (double)states[2 * x], im = (double)states[2 * x + 1];
+    const double p = re * re + im * im;
+    tot += p;
+    for (int r = 0; r < nb; r++) sg[r] += ((i >> r) & 1) ? -p : p;
+  }
+  sred[threadIdx.x * 6] = tot;
+  for (int r = 0; r < 5; r++) sred[threadIdx.x * 6 + 1 + r] = sg[r];
+  __syncthreads();
+  for (int j = threadIdx.x; j <= zb; j += nthr) {
+    double acc = 0.0;
+    if (j == zb) {
+      for (int u = 0; u < nthr; u++) acc += sred[u * 6];
+    } else if (j < lg) {
+      for (int u = 0; u < nthr; u++) acc += ((u >> j) & 1) ? -sred[u * 6] : sred[u * 6];
+    } else {
+      for (int u = 0; u < nthr; u++) acc += sred[u * 6 + 1 + (j - lg)];
+    }
+    part[blk * (zb + 1) + j] = acc;
+  }
+}
+
+__global__ void z_block_final_kernel(const double* part, int n, int zb, int B, double* z) {
+  __shared__ double sh[32];
+  const int b = blockIdx.x / n, q = blockIdx.x - (blockIdx.x / n) * n;
+  const int pos = n - 1 - q;
+  const int64_t bps = (int64_t)1 << (n - zb);
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < bps; t += blockDim.x) {
+    const double* row = part + ((int64_t)b * bps + t) * (zb + 1);
+    if (pos < zb) acc += row[pos];
+    else acc += ((t >> (pos - zb)) & 1) ? -row[zb] : row[zb];
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) z[(int64_t)b * n + q] = acc;
+}
+
+int64_t z_partials_count(int n, int B) {
+  const int zb = n < kZBits ? n : kZBits;
+  return (int64_t)B * ((int64_t)1 << (n - zb)) * (zb + 1);
+}
+
+cudaError_t launch_expval_z(const void* states, int n, int B, int dtype, double* scratch, double* z,
+                            cudaStream_t st) {
+  if ((int64_t)B * n == 0) return cudaSuccess;
+  const int zb = n < kZBits ? n : kZBits;
+  int thr = kZThreads;
+  while (thr > (1 << zb)) thr >>= 1;
+  if (thr < 32) thr = 32;
+  const int64_t blocks = (int64_t)B << (n - zb);
+  if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  if ((1 << zb) < thr) {
+    // fewer amplitudes than a warp: the per-thread loop would be empty for some threads
+    thr = 1 << zb;
+  }
+  if (dtype == QSIM_C128)
+    z_partials_kernel<double><<<(unsigned)blocks, thr, 0, st>>>(reinterpret_cast<const double*>(states), n, zb, scratch);
+  else
+    z_partials_kernel<float><<<(unsigned)blocks, thr, 0, st>>>(reinterpret_cast<const float*>(states), n, zb, scratch);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  z_block_final_kernel<<<(unsigned)(B * n), 256, 0, st>>>(scratch, n, zb, B, z);
+  g_kernel_launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace qsim

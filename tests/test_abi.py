@@ -1,0 +1,83 @@
+"""The C ABI library: it loads, exports every function that include/qsim.h declares, and its host-only
+entry points (planning, validation, schedule description, index maps) behave. No GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qsim.h")
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2404_09213_gb300 import build
+    build.build()
+    import paper_2404_09213_gb300 as q
+    return q
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qsim_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("qsim_plan", "qsim_forward", "qsim_backward", "qsim_plan_destroy", "qsim_last_error",
+                 "qsim_sync_status", "qsim_expval_z"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(q):
+    from paper_2404_09213_gb300 import _lib
+    L = ctypes.CDLL(_lib.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(L, name), f"{name} declared in qsim.h but not exported"
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature in the binding"
+
+
+def test_struct_sizes_match_header(q):
+    from paper_2404_09213_gb300 import _lib
+    assert ctypes.sizeof(_lib.QsimGate) == 24
+    assert ctypes.sizeof(_lib.QsimPlanOpts) == 32
+    assert ctypes.sizeof(_lib.QsimPlanInfo) == 48
+
+
+@pytest.mark.parametrize("gates,n,code", [
+    ([W.gate(9, (0,))], 2, -4),                                 # unknown type
+    ([W.gate(W.RX, (2,), param=0)], 2, -2),                      # qubit out of range
+    ([W.gate(W.CNOT, (1,), (1,))], 2, -2),                       # control == target
+    ([W.gate(W.RY, (0,))], 2, -3),                               # rotation without parameter
+    ([W.gate(W.H, (0,), param=3)], 2, -3),                       # fixed gate with a parameter
+    ([W.gate(W.RX, (0, 1), param=0)], 2, -2),                    # stray second target
+    ([], 0, -9),                                                 # n_qubits out of range
+    ([], 35, -9),
+])
+def test_validation_errors(q, gates, n, code):
+    with pytest.raises(q.QsimError) as e:
+        q.Plan(gates, n)
+    assert e.value.code == code
+    assert str(e.value)
+
+
+def test_backward_without_forward_is_rejected(q):
+    p = q.Plan(W.ring_ansatz(3, 1), 3)
+    from paper_2404_09213_gb300 import _lib
+    rc = _lib.lib().qsim_backward(p._h, ctypes.c_void_p(16), None, None, None)
+    assert rc == -5 and b"without a preceding forward" in _lib.lib().qsim_last_error()
+
+
+def test_plan_info_and_defaults(q):
+    p = q.Plan(W.ring_ansatz(20, 10), 20)
+    inf = p.info()
+    assert (inf["n_qubits"], inf["n_gates"], inf["n_params"], inf["n_inputs"], inf["k"]) == (20, 620, 400, 20, 12)
+    p2 = q.Plan(W.ring_ansatz(20, 2), 20, dtype="c128")
+    assert p2.info()["k"] == 11
+    p3 = q.Plan(W.ring_ansatz(5, 2), 5, mode="per_gate")
+    assert p3.info()["n_passes"] == len(W.ring_ansatz(5, 2))

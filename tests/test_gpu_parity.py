@@ -1,0 +1,217 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: complex64 |dz| <= 1e-5, states <= 1e-5, gradients norm-wise relative <= 1e-4 and
+elementwise <= 1e-4 max|g_ref| + 1e-7; complex128 1e-12 throughout.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from gpu_util import TOL, tensors, rounded, check_grad, random_circuit, shift_grad_strided
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def q():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_09213_gb300 import build
+    build.build()
+    import paper_2404_09213_gb300 as q
+    return q
+
+
+def run(q, wl, dtype, mode="fused", init=None, backward=True, **kw):
+    plan = q.Plan(wl.gates, wl.n, dtype=dtype, mode=mode, **kw)
+    p, x, g = tensors(wl, dtype)
+    states, z = plan.forward(p, x, init=init)
+    out = {"states": states.cpu().numpy(), "z": z.cpu().numpy(), "plan": plan}
+    if backward:
+        dp, di = plan.backward(g)
+        out["dp"], out["di"] = dp.cpu().numpy(), di.cpu().numpy()
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    return out
+
+
+# ---------------------------------------------------------------- C1 (4 qubits, batch 8, complex128)
+@pytest.mark.parametrize("mode", ["fused", "per_gate"])
+def test_c1_complex128(q, mode):
+    wl = W.config(1)
+    r = run(q, wl, "c128", mode)
+    psi = oracle.simulate_kron(wl.gates, wl.n, wl.params, wl.inputs)
+    np.testing.assert_allclose(r["states"], psi, atol=1e-12, rtol=0)
+    zref = np.loadtxt(os.path.join(GOLDEN, "c1_z.txt"))
+    np.testing.assert_allclose(r["z"], zref, atol=1e-12, rtol=0)
+    dp, di = oracle.grad_param_shift(wl.gates, wl.n, wl.params, wl.inputs, wl.grad_out)
+    check_grad(r["dp"], dp, "c128", "C1 dparams")
+    check_grad(r["di"], di, "c128", "C1 dinputs")
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_c1_fused_tile_sizes(q, k):
+    wl = W.config(1)
+    r = run(q, wl, "c128", "fused", k=k, contiguous_bits=1)
+    psi = oracle.simulate_kron(wl.gates, wl.n, wl.params, wl.inputs)
+    np.testing.assert_allclose(r["states"], psi, atol=1e-12, rtol=0)
+
+
+# ---------------------------------------------------------------- random circuits, all gate types
+CASES = []
+for seed, (n, dtype, mode, k, c) in enumerate([
+        (1, "c64", "fused", 1, 1), (2, "c64", "fused", 2, 1), (3, "c128", "fused", 3, 1),
+        (5, "c64", "fused", 4, 2), (6, "c128", "fused", 5, 2), (7, "c64", "fused", 5, 3),
+        (8, "c64", "fused", 6, 2), (9, "c128", "fused", 7, 3), (10, "c64", "fused", 8, 4),
+        (10, "c64", "fused", 10, 4), (11, "c64", "fused", 7, 2), (6, "c64", "per_gate", 0, 0),
+        (9, "c128", "per_gate", 0, 0), (12, "c64", "fused", 12, 4), (13, "c128", "fused", 11, 4)]):
+    CASES.append((seed, n, dtype, mode, k, c))
+
+
+@pytest.mark.parametrize("seed,n,dtype,mode,k,c", CASES)
+def test_random_circuits(q, seed, n, dtype, mode, k, c):
+    rng = np.random.default_rng(100 + seed)
+    n_par, n_in, B = 7, 3, 3
+    gates = random_circuit(rng, n, 8 * n + 10, n_par, n_in)
+    params = rng.uniform(0, 2 * math.pi, n_par)
+    inputs = rng.uniform(0, math.pi, (B, n_in))
+    g = rng.uniform(-1, 1, (B, n))
+    use_init = seed % 3 == 1
+    init_np = None
+    if use_init:
+        init_np = rng.normal(size=(B, 2 ** n)) + 1j * rng.normal(size=(B, 2 ** n))
+        init_np /= np.linalg.norm(init_np, axis=1, keepdims=True)
+    wl = W.Workload("rand", n, B, dtype, gates, params, inputs, g)
+    pr, ir = rounded(wl, dtype)
+    cdt = torch.complex128 if dtype == "c128" else torch.complex64
+    init = torch.tensor(init_np, dtype=cdt, device="cuda") if use_init else None
+    r = run(q, wl, dtype, mode, init=init, k=k, contiguous_bits=c)
+    init_ref = init.cpu().numpy().astype(np.complex128) if use_init else None
+    psi = oracle.simulate_strided(gates, n, pr, ir, init=init_ref)
+    t = TOL[dtype]
+    np.testing.assert_allclose(r["states"], psi, atol=t["state"], rtol=0)
+    np.testing.assert_allclose(r["z"], oracle.expval_z(psi, n), atol=t["z"], rtol=0)
+    dp, di = oracle.grad_param_shift(gates, n, pr, ir, g, method="strided", init=init_ref)
+    check_grad(r["dp"], dp, dtype, "dparams")
+    check_grad(r["di"], di, dtype, "dinputs")
+
+
+# ---------------------------------------------------------------- C2 (12 qubits, batch 1024, complex64)
+@pytest.mark.parametrize("mode", ["fused", "per_gate"])
+def test_c2_full_batch(q, mode):
+    wl = W.config(2)
+    r = run(q, wl, "c64", mode, backward=False)
+    pr, ir = rounded(wl, "c64")
+    zref = oracle.forward_z(wl.gates, wl.n, pr, ir[:32], method="strided")
+    np.testing.assert_allclose(r["z"][:32], zref, atol=1e-5, rtol=0)
+    norms = np.linalg.norm(r["states"], axis=1)
+    np.testing.assert_allclose(norms, 1.0, atol=1e-5)
+
+
+def test_c2_fused_equals_per_gate_all_samples(q):
+    wl = W.config(2)
+    a = run(q, wl, "c64", "fused", backward=False)
+    b = run(q, wl, "c64", "per_gate", backward=False)
+    np.testing.assert_allclose(a["z"], b["z"], atol=1e-5, rtol=0)
+    np.testing.assert_allclose(a["states"], b["states"], atol=1e-5, rtol=0)
+
+
+# ---------------------------------------------------------------- C3 (20 qubits, batch 64) at full size
+def test_c3_full_size_sampled(q):
+    wl = W.config(3)
+    # only samples 0 and 1 carry loss weight, so the batch-summed parameter gradient is checkable
+    g = np.zeros_like(wl.grad_out)
+    g[:2] = wl.grad_out[:2]
+    wl.grad_out = g
+    r = run(q, wl, "c64", "fused")
+    pr, ir = rounded(wl, "c64")
+    norms = np.linalg.norm(r["states"], axis=1)
+    np.testing.assert_allclose(norms, 1.0, atol=1e-5)
+    psi = oracle.simulate_strided(wl.gates, wl.n, pr, ir[:2])
+    np.testing.assert_allclose(r["states"][:2], psi, atol=1e-5, rtol=0)
+    np.testing.assert_allclose(r["z"][:2], oracle.expval_z(psi, wl.n), atol=1e-5, rtol=0)
+    # parameter-shift on a sample of gates: two in the last layer, one in the first trainable layer
+    L = len(wl.gates)
+    first = L - 2 * wl.n - 3
+    pre = (first, oracle.simulate_strided(wl.gates[:first], wl.n, pr, ir[:2]))
+    for gi in (L - wl.n - 1, first):
+        d = shift_grad_strided(wl.gates, wl.n, pr, ir[:2], g[:2], gi, prefix=pre)
+        p = wl.gates[gi][3]
+        ref = d.sum()
+        assert abs(r["dp"][p] - ref) <= 1e-4 * max(1e-3, np.abs(r["dp"]).max()), (gi, r["dp"][p], ref)
+
+
+# ---------------------------------------------------------------- C5 ansatz at 12 qubits, checkpointed
+@pytest.mark.parametrize("ckpt", [0, 1, 3])
+def test_c5_ansatz_12q_checkpointed(q, ckpt):
+    wl = W.config(5, n=12, batch=2)
+    r = run(q, wl, "c64", "fused", k=8, checkpoint_passes=ckpt)
+    if ckpt:
+        assert r["plan"].info()["n_checkpoints"] >= 1
+    pr, ir = rounded(wl, "c64")
+    psi = oracle.simulate_strided(wl.gates, wl.n, pr, ir)
+    np.testing.assert_allclose(r["z"], oracle.expval_z(psi, wl.n), atol=1e-5, rtol=0)
+    subset = list(range(0, wl.n_params, 12))
+    dp, di = oracle.grad_param_shift(wl.gates, wl.n, pr, ir, wl.grad_out, method="strided",
+                                     param_subset=subset)
+    check_grad(r["dp"][subset], dp[subset], "c64", "C5@12q dparams subset")
+    check_grad(r["di"], di, "c64", "C5@12q dinputs")
+
+
+# ---------------------------------------------------------------- determinism, in-place init, edges
+def test_bitwise_deterministic(q):
+    wl = W.config(3, batch=4, layers=3)
+    a = run(q, wl, "c64")
+    b = run(q, wl, "c64")
+    assert np.array_equal(a["z"], b["z"]) and np.array_equal(a["dp"], b["dp"]) and np.array_equal(a["di"], b["di"])
+
+
+def test_inplace_init_and_empty_circuit(q):
+    n, B = 9, 2
+    rng = np.random.default_rng(1)
+    s = rng.normal(size=(B, 2 ** n)) + 1j * rng.normal(size=(B, 2 ** n))
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    st = torch.tensor(s, dtype=torch.complex64, device="cuda")
+    plan = q.Plan([], n)
+    out, z = plan.forward(None, None, init=st, states=st)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(z.cpu().numpy(), oracle.expval_z(st.cpu().numpy().astype(complex), n), atol=1e-6)
+    wl = W.config(3, n=n, batch=B, layers=2)
+    plan = q.Plan(wl.gates, n, k=6)
+    p, x, g = tensors(wl, "c64")
+    st2 = torch.tensor(s, dtype=torch.complex64, device="cuda")
+    out, z = plan.forward(p, x, init=st2, states=st2)
+    pr, ir = rounded(wl, "c64")
+    psi = oracle.simulate_strided(wl.gates, n, pr, ir, init=s.astype(np.complex64).astype(complex))
+    np.testing.assert_allclose(out.cpu().numpy(), psi, atol=1e-5)
+
+
+def test_expval_z_standalone(q):
+    rng = np.random.default_rng(4)
+    for n, B, dt in ((1, 3, torch.complex64), (5, 2, torch.complex128), (13, 3, torch.complex64),
+                     (16, 2, torch.complex128)):
+        s = rng.normal(size=(B, 2 ** n)) + 1j * rng.normal(size=(B, 2 ** n))
+        s /= np.linalg.norm(s, axis=1, keepdims=True)
+        st = torch.tensor(s, dtype=dt, device="cuda")
+        z = q.expval_z(st, n).cpu().numpy()
+        np.testing.assert_allclose(z, oracle.expval_z(st.cpu().numpy().astype(complex), n),
+                                   atol=1e-6 if dt == torch.complex64 else 1e-13)
+
+
+def test_autograd_layer(q):
+    wl = W.config(3, n=8, batch=4, layers=3)
+    layer = q.QSimLayer(wl.gates, wl.n, init_params=wl.params).cuda()
+    x = torch.tensor(wl.inputs, dtype=torch.float32, device="cuda", requires_grad=True)
+    z = layer(x)
+    loss = (torch.tensor(wl.grad_out, device="cuda") * z).sum()
+    loss.backward()
+    pr, ir = rounded(wl, "c64")
+    dp, di = oracle.grad_param_shift(wl.gates, wl.n, pr, ir, wl.grad_out, method="strided")
+    check_grad(layer.weight.grad.double().cpu().numpy(), dp, "c64", "layer dparams")
+    check_grad(x.grad.double().cpu().numpy(), di, "c64", "layer dinputs")

@@ -1,0 +1,146 @@
+"""Host planner invariants (bit-exact): every gate emitted once, per-wire order kept, passes k-local,
+register phases consistent, shared-memory layouts bijective, gather/scatter index maps equal to a
+brute-force permutation of the 2^n indices."""
+import itertools
+import random
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2404_09213_gb300 import build
+    build.build()
+    import paper_2404_09213_gb300 as q
+    return q
+
+
+def random_circuit(rng, n, g, n_params=6, n_inputs=2):
+    out = []
+    for _ in range(g):
+        k = rng.randrange(7)
+        if k in (W.RX, W.RY, W.RZ):
+            p = rng.randrange(n_params) if (rng.random() < 0.7 or n_inputs == 0) else W.input_param(rng.randrange(n_inputs))
+            out.append(W.gate(k, (rng.randrange(n),), param=p))
+        elif k in (W.H, W.X):
+            out.append(W.gate(k, (rng.randrange(n),)))
+        elif n >= 2:
+            c, t = rng.sample(range(n), 2)
+            out.append(W.gate(k, (t,), (c,)))
+    return out
+
+
+def gate_qubits(g):
+    return [g[1][0]] + ([g[2][0]] if g[2][0] >= 0 else [])
+
+
+CASES = [("ring20", W.ring_ansatz(20, 10), 20, {}), ("ring12", W.ring_ansatz(12, 6), 12, {}),
+         ("ring30", W.ring_ansatz(30, 2), 30, {}), ("hea15", W.hea_cz_ansatz(15, 5), 15, {}),
+         ("ring20k8", W.ring_ansatz(20, 3), 20, {"k": 8}), ("ring10c2", W.ring_ansatz(10, 3), 10, {"k": 6, "contiguous_bits": 2}),
+         ("c128", W.ring_ansatz(16, 3), 16, {"dtype": "c128"})]
+_r = random.Random(7)
+for i in range(12):
+    n = _r.randint(1, 14)
+    CASES.append((f"rand{i}", random_circuit(_r, n, _r.randint(0, 60)), n, {"k": _r.randint(min(n, 6), 12)}))
+
+
+@pytest.mark.parametrize("name,gates,n,kw", CASES, ids=[c[0] for c in CASES])
+def test_schedule_invariants(q, name, gates, n, kw):
+    p = q.Plan(gates, n, **kw)
+    d = p.describe()
+    k, R = d["k"], d["R"]
+    order = [g for ps in d["passes"] for g in ps["gates"]]
+    # every gate exactly once
+    assert sorted(order) == list(range(len(gates)))
+    # per-wire order preserved across passes
+    pos = {g: i for i, g in enumerate(order)}
+    last = {}
+    for gi, g in enumerate(gates):
+        for w in gate_qubits(g):
+            if w in last:
+                assert pos[last[w]] < pos[gi], f"wire {w}: gate {gi} before {last[w]}"
+            last[w] = gi
+    for ps in d["passes"]:
+        local = ps["local_qubits"]
+        assert len(local) == k and len(set(local)) == k
+        assert sorted(ps["L"]) == ps["L"] and ps["L"] == [n - 1 - q_ for q_ in local]
+        assert sorted(ps["L"] + ps["nonlocal"]) == list(range(n))
+        c = d["c"]
+        assert ps["L"][:c] == list(range(c)), "low index bits must be local (coalescing)"
+        for g in ps["gates"]:
+            assert set(gate_qubits(gates[g])) <= set(local)
+        # phases: same gates, order per wire preserved, register bits hold the targets that need them
+        ph_order = [op["gate"] for ph in ps["phases"] for op in ph["ops"]]
+        assert sorted(ph_order) == sorted(ps["gates"])
+        last_in_pass = {}
+        ppos = {g: i for i, g in enumerate(ph_order)}
+        for g in sorted(ps["gates"]):
+            for w in gate_qubits(gates[g]):
+                if w in last_in_pass:
+                    assert ppos[last_in_pass[w]] < ppos[g]
+                last_in_pass[w] = g
+        tb_of_q = {q_: j for j, q_ in enumerate(local)}
+        for ph in ps["phases"]:
+            rb, tb = ph["rbits"], ph["tbits"]
+            assert rb[0] == 0 and len(rb) == R and sorted(rb + tb) == list(range(k))
+            for op in ph["ops"]:
+                g = gates[op["gate"]]
+                t = tb_of_q[g[1][0]]
+                kind = op["kind"]
+                if kind in ("ry", "rx", "h", "x", "rz", "cx", "cx_t", "cz", "cz_t"):
+                    assert rb[op["a"]] == t or (kind in ("cz", "cz_t") and rb[op["a"]] == tb_of_q[g[2][0]])
+                if kind == "rz_t":
+                    assert op["a"] == t and t in tb
+                if kind == "cx":
+                    assert rb[op["b"]] == tb_of_q[g[2][0]]
+                if kind == "cx_t":
+                    assert op["b"] == tb_of_q[g[2][0]] and op["b"] in tb
+        # layouts are bijections of the tile
+        for m in ps["layouts"]:
+            e = np.arange(1 << k)
+            s = e.copy()
+            for j in range(k):
+                s ^= np.where((e >> j) & 1, m[j], 0)
+            assert len(np.unique(s)) == 1 << k
+            pair_ok = (s[0::2] ^ 1) == s[1::2]
+            assert pair_ok.all(), "neighbouring amplitudes must stay in adjacent words"
+        # gradient slots: one per rotation, dense
+        slots = sorted(op["gslot"] for ph in ps["phases"] for op in ph["ops"] if op["gslot"] >= 0)
+        assert slots == list(range(ps["n_gslots"]))
+        assert ps["n_gslots"] == sum(1 for g in ps["gates"] if gates[g][0] in (W.RX, W.RY, W.RZ))
+
+
+@pytest.mark.parametrize("n,kw", [(6, {"k": 4, "contiguous_bits": 2}), (10, {"k": 6}), (14, {"k": 9}),
+                                  (16, {"k": 12})])
+def test_index_maps_are_the_brute_force_permutation(q, n, kw):
+    gates = W.ring_ansatz(n, 2)
+    p = q.Plan(gates, n, **kw)
+    d = p.describe()
+    for pi, ps in enumerate(d["passes"][:4]):
+        L, NL = ps["L"], ps["nonlocal"]
+        # brute force: element index x has bit L[j] = bit j of e, bit NL[j] = bit j of tile
+        idx = np.arange(1 << n).reshape((2,) * n)                  # axis a <-> bit n-1-a
+        axes = [n - 1 - b for b in reversed(NL)] + [n - 1 - b for b in reversed(L)]
+        brute = idx.transpose(axes).reshape(1 << len(NL), 1 << len(L))
+        seen = []
+        for t in range(1 << len(NL)):
+            m = p.tile_index_map(pi, t)
+            np.testing.assert_array_equal(m, brute[t])
+            seen.append(m)
+        assert np.array_equal(np.sort(np.concatenate(seen)), np.arange(1 << n))
+
+
+def test_per_gate_schedule(q):
+    gates = W.ring_ansatz(4, 2)
+    d = q.Plan(gates, 4, mode="per_gate").describe()
+    assert [ps["gates"] for ps in d["passes"]] == [[i] for i in range(len(gates))]
+
+
+def test_empty_circuit_and_single_qubit(q):
+    d = q.Plan([], 3).describe()
+    assert len(d["passes"]) == 1 and d["passes"][0]["gates"] == []
+    d1 = q.Plan([W.gate(W.RX, (0,), param=0), W.gate(W.H, (0,))], 1).describe()
+    assert d1["k"] == 1 and [ps["gates"] for ps in d1["passes"]] == [[0, 1]]
