@@ -42,6 +42,9 @@ struct qsim_plan_s {
   // device copy of the schedule
   bool uploaded = false;
   DevPass* d_passes = nullptr;
+  DevPass* d_passes_b = nullptr;
+  int32_t* d_exec_gates_b = nullptr;
+  int32_t* d_exec_begin_b = nullptr;
   DevPhase* d_phases = nullptr;
   DevOp* d_ops = nullptr;
   DevLayout* d_layouts = nullptr;
@@ -133,8 +136,9 @@ struct qsim_plan_s {
   void free_all() {
     free_ws();
     destroy_events();
-    void* ptrs[] = {d_passes, d_phases, d_ops, d_layouts, d_gate_type, d_gate_param, d_exec_gates, d_exec_begin,
-                    d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Lnl_last};
+    void* ptrs[] = {d_passes, d_passes_b, d_phases, d_ops, d_layouts, d_gate_type, d_gate_param, d_exec_gates,
+                    d_exec_begin, d_exec_gates_b, d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ,
+                    d_i_ptr, d_i_occ, d_Lnl_last};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     uploaded = false;
@@ -143,26 +147,31 @@ struct qsim_plan_s {
   int upload_schedule() {
     if (uploaded) return QSIM_OK;
     cudaError_t e = cudaSuccess;
-    std::vector<DevPass> passes;
-    std::vector<int32_t> gtype, gparam, exec, exec_begin;
+    std::vector<DevPass> passes, passes_b;
+    std::vector<int32_t> gtype, gparam, exec, exec_begin, exec_b, exec_begin_b;
     for (auto& g : s.gates) {
       gtype.push_back(g.type);
       gparam.push_back(g.param);
     }
     for (auto& pp : s.passes) {
       passes.push_back(pp.dev);
+      passes_b.push_back(pp.devb);
       exec_begin.push_back((int32_t)exec.size());
+      exec_begin_b.push_back((int32_t)exec_b.size());
       if (s.mode == QSIM_PER_GATE) {
         exec.push_back(pp.gates[0]);
+        exec_b.push_back(pp.gates[0]);
       } else {
         for (int i = 0; i < pp.dev.n_ops; i++) exec.push_back(s.ops[pp.dev.op0 + i].gate);
+        for (int i = 0; i < pp.devb.n_ops; i++) exec_b.push_back(s.ops[pp.devb.op0 + i].gate);
       }
     }
     exec_begin.push_back((int32_t)exec.size());
+    exec_begin_b.push_back((int32_t)exec_b.size());
     n_occ = (int)s.grad_gate.size();
     std::vector<int32_t> occ_gate(s.grad_gate.begin(), s.grad_gate.end());
     std::vector<int64_t> occ_slot(n_occ);
-    for (int j = 0; j < n_occ; j++) occ_slot[j] = s.passes[s.grad_pass[j]].dev.gpart_offset + s.grad_slot[j];
+    for (int j = 0; j < n_occ; j++) occ_slot[j] = s.passes[s.grad_pass[j]].devb.gpart_offset + s.grad_slot[j];
     std::vector<int32_t> p_ptr(s.n_params + 1, 0), i_ptr(s.n_inputs + 1, 0), p_occ, i_occ;
     for (int p = 0; p < s.n_params; p++) {
       for (int j = 0; j < n_occ; j++)
@@ -184,6 +193,9 @@ struct qsim_plan_s {
 #define QSIM_UP(PTR, VEC) \
   if (e == cudaSuccess) e = upload(&PTR, VEC);
     QSIM_UP(d_passes, passes)
+    QSIM_UP(d_passes_b, passes_b)
+    QSIM_UP(d_exec_gates_b, exec_b)
+    QSIM_UP(d_exec_begin_b, exec_begin_b)
     QSIM_UP(d_phases, s.phases)
     QSIM_UP(d_ops, s.ops)
     QSIM_UP(d_layouts, s.layouts)
@@ -203,9 +215,8 @@ struct qsim_plan_s {
     if (s.mode == QSIM_FUSED) {
       size_t mf = 0, mb = 0;
       for (auto& pp : s.passes) {
-        const int Rf = fwd_R_for(pp.dev.k, s.dtype), Rb = bwd_R_for(pp.dev.k, s.dtype);
-        mf = std::max(mf, fwd_pass_smem(pp.dev, s.dtype, 1 << (pp.dev.k - Rf)));
-        mb = std::max(mb, bwd_pass_smem(pp.dev, s.dtype, 1 << (pp.dev.k - Rb)));
+        mf = std::max(mf, fwd_pass_smem(pp.dev, s.dtype, 1 << (pp.dev.k - pp.dev.R)));
+        mb = std::max(mb, bwd_pass_smem(pp.devb, s.dtype, 1 << (pp.devb.k - pp.devb.R)));
       }
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
@@ -284,10 +295,10 @@ struct qsim_plan_s {
     return n_segments - 1;
   }
 
-  PassLaunch pass_launch(int p, const void* scale) const {
+  PassLaunch pass_launch(int p, const void* scale, bool bwd) const {
     PassLaunch L{};
-    L.h_pass = &s.passes[p].dev;
-    L.d_pass = d_passes + p;
+    L.h_pass = bwd ? &s.passes[p].devb : &s.passes[p].dev;
+    L.d_pass = (bwd ? d_passes_b : d_passes) + p;
     L.d_phases = d_phases;
     L.d_ops = d_ops;
     L.d_layouts = d_layouts;
@@ -357,7 +368,7 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
     if (o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   }
   p->opts = o;
-  rc = build_schedule(gv, n_qubits, o, fwd_R_for(o.k > 0 ? o.k : 12, o.dtype), p->s, err);
+  rc = build_schedule(gv, n_qubits, o, fwd_R_for(16, o.dtype), bwd_R_for(16, o.dtype), p->s, err);
   if (rc) {
     delete p;
     return fail(rc, err);
@@ -434,6 +445,8 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   ca.gate_param = p->d_gate_param;
   ca.exec_gates = p->d_exec_gates;
   ca.exec_begin = p->d_exec_begin;
+  ca.exec_gates_b = p->d_exec_gates_b;
+  ca.exec_begin_b = p->d_exec_begin_b;
   ca.params = d_params;
   ca.inputs = d_inputs;
   ca.n_inputs = s.n_inputs;
@@ -470,7 +483,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
       else in = out;
       double* zp = (q == P_ - 1) ? p->zpart : nullptr;
       if (p->profiling) cudaEventRecord(p->ev_f0[p->fslot(q)], st);
-      e = launch_fwd_pass(p->pass_launch(q, sf + (size_t)q * batch * p->sc), s.dtype, in, out, zp, st);
+      e = launch_fwd_pass(p->pass_launch(q, sf + (size_t)q * batch * p->sc, false), s.dtype, in, out, zp, st);
       if (e != cudaSuccess) return cuda_fail(e, "fused forward pass");
       if (p->profiling) cudaEventRecord(p->ev_f1[p->fslot(q)], st);
     }
@@ -515,7 +528,7 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
       void* pout = q == 0 ? nullptr : p->W;
       void* lout = q == 0 ? nullptr : p->Lam;
       if (p->profiling) cudaEventRecord(p->ev_b0[p->bslot(q)], st);
-      e = launch_bwd_pass(p->pass_launch(q, sbk + (size_t)q * B * p->sc), s.dtype, pin, pout, lin, lout, d_grad_out,
+      e = launch_bwd_pass(p->pass_launch(q, sbk + (size_t)q * B * p->sc, true), s.dtype, pin, pout, lin, lout, d_grad_out,
                           p->gpart, st);
       if (e != cudaSuccess) return cuda_fail(e, "fused backward pass");
       if (p->profiling) cudaEventRecord(p->ev_b1[p->bslot(q)], st);

@@ -678,7 +678,7 @@ cudaError_t prepare_pass_kernels(int dtype, size_t max_fwd_smem, size_t max_bwd_
 template <typename T>
 static cudaError_t fwd_dispatch(const PassLaunch& L, const void* in, void* out, double* zpart, cudaStream_t st) {
   const DevPass& p = *L.h_pass;
-  const int R = fwd_R_for(p.k, sizeof(T) == 8 ? QSIM_C128 : QSIM_C64);
+  const int R = p.R;
   const int nthr = 1 << (p.k - R);
   const size_t smem = fwd_pass_smem(p, sizeof(T) == 8 ? QSIM_C128 : QSIM_C64, nthr);
   const int64_t blocks = p.tiles_per_sample * L.B;
@@ -700,7 +700,7 @@ template <typename T>
 static cudaError_t bwd_dispatch(const PassLaunch& L, const void* pin, void* pout, const void* lin, void* lout,
                                 const double* g, double* gpart, cudaStream_t st) {
   const DevPass& p = *L.h_pass;
-  const int R = bwd_R_for(p.k, sizeof(T) == 8 ? QSIM_C128 : QSIM_C64);
+  const int R = p.R;
   const int nthr = 1 << (p.k - R);
   const size_t smem = bwd_pass_smem(p, sizeof(T) == 8 ? QSIM_C128 : QSIM_C64, nthr);
   const int64_t blocks = p.tiles_per_sample * L.B;

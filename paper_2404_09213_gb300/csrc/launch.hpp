@@ -48,8 +48,10 @@ int max_k_for(int dtype);
 struct CoefArgs {
   const int32_t* gate_type;     // [G]
   const int32_t* gate_param;    // [G]
-  const int32_t* exec_gates;    // gate indices of every pass in execution order
+  const int32_t* exec_gates;    // gate indices of every pass in forward execution order
   const int32_t* exec_begin;    // [P + 1]
+  const int32_t* exec_gates_b;  // gate indices of every pass in the backward op order (undone last to first)
+  const int32_t* exec_begin_b;  // [P + 1]
   const void* params;
   const void* inputs;
   int n_inputs, B, P;

@@ -145,8 +145,7 @@ int64_t tile_element_index(const DevPass& p, int64_t tile, int64_t e) {
   return x;
 }
 
-static int build_phases(Schedule& s, PassPlan& pp, int w0, Lcg& rng, std::string& err) {
-  DevPass& d = pp.dev;
+static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w0, Lcg& rng, std::string& err) {
   const int n = s.n, k = d.k, R = d.R;
   int tb_of_q[kMaxQubits];
   for (int q = 0; q < n; q++) tb_of_q[q] = -1;
@@ -240,9 +239,11 @@ static int build_phases(Schedule& s, PassPlan& pp, int w0, Lcg& rng, std::string
       if (is_rot(g.type)) {
         op.rot = 1;
         op.gslot = gslot++;
-        s.grad_gate.push_back(gi);
-        s.grad_pass.push_back((int)(&pp - &s.passes[0]));
-        s.grad_slot.push_back(op.gslot);
+        if (grads) {
+          s.grad_gate.push_back(gi);
+          s.grad_pass.push_back((int)(&pp - &s.passes[0]));
+          s.grad_slot.push_back(op.gslot);
+        }
       }
       s.ops.push_back(op);
     }
@@ -264,7 +265,7 @@ static int build_phases(Schedule& s, PassPlan& pp, int w0, Lcg& rng, std::string
   return QSIM_OK;
 }
 
-int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& o, int R_fwd,
+int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& o, int R_fwd, int R_bwd,
                    Schedule& s, std::string& err) {
   s = Schedule{};
   s.n = n;
@@ -284,8 +285,10 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
     return QSIM_ERR_ARG;
   }
   int R = std::min(R_fwd, k);
+  int Rb = std::min(R_bwd, k);
   s.k = k;
   s.R = R;
+  s.Rb = Rb;
   s.c = c;
   int G = (int)gates.size();
   for (auto& g : gates) {
@@ -302,6 +305,7 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
       pp.dev.k = 0;
       pp.dev.n_gslots = is_rot(gates[i].type) ? 1 : 0;
       pp.dev.gpart_offset = s.total_gslots;
+      pp.devb = pp.dev;
       if (is_rot(gates[i].type)) {
         s.grad_gate.push_back(i);
         s.grad_pass.push_back(i);
@@ -369,10 +373,15 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
   const int w0 = (o.dtype == QSIM_C128) ? 0 : 1;
   Lcg rng{0x51ED270B5EEDULL};
   for (auto& pp : s.passes) {
-    int rc = build_phases(s, pp, w0, rng, err);
+    pp.devb = pp.dev;
+    pp.devb.R = Rb;
+    int rc = build_phases(s, pp, pp.dev, false, w0, rng, err);
+    if (rc) return rc;
+    rc = build_phases(s, pp, pp.devb, true, w0, rng, err);
     if (rc) return rc;
     pp.dev.gpart_offset = s.total_gslots;
-    s.total_gslots += pp.dev.n_gslots;
+    pp.devb.gpart_offset = s.total_gslots;
+    s.total_gslots += pp.devb.n_gslots;
   }
   return QSIM_OK;
 }
@@ -380,7 +389,7 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
 std::string describe_schedule(const Schedule& s) {
   static const char* kn[] = {"ry", "rx", "rz", "h", "x", "rz_t", "cx", "cx_t", "cz", "cz_t", "cz_tt"};
   std::ostringstream o;
-  o << "{\"n\":" << s.n << ",\"k\":" << s.k << ",\"R\":" << s.R << ",\"c\":" << s.c
+  o << "{\"n\":" << s.n << ",\"k\":" << s.k << ",\"R\":" << s.R << ",\"Rb\":" << s.Rb << ",\"c\":" << s.c
     << ",\"mode\":" << s.mode << ",\"n_params\":" << s.n_params << ",\"n_inputs\":" << s.n_inputs
     << ",\"passes\":[";
   for (size_t p = 0; p < s.passes.size(); p++) {
@@ -395,31 +404,36 @@ std::string describe_schedule(const Schedule& s) {
     for (int j = 0; j < d.k; j++) o << (j ? "," : "") << (int)d.L[j];
     o << "],\"nonlocal\":[";
     for (int j = 0; j < d.n_nonlocal; j++) o << (j ? "," : "") << (int)d.nonlocal[j];
-    o << "],\"n_gslots\":" << d.n_gslots << ",\"phases\":[";
-    for (int ph = 0; ph < d.n_phases; ph++) {
-      const DevPhase& P = s.phases[d.phase0 + ph];
-      if (ph) o << ",";
-      o << "{\"rbits\":[";
-      for (int i = 0; i < d.R; i++) o << (i ? "," : "") << (int)P.rbit[i];
-      o << "],\"tbits\":[";
-      for (int i = 0; i < P.n_tbits; i++) o << (i ? "," : "") << (int)P.tbit[i];
-      o << "],\"ops\":[";
-      for (int i = P.op_begin; i < P.op_end; i++) {
-        const DevOp& op = s.ops[i];
-        o << (i > P.op_begin ? "," : "") << "{\"kind\":\"" << kn[op.kind] << "\",\"gate\":" << op.gate
-          << ",\"a\":" << (int)op.a << ",\"b\":" << (int)op.b << ",\"gslot\":" << op.gslot << "}";
+    o << "],\"n_gslots\":" << d.n_gslots;
+    for (int dir = 0; dir < 2; dir++) {
+      const DevPass& D = dir == 0 ? pp.dev : pp.devb;
+      o << (dir == 0 ? ",\"phases\":[" : ",\"bwd_phases\":[");
+      for (int ph = 0; ph < D.n_phases; ph++) {
+        const DevPhase& P = s.phases[D.phase0 + ph];
+        if (ph) o << ",";
+        o << "{\"rbits\":[";
+        for (int i = 0; i < D.R; i++) o << (i ? "," : "") << (int)P.rbit[i];
+        o << "],\"tbits\":[";
+        for (int i = 0; i < P.n_tbits; i++) o << (i ? "," : "") << (int)P.tbit[i];
+        o << "],\"ops\":[";
+        for (int i = P.op_begin; i < P.op_end; i++) {
+          const DevOp& op = s.ops[i];
+          o << (i > P.op_begin ? "," : "") << "{\"kind\":\"" << kn[op.kind] << "\",\"gate\":" << op.gate
+            << ",\"a\":" << (int)op.a << ",\"b\":" << (int)op.b << ",\"gslot\":" << op.gslot << "}";
+        }
+        o << "]}";
       }
-      o << "]}";
+      o << (dir == 0 ? "],\"layouts\":[" : "],\"bwd_layouts\":[");
+      if (D.k > 0)
+        for (int i = 0; i <= D.n_phases; i++) {
+          const DevLayout& L = s.layouts[D.lay0 + i];
+          o << (i ? "," : "") << "[";
+          for (int j = 0; j < D.k; j++) o << (j ? "," : "") << (int)L.m[j];
+          o << "]";
+        }
+      o << "]";
     }
-    o << "],\"layouts\":[";
-    if (d.k > 0)
-      for (int i = 0; i <= d.n_phases; i++) {
-        const DevLayout& L = s.layouts[d.lay0 + i];
-        o << (i ? "," : "") << "[";
-        for (int j = 0; j < d.k; j++) o << (j ? "," : "") << (int)L.m[j];
-        o << "]";
-      }
-    o << "]}";
+    o << "}";
   }
   o << "]}";
   return o.str();

@@ -18,13 +18,14 @@ struct Gate {
 };
 
 struct PassPlan {
-  DevPass dev{};
+  DevPass dev{};                     // forward: register phases with the forward register count
+  DevPass devb{};                    // backward: same tile, phases for the backward register count
   std::vector<int> local_qubits;     // qubits held in the tile (by tile bit order)
   std::vector<int> gates;            // gate indices in execution order
 };
 
 struct Schedule {
-  int n = 0, k = 0, R = 0, c = 0, dtype = 0, mode = 0;
+  int n = 0, k = 0, R = 0, Rb = 0, c = 0, dtype = 0, mode = 0;
   int n_params = 0, n_inputs = 0;
   std::vector<Gate> gates;
   std::vector<PassPlan> passes;
@@ -43,7 +44,7 @@ int validate_gates(const qsim_gate* g, int n_gates, int n, std::vector<Gate>& ou
                    int& n_inputs, std::string& err);
 
 // Build the full schedule. R is the register bits per phase (<= kMaxR).
-int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& o, int R_fwd,
+int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& o, int R_fwd, int R_bwd,
                    Schedule& s, std::string& err);
 
 std::string describe_schedule(const Schedule& s);

@@ -45,10 +45,11 @@ __global__ void coef_kernel(CoefArgs a) {
     }
   }
   reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)fs;
-  // backward: ops undone in reverse execution order; gm = (product of inverse scales so far)^2
+  // backward: ops undone in reverse order of the backward op list; gm = (product of inverse scales so far)^2
   double bs = 1.0;
-  for (int e = e1 - 1; e >= e0; e--) {
-    const int g = a.exec_gates[e];
+  const int b0 = a.exec_begin_b[p], b1 = a.exec_begin_b[p + 1];
+  for (int e = b1 - 1; e >= b0; e--) {
+    const int g = a.exec_gates_b[e];
     const int ty = a.gate_type[g];
     if (ty <= QSIM_RZ) {
       const int64_t gi = (int64_t)g * a.B + b;

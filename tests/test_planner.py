@@ -72,45 +72,50 @@ def test_schedule_invariants(q, name, gates, n, kw):
         assert ps["L"][:c] == list(range(c)), "low index bits must be local (coalescing)"
         for g in ps["gates"]:
             assert set(gate_qubits(gates[g])) <= set(local)
-        # phases: same gates, order per wire preserved, register bits hold the targets that need them
-        ph_order = [op["gate"] for ph in ps["phases"] for op in ph["ops"]]
-        assert sorted(ph_order) == sorted(ps["gates"])
-        last_in_pass = {}
-        ppos = {g: i for i, g in enumerate(ph_order)}
-        for g in sorted(ps["gates"]):
-            for w in gate_qubits(gates[g]):
-                if w in last_in_pass:
-                    assert ppos[last_in_pass[w]] < ppos[g]
-                last_in_pass[w] = g
-        tb_of_q = {q_: j for j, q_ in enumerate(local)}
-        for ph in ps["phases"]:
-            rb, tb = ph["rbits"], ph["tbits"]
-            assert rb[0] == 0 and len(rb) == R and sorted(rb + tb) == list(range(k))
-            for op in ph["ops"]:
-                g = gates[op["gate"]]
-                t = tb_of_q[g[1][0]]
-                kind = op["kind"]
-                if kind in ("ry", "rx", "h", "x", "rz", "cx", "cx_t", "cz", "cz_t"):
-                    assert rb[op["a"]] == t or (kind in ("cz", "cz_t") and rb[op["a"]] == tb_of_q[g[2][0]])
-                if kind == "rz_t":
-                    assert op["a"] == t and t in tb
-                if kind == "cx":
-                    assert rb[op["b"]] == tb_of_q[g[2][0]]
-                if kind == "cx_t":
-                    assert op["b"] == tb_of_q[g[2][0]] and op["b"] in tb
-        # layouts are bijections of the tile
-        for m in ps["layouts"]:
-            e = np.arange(1 << k)
-            s = e.copy()
-            for j in range(k):
-                s ^= np.where((e >> j) & 1, m[j], 0)
-            assert len(np.unique(s)) == 1 << k
-            pair_ok = (s[0::2] ^ 1) == s[1::2]
-            assert pair_ok.all(), "neighbouring amplitudes must stay in adjacent words"
-        # gradient slots: one per rotation, dense
-        slots = sorted(op["gslot"] for ph in ps["phases"] for op in ph["ops"] if op["gslot"] >= 0)
+        for ph_key, lay_key, RR in (("phases", "layouts", R), ("bwd_phases", "bwd_layouts", d["Rb"])):
+            check_phases(gates, ps, ps[ph_key], ps[lay_key], k, RR, local)
+        # gradient slots (backward ops): one per rotation, dense
+        slots = sorted(op["gslot"] for ph in ps["bwd_phases"] for op in ph["ops"] if op["gslot"] >= 0)
         assert slots == list(range(ps["n_gslots"]))
         assert ps["n_gslots"] == sum(1 for g in ps["gates"] if gates[g][0] in (W.RX, W.RY, W.RZ))
+
+
+def check_phases(gates, ps, phases, layouts, k, R, local):
+    # phases: same gates, order per wire preserved, register bits hold the targets that need them
+    ph_order = [op["gate"] for ph in phases for op in ph["ops"]]
+    assert sorted(ph_order) == sorted(ps["gates"])
+    last_in_pass = {}
+    ppos = {g: i for i, g in enumerate(ph_order)}
+    for g in sorted(ps["gates"]):
+        for w in gate_qubits(gates[g]):
+            if w in last_in_pass:
+                assert ppos[last_in_pass[w]] < ppos[g]
+            last_in_pass[w] = g
+    tb_of_q = {q_: j for j, q_ in enumerate(local)}
+    for ph in phases:
+        rb, tb = ph["rbits"], ph["tbits"]
+        assert rb[0] == 0 and len(rb) == R and sorted(rb + tb) == list(range(k))
+        for op in ph["ops"]:
+            g = gates[op["gate"]]
+            t = tb_of_q[g[1][0]]
+            kind = op["kind"]
+            if kind in ("ry", "rx", "h", "x", "rz", "cx", "cx_t", "cz", "cz_t"):
+                assert rb[op["a"]] == t or (kind in ("cz", "cz_t") and rb[op["a"]] == tb_of_q[g[2][0]])
+            if kind == "rz_t":
+                assert op["a"] == t and t in tb
+            if kind == "cx":
+                assert rb[op["b"]] == tb_of_q[g[2][0]]
+            if kind == "cx_t":
+                assert op["b"] == tb_of_q[g[2][0]] and op["b"] in tb
+    # layouts are bijections of the tile
+    for m in layouts:
+        e = np.arange(1 << k)
+        s = e.copy()
+        for j in range(k):
+            s ^= np.where((e >> j) & 1, m[j], 0)
+        assert len(np.unique(s)) == 1 << k
+        pair_ok = (s[0::2] ^ 1) == s[1::2]
+        assert pair_ok.all(), "neighbouring amplitudes must stay in adjacent words"
 
 
 @pytest.mark.parametrize("n,kw", [(6, {"k": 4, "contiguous_bits": 2}), (10, {"k": 6}), (14, {"k": 9}),
