@@ -113,6 +113,8 @@ class Plan:
             int(init.shape[0]) if init is not None else 1)
         dev = (params if params is not None and params.numel() else inputs).device if (
             params is not None or inputs is not None) else torch.device("cuda")
+        self._widths = (params.shape[0] if params is not None else self.n_params,
+                        inputs.shape[1] if inputs is not None and inputs.dim() == 2 else self.n_inputs)
         params = self._prep(params, (self.n_params,))
         inputs = self._prep(inputs, (B, self.n_inputs))
         if init is not None:
@@ -134,12 +136,18 @@ class Plan:
         _, _, states, B = self._saved
         grad_z = grad_z.to(torch.float64).contiguous()
         assert grad_z.shape == (B, self.n)
+        wp, wi = getattr(self, "_widths", (self.n_params, self.n_inputs))
         if dparams is None:
-            dparams = torch.empty((self.n_params,), dtype=torch.float64, device=states.device)
+            dparams = torch.zeros((wp,), dtype=torch.float64, device=states.device)
         if dinputs is None:
-            dinputs = torch.empty((B, self.n_inputs), dtype=torch.float64, device=states.device)
-        _lib.check(_lib.lib().qsim_backward(self._h, _ptr(grad_z), _ptr(dparams) if self.n_params else None,
-                                            _ptr(dinputs) if self.n_inputs else None, _stream(stream)))
+            dinputs = torch.zeros((B, wi), dtype=torch.float64, device=states.device)
+        dp_c = dparams[:self.n_params]
+        di_c = dinputs if wi == self.n_inputs else torch.empty((B, self.n_inputs), dtype=torch.float64,
+                                                                    device=states.device)
+        _lib.check(_lib.lib().qsim_backward(self._h, _ptr(grad_z), _ptr(dp_c) if self.n_params else None,
+                                            _ptr(di_c) if self.n_inputs else None, _stream(stream)))
+        if di_c is not dinputs:
+            dinputs[:, :self.n_inputs] = di_c
         return dparams, dinputs
 
     def set_profiling(self, depth=1):
@@ -160,10 +168,13 @@ class Plan:
         return _lib.lib().qsim_sync_status(self._h)
 
     def _prep(self, t, shape):
+        """Cast to the plan's real dtype; extra trailing parameters / input columns are ignored."""
         if t is None or (shape[-1] == 0):
             return None
         if t.dtype != self.rdtype:
             t = t.to(self.rdtype)
+        if t.shape[-1] > shape[-1]:
+            t = t[..., :shape[-1]]
         t = t.contiguous()
         assert tuple(t.shape) == tuple(shape), (t.shape, shape)
         return t
