@@ -106,6 +106,13 @@ int qsim_plan_info_get(qsim_plan_t plan, qsim_plan_info* info);
  * *needed. */
 int qsim_plan_describe(qsim_plan_t plan, char* h_buf, size_t cap, size_t* needed);
 
+/* The fused pass kernels of a plan are specialised per pass structure and compiled with NVRTC for
+ * sm_103a the first time a plan is used (compiled binaries are cached on disk, keyed by the source).
+ * qsim_plan_kernel_source returns that program text (same buffer convention as qsim_plan_describe);
+ * qsim_plan_compile_kernels compiles it (or finds it in the cache) without touching a GPU. */
+int qsim_plan_kernel_source(qsim_plan_t plan, char* h_buf, size_t cap, size_t* needed);
+int qsim_plan_compile_kernels(qsim_plan_t plan);
+
 /* Physical amplitude indices (within one sample) of the 2^k elements of tile `tile` of pass
  * `pass`, in tile order (tile bit j <-> physical bit L_j): the gather/scatter map of that pass.
  * h_out must hold 2^k int64 values. Host only. */

@@ -99,6 +99,19 @@ class Plan:
         _lib.check(L.qsim_plan_describe(self._h, buf, need.value, ctypes.byref(need)))
         return json.loads(buf.value.decode())
 
+    def kernel_source(self):
+        """NVRTC program text of the plan's specialised pass kernels."""
+        need = ctypes.c_size_t()
+        L = _lib.lib()
+        _lib.check(L.qsim_plan_kernel_source(self._h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _lib.check(L.qsim_plan_kernel_source(self._h, buf, need.value, ctypes.byref(need)))
+        return buf.value.decode()
+
+    def compile_kernels(self):
+        """Compile the specialised kernels (host only; fills the on-disk cache)."""
+        _lib.check(_lib.lib().qsim_plan_compile_kernels(self._h))
+
     def tile_index_map(self, pass_index, tile):
         k = self.describe()["k"]
         out = np.zeros(1 << k, dtype=np.int64)

@@ -53,6 +53,9 @@ SIGNATURES = {
     "qsim_plan_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(QsimPlanInfo)]),
     "qsim_plan_describe": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_size_t)]),
+    "qsim_plan_kernel_source": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_size_t,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "qsim_plan_compile_kernels": (ctypes.c_int, [ctypes.c_void_p]),
     "qsim_tile_index_map": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
                                            ctypes.POINTER(ctypes.c_int64)]),
     "qsim_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,

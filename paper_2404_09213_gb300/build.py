@@ -35,8 +35,7 @@ def _compile(src: str, nvcc: str, extra) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     cmd = [nvcc, *ARCH, *COMMON, *extra, "-c", src, "-o", obj]
     if src.endswith(".cpp"):
-        cmd = [nvcc, *COMMON, *extra, "-x", "cu", "-c", src, "-o", obj] if False else \
-              [nvcc, *COMMON, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *COMMON, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"compile failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
@@ -52,16 +51,29 @@ def _stale(srcs) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
+def _embed_jit_source():
+    """jit_device.cuh as a C++ raw string, compiled into the library for NVRTC."""
+    src = open(os.path.join(CSRC, "jit_device.cuh")).read()
+    assert ")QSIMJIT\"" not in src
+    text = "static const char kJitDeviceSource[] = R\"QSIMJIT(" + src + ")QSIMJIT\";\n"
+    path = os.path.join(BUILD, "jit_embed.inc")
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     srcs = sources()
     if not force and not _stale(srcs):
         return OUT
     os.makedirs(BUILD, exist_ok=True)
+    _embed_jit_source()
+    extra = list(extra) + ["-I", BUILD]
     nvcc = _nvcc()
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, nvcc, list(extra)), srcs))
     tmp = OUT + ".tmp"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

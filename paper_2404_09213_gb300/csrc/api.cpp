@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/qsim.h"
+#include "jit.hpp"
 #include "launch.hpp"
 #include "planner.hpp"
 
@@ -41,13 +42,12 @@ struct qsim_plan_s {
   int el = 8, sc = 4;
   // device copy of the schedule
   bool uploaded = false;
-  DevPass* d_passes = nullptr;
-  DevPass* d_passes_b = nullptr;
   int32_t* d_exec_gates_b = nullptr;
   int32_t* d_exec_begin_b = nullptr;
-  DevPhase* d_phases = nullptr;
-  DevOp* d_ops = nullptr;
-  DevLayout* d_layouts = nullptr;
+  uint8_t* d_bits = nullptr;            // per pass: L[k] then nonlocal[n-k]
+  int32_t* d_op_gate = nullptr;         // per pass: forward ops' gates, then backward ops' gates (-1: none)
+  std::vector<int64_t> off_bits, off_opf, off_opb;
+  JitPlan jit;
   int32_t* d_gate_type = nullptr;
   int32_t* d_gate_param = nullptr;
   int32_t* d_exec_gates = nullptr;
@@ -136,26 +136,39 @@ struct qsim_plan_s {
   void free_all() {
     free_ws();
     destroy_events();
-    void* ptrs[] = {d_passes, d_passes_b, d_phases, d_ops, d_layouts, d_gate_type, d_gate_param, d_exec_gates,
-                    d_exec_begin, d_exec_gates_b, d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ,
-                    d_i_ptr, d_i_occ, d_Lnl_last};
+    void* ptrs[] = {d_bits, d_op_gate, d_gate_type, d_gate_param, d_exec_gates, d_exec_begin, d_exec_gates_b,
+                    d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Lnl_last};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    jit_free(jit);
     uploaded = false;
   }
 
   int upload_schedule() {
     if (uploaded) return QSIM_OK;
     cudaError_t e = cudaSuccess;
-    std::vector<DevPass> passes, passes_b;
-    std::vector<int32_t> gtype, gparam, exec, exec_begin, exec_b, exec_begin_b;
+    std::vector<int32_t> gtype, gparam, exec, exec_begin, exec_b, exec_begin_b, op_gate;
+    std::vector<uint8_t> bits;
     for (auto& g : s.gates) {
       gtype.push_back(g.type);
       gparam.push_back(g.param);
     }
     for (auto& pp : s.passes) {
-      passes.push_back(pp.dev);
-      passes_b.push_back(pp.devb);
+      off_bits.push_back((int64_t)bits.size());
+      for (int j = 0; j < pp.dev.k; j++) bits.push_back(pp.dev.L[j]);
+      for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.nonlocal[j]);
+      bits.push_back(0);
+      off_opf.push_back((int64_t)op_gate.size());
+      for (int i = 0; i < pp.dev.n_ops; i++) {
+        const DevOp& op = s.ops[pp.dev.op0 + i];
+        op_gate.push_back(op.rot ? op.gate : -1);
+      }
+      off_opb.push_back((int64_t)op_gate.size());
+      for (int i = 0; i < pp.devb.n_ops; i++) {
+        const DevOp& op = s.ops[pp.devb.op0 + i];
+        op_gate.push_back(op.rot ? op.gate : -1);
+      }
+      op_gate.push_back(-1);
       exec_begin.push_back((int32_t)exec.size());
       exec_begin_b.push_back((int32_t)exec_b.size());
       if (s.mode == QSIM_PER_GATE) {
@@ -192,13 +205,10 @@ struct qsim_plan_s {
     }
 #define QSIM_UP(PTR, VEC) \
   if (e == cudaSuccess) e = upload(&PTR, VEC);
-    QSIM_UP(d_passes, passes)
-    QSIM_UP(d_passes_b, passes_b)
+    QSIM_UP(d_bits, bits)
+    QSIM_UP(d_op_gate, op_gate)
     QSIM_UP(d_exec_gates_b, exec_b)
     QSIM_UP(d_exec_begin_b, exec_begin_b)
-    QSIM_UP(d_phases, s.phases)
-    QSIM_UP(d_ops, s.ops)
-    QSIM_UP(d_layouts, s.layouts)
     QSIM_UP(d_gate_type, gtype)
     QSIM_UP(d_gate_param, gparam)
     QSIM_UP(d_exec_gates, exec)
@@ -213,18 +223,15 @@ struct qsim_plan_s {
 #undef QSIM_UP
     if (e != cudaSuccess) return cuda_fail(e, "uploading the plan");
     if (s.mode == QSIM_FUSED) {
-      size_t mf = 0, mb = 0;
-      for (auto& pp : s.passes) {
-        mf = std::max(mf, fwd_pass_smem(pp.dev, s.dtype, 1 << (pp.dev.k - pp.dev.R)));
-        mb = std::max(mb, bwd_pass_smem(pp.devb, s.dtype, 1 << (pp.devb.k - pp.devb.R)));
-      }
       int dev = 0, optin = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-      if ((int64_t)mf > optin || (int64_t)mb > optin)
-        return fail(QSIM_ERR_UNSUPPORTED, "tile does not fit in shared memory: lower k");
-      e = prepare_pass_kernels(s.dtype, mf, mb);
-      if (e != cudaSuccess) return cuda_fail(e, "setting kernel attributes");
+      for (auto& pp : s.passes)
+        if ((int64_t)jit_smem_bytes(pp.dev, s.dtype, false) > optin || (int64_t)jit_smem_bytes(pp.devb, s.dtype, true) > optin)
+          return fail(QSIM_ERR_UNSUPPORTED, "tile does not fit in shared memory: lower k");
+      std::string err;
+      int rc = jit_build(s, jit, err);
+      if (rc) return fail(rc, err);
     }
     uploaded = true;
     return QSIM_OK;
@@ -295,19 +302,21 @@ struct qsim_plan_s {
     return n_segments - 1;
   }
 
-  PassLaunch pass_launch(int p, const void* scale, bool bwd) const {
-    PassLaunch L{};
-    L.h_pass = bwd ? &s.passes[p].devb : &s.passes[p].dev;
-    L.d_pass = (bwd ? d_passes_b : d_passes) + p;
-    L.d_phases = d_phases;
-    L.d_ops = d_ops;
-    L.d_layouts = d_layouts;
-    L.n = s.n;
-    L.B = B;
-    L.coef = coef;
-    L.form = form;
-    L.scale = scale;
-    return L;
+  JitArgs jit_args(int p, bool bwd, const void* scale) const {
+    JitArgs a{};
+    const DevPass& d = bwd ? s.passes[p].devb : s.passes[p].dev;
+    a.coef = coef;
+    a.form = form;
+    a.op_gate = d_op_gate + (bwd ? off_opb[p] : off_opf[p]);
+    a.scale = scale;
+    a.L = d_bits + off_bits[p];
+    a.nonlocal = d_bits + off_bits[p] + d.k;
+    a.tps = d.tiles_per_sample;
+    a.gpart_offset = d.gpart_offset;
+    a.n_nonlocal = d.n_nonlocal;
+    a.n = s.n;
+    a.B = B;
+    return a;
   }
 
   PerGateArgs pg_args(int g, const void* scale) const {
@@ -407,6 +416,33 @@ int qsim_plan_describe(qsim_plan_t p, char* buf, size_t cap, size_t* needed) {
   return QSIM_OK;
 }
 
+int qsim_plan_kernel_source(qsim_plan_t p, char* buf, size_t cap, size_t* needed) {
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  std::string src;
+  if (p->s.mode == QSIM_FUSED) {
+    std::vector<std::string> fn, bn;
+    src = jit_generate(p->s, fn, bn);
+  }
+  if (needed) *needed = src.size() + 1;
+  if (buf && cap > 0) {
+    size_t m = std::min(cap - 1, src.size());
+    std::memcpy(buf, src.data(), m);
+    buf[m] = 0;
+  }
+  return QSIM_OK;
+}
+
+int qsim_plan_compile_kernels(qsim_plan_t p) {
+  if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  if (p->s.mode != QSIM_FUSED) return QSIM_OK;
+  std::string err;
+  std::map<std::string, std::string> cubins;
+  std::vector<std::string> fn, bn;
+  int rc = jit_compile(p->s, cubins, fn, bn, err);
+  if (rc) return fail(rc, err);
+  return QSIM_OK;
+}
+
 int qsim_tile_index_map(qsim_plan_t p, int32_t pass, int64_t tile, int64_t* out) {
   if (!p || !out) return fail(QSIM_ERR_ARG, "NULL argument");
   if (p->s.mode != QSIM_FUSED) return fail(QSIM_ERR_ARG, "index maps exist only for fused plans");
@@ -481,9 +517,12 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
       const void* in;
       if (q == p->seg_begin[seg]) in = (seg == 0) ? d_init : p->ckpt[seg - 1];
       else in = out;
-      double* zp = (q == P_ - 1) ? p->zpart : nullptr;
+      JitArgs ja = p->jit_args(q, false, sf + (size_t)q * batch * p->sc);
+      ja.in = in;
+      ja.out = out;
+      ja.zpart = (q == P_ - 1) ? p->zpart : nullptr;
       if (p->profiling) cudaEventRecord(p->ev_f0[p->fslot(q)], st);
-      e = launch_fwd_pass(p->pass_launch(q, sf + (size_t)q * batch * p->sc, false), s.dtype, in, out, zp, st);
+      e = jit_launch(p->jit.fwd[q], s.passes[q].dev.tiles_per_sample * batch, ja, st);
       if (e != cudaSuccess) return cuda_fail(e, "fused forward pass");
       if (p->profiling) cudaEventRecord(p->ev_f1[p->fslot(q)], st);
     }
@@ -527,9 +566,15 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
       const void* lin = (q == P_ - 1) ? nullptr : p->Lam;
       void* pout = q == 0 ? nullptr : p->W;
       void* lout = q == 0 ? nullptr : p->Lam;
+      JitArgs ja = p->jit_args(q, true, sbk + (size_t)q * B * p->sc);
+      ja.in = pin;
+      ja.out = pout;
+      ja.lam_in = lin;
+      ja.lam_out = lout;
+      ja.grad_out = d_grad_out;
+      ja.gpart = p->gpart;
       if (p->profiling) cudaEventRecord(p->ev_b0[p->bslot(q)], st);
-      e = launch_bwd_pass(p->pass_launch(q, sbk + (size_t)q * B * p->sc, true), s.dtype, pin, pout, lin, lout, d_grad_out,
-                          p->gpart, st);
+      e = jit_launch(p->jit.bwd[q], s.passes[q].devb.tiles_per_sample * B, ja, st);
       if (e != cudaSuccess) return cuda_fail(e, "fused backward pass");
       if (p->profiling) cudaEventRecord(p->ev_b1[p->bslot(q)], st);
     }

@@ -1,0 +1,467 @@
+// Specialised fused-pass kernels: source generation per pass structure, NVRTC compilation
+// (libnvrtc opened at run time), an on-disk cubin cache and loading through cudaLibrary.
+//
+// Every fused pass is a straight-line program of register phases. Its structure (tile size, register
+// bits of each phase, op kinds and operand bits, shared-memory layouts) becomes compile-time code in a
+// generated "Spec" struct; passes with the same structure share one kernel. Per-pass data that does not
+// change the code (physical bit positions, the gate of every op) is passed at run time.
+#include "jit.hpp"
+
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <algorithm>
+#include <map>
+#include <atomic>
+#include <mutex>
+#include <thread>
+#include <sstream>
+
+#include "launch.hpp"
+
+namespace qsim {
+
+#include "jit_embed.inc"   // const char* kJitDeviceSource (jit_device.cuh as text)
+
+// ------------------------------------------------------------------ NVRTC via dlopen
+namespace {
+typedef int nvrtcResult_t;
+typedef struct _nvrtcProgram* nvrtcProgram_t;
+struct Nvrtc {
+  void* h = nullptr;
+  nvrtcResult_t (*create)(nvrtcProgram_t*, const char*, const char*, int, const char* const*, const char* const*) = nullptr;
+  nvrtcResult_t (*compile)(nvrtcProgram_t, int, const char* const*) = nullptr;
+  nvrtcResult_t (*log_size)(nvrtcProgram_t, size_t*) = nullptr;
+  nvrtcResult_t (*log)(nvrtcProgram_t, char*) = nullptr;
+  nvrtcResult_t (*cubin_size)(nvrtcProgram_t, size_t*) = nullptr;
+  nvrtcResult_t (*cubin)(nvrtcProgram_t, char*) = nullptr;
+  nvrtcResult_t (*destroy)(nvrtcProgram_t*) = nullptr;
+  nvrtcResult_t (*version)(int*, int*) = nullptr;
+  std::string error;
+};
+
+Nvrtc& nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    std::vector<std::string> cand = {"libnvrtc.so.13", "libnvrtc.so"};
+    if (const char* ch = getenv("CUDA_HOME")) cand.push_back(std::string(ch) + "/lib64/libnvrtc.so.13");
+    cand.push_back("/usr/local/cuda/lib64/libnvrtc.so.13");
+    cand.push_back("/usr/local/cuda/lib64/libnvrtc.so");
+    for (auto& c : cand) {
+      n.h = dlopen(c.c_str(), RTLD_NOW | RTLD_LOCAL);
+      if (n.h) break;
+    }
+    if (!n.h) {
+      n.error = "cannot load libnvrtc (set CUDA_HOME): " + std::string(dlerror() ? dlerror() : "");
+      return;
+    }
+#define QSIM_SYM(F, NAME)                                                       \
+  n.F = reinterpret_cast<decltype(n.F)>(dlsym(n.h, NAME));                     \
+  if (!n.F) {                                                                  \
+    n.error = std::string("libnvrtc lacks ") + NAME;                           \
+    n.h = nullptr;                                                             \
+    return;                                                                    \
+  }
+    QSIM_SYM(create, "nvrtcCreateProgram")
+    QSIM_SYM(compile, "nvrtcCompileProgram")
+    QSIM_SYM(log_size, "nvrtcGetProgramLogSize")
+    QSIM_SYM(log, "nvrtcGetProgramLog")
+    QSIM_SYM(cubin_size, "nvrtcGetCUBINSize")
+    QSIM_SYM(cubin, "nvrtcGetCUBIN")
+    QSIM_SYM(destroy, "nvrtcDestroyProgram")
+    QSIM_SYM(version, "nvrtcVersion")
+#undef QSIM_SYM
+  });
+  return n;
+}
+
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ULL) {
+  for (unsigned char c : s) {
+    h ^= c;
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+
+std::string hex64(uint64_t v) {
+  char b[17];
+  snprintf(b, sizeof b, "%016llx", (unsigned long long)v);
+  return b;
+}
+
+std::string cache_dir() {
+  if (const char* e = getenv("QSIM_JIT_CACHE")) return e;
+  Dl_info info;
+  if (dladdr(reinterpret_cast<void*>(&cache_dir), &info) && info.dli_fname) {
+    std::string p = info.dli_fname;
+    size_t s = p.rfind('/');
+    if (s != std::string::npos) return p.substr(0, s) + "/_jit_cache";
+  }
+  return "/tmp/qsim_jit_cache";
+}
+
+bool read_file(const std::string& path, std::string& out) {
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return false;
+  std::ostringstream o;
+  o << f.rdbuf();
+  out = o.str();
+  return true;
+}
+
+void write_file_atomic(const std::string& dir, const std::string& path, const std::string& data) {
+  mkdir(dir.c_str(), 0755);
+  std::string tmp = path + ".tmp." + std::to_string(getpid());
+  {
+    std::ofstream f(tmp, std::ios::binary);
+    if (!f) return;
+    f.write(data.data(), (std::streamsize)data.size());
+  }
+  rename(tmp.c_str(), path.c_str());
+}
+
+// shared-memory layout function of a DevLayout as C++ source
+std::string lay_fn(const std::string& name, const DevLayout& L, int k) {
+  std::ostringstream o;
+  o << "  static __device__ __forceinline__ qj::u32 " << name << "(qj::u32 e) { return e";
+  for (int j = 0; j < k; j++)
+    if (L.m[j]) o << " ^ (((e >> " << j << ") & 1u) ? " << (unsigned)L.m[j] << "u : 0u)";
+  o << "; }\n";
+  return o.str();
+}
+
+uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
+  uint32_t s = e;
+  for (int j = 0; j < k; j++)
+    if ((e >> j) & 1u) s ^= L.m[j];
+  return s;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ generation
+static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) {
+  const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
+  std::ostringstream o;
+  o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
+  o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
+  for (int i = 0; i <= d.n_phases; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
+  o << "  static __device__ __forceinline__ qj::u32 lay_first(qj::u32 e) { return L0(e); }\n";
+  o << "  static __device__ __forceinline__ qj::u32 lay_last(qj::u32 e) { return L" << d.n_phases << "(e); }\n";
+  if (!bwd) {
+    o << "  template <typename T> static __device__ __forceinline__ void fwd_phases(void* tile, const T* cf, "
+         "const qj::u8* fm, qj::u32 tid) {\n";
+    o << "    T re[" << N << "], im[" << N << "];\n";
+  } else {
+    o << "  template <typename T, typename A> static __device__ __forceinline__ void bwd_phases(void* tp, void* tl, "
+         "const T* cf, const qj::u8* fm, A* red, qj::u32 tid) {\n";
+    o << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n";
+    o << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n";
+    o << "    (void)lane; (void)warp;\n";
+  }
+  for (int step = 0; step < d.n_phases; step++) {
+    const int ph = bwd ? d.n_phases - 1 - step : step;
+    const DevPhase& P = s.phases[d.phase0 + ph];
+    const int lin = bwd ? ph + 1 : ph, lout = bwd ? ph : ph + 1;
+    const DevLayout& Li = s.layouts[d.lay0 + lin];
+    const DevLayout& Lo = s.layouts[d.lay0 + lout];
+    o << "    { // phase " << ph << "\n";
+    o << "      const qj::u32 tb = 0u";
+    for (int j = 0; j < P.n_tbits; j++) o << " | (((tid >> " << j << ") & 1u) << " << (int)P.tbit[j] << ")";
+    o << ";\n      (void)tb;\n";
+    o << "      const qj::u32 si = L" << lin << "(tb), so = L" << lout << "(tb);\n";
+    auto dep = [&](int i) {
+      uint32_t e = 0;
+      for (int r = 0; r < R; r++)
+        if ((i >> r) & 1) e |= 1u << P.rbit[r];
+      return e;
+    };
+    for (int i = 0; i < N; i += 2) {
+      const uint32_t c = lay_eval(Li, K, dep(i));
+      if (!bwd) {
+        o << "      qj::ldp(tile, si ^ " << c << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+      } else {
+        o << "      qj::ldp(tp, si ^ " << c << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
+        o << "      qj::ldp(tl, si ^ " << c << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+      }
+    }
+    std::vector<int> order;
+    for (int oi = P.op_begin; oi < P.op_end; oi++) order.push_back(oi);
+    if (bwd) std::reverse(order.begin(), order.end());
+    for (int oi : order) {
+      const DevOp& op = s.ops[oi];
+      const int li = oi - d.op0;
+      const int SA = 1 << op.a, SB = 1 << op.b;
+      std::string C = "cf[" + std::to_string(li) + "], fm[" + std::to_string(li) + "]";
+      std::string call;
+      std::ostringstream g;   // gradient expression (backward, rotations)
+      switch (op.kind) {
+        case K_RY_R:
+          call = "qj::ry<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
+          g << "qj::g_ry<" << N << ", " << SA << ">(pr, pq, lr, lq)";
+          break;
+        case K_RX_R:
+          call = "qj::rx<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
+          g << "qj::g_rx<" << N << ", " << SA << ">(pr, pq, lr, lq)";
+          break;
+        case K_RZ_R:
+          call = "qj::rz<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
+          g << "qj::g_rz<" << N << ", " << SA << ">(pr, pq, lr, lq)";
+          break;
+        case K_H_R:
+          call = "qj::hd<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I);";
+          break;
+        case K_X_R:
+          call = "qj::swp<" + std::to_string(N) + ", " + std::to_string(SA) + ", 0>(%R, %I);";
+          break;
+        case K_RZ_T:
+          call = "qj::rz_t<" + std::to_string(N) + ">(%R, %I, " + C + ", ((tb >> " + std::to_string(op.a) +
+                 ") & 1u) ? T(-1) : T(1));";
+          g << "((((tb >> " << (int)op.a << ") & 1u) ? A(-1) : A(1)) * qj::g_im<" << N << ">(pr, pq, lr, lq))";
+          break;
+        case K_CNOT_RR:
+          call = "qj::swp<" + std::to_string(N) + ", " + std::to_string(SA) + ", " + std::to_string(SB) + ">(%R, %I);";
+          break;
+        case K_CNOT_RT:
+          call = "qj::cnot_t<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, ((tb >> " +
+                 std::to_string(op.b) + ") & 1u) != 0u);";
+          break;
+        case K_CZ_RR:
+          call = "qj::cz<" + std::to_string(N) + ", " + std::to_string(SA) + ", " + std::to_string(SB) + ">(%R, %I);";
+          break;
+        case K_CZ_RT:
+          call = "qj::cz_t<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, ((tb >> " +
+                 std::to_string(op.b) + ") & 1u) != 0u);";
+          break;
+        case K_CZ_TT:
+          call = "if (((tb >> " + std::to_string(op.a) + ") & 1u) && ((tb >> " + std::to_string(op.b) +
+                 ") & 1u)) qj::scal<" + std::to_string(N) + ">(%R, %I, T(-1));";
+          break;
+      }
+      auto inst = [&](const char* rr, const char* ii) {
+        std::string c2 = call;
+        size_t p;
+        while ((p = c2.find("%R")) != std::string::npos) c2.replace(p, 2, rr);
+        while ((p = c2.find("%I")) != std::string::npos) c2.replace(p, 2, ii);
+        return c2;
+      };
+      if (!bwd) {
+        o << "      " << inst("re", "im") << "\n";
+      } else {
+        if (op.rot) {
+          o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ">(g); if (lane == 0u) red[warp * "
+            << (d.n_gslots > 0 ? d.n_gslots : 1) << " + " << op.gslot << "] = g; }\n";
+        }
+        o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
+      }
+    }
+    o << "      __syncthreads();\n";
+    for (int i = 0; i < N; i += 2) {
+      const uint32_t c = lay_eval(Lo, K, dep(i));
+      if (!bwd) {
+        o << "      qj::stp(tile, so ^ " << c << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+      } else {
+        o << "      qj::stp(tp, so ^ " << c << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
+        o << "      qj::stp(tl, so ^ " << c << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+      }
+    }
+    o << "      __syncthreads();\n    }\n";
+  }
+  o << "  }\n";
+  return o.str();
+}
+
+// Register bits per phase: complex64 forward 5 (32 amplitudes per thread), backward 4 (psi and
+// lambda); complex128 one less each. Threads per CTA = 2^(k - R) <= 256, so k <= 12 (11 for c128).
+int fwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 4 : 5; return k < r ? k : r; }
+int bwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 3 : 4; return k < r ? k : r; }
+int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
+
+size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd) {
+  const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
+  const size_t nops = d.n_ops > 0 ? d.n_ops : 1;
+  if (!bwd) return ((tile + nops * sc + d.n_ops) + 15) & ~(size_t)15;
+  const int nthr = 1 << (d.k - d.R);
+  const size_t nw = (nthr + 31) / 32, ng = d.n_gslots > 0 ? d.n_gslots : 1;
+  size_t red = nw * ng + (nw * ng) % 2 + 2;
+  return ((2 * tile + red * sc + (d.k + 2) * 8 + nops * sc + d.n_ops) + 15) & ~(size_t)15;
+}
+
+// One NVRTC unit per distinct kernel: name -> source (device header + Spec + entry point).
+static void jit_units(const Schedule& s, std::vector<std::string>& fnames, std::vector<std::string>& bnames,
+                      std::map<std::string, std::string>& units) {
+  const char* T = s.dtype == QSIM_C128 ? "double" : "float";
+  fnames.clear();
+  bnames.clear();
+  for (auto& pp : s.passes) {
+    for (int dir = 0; dir < 2; dir++) {
+      const DevPass& d = dir == 0 ? pp.dev : pp.devb;
+      const bool bwd = dir == 1;
+      const int K = d.k, R = d.R, NTHR = 1 << (K - R);
+      std::string body = gen_spec_body(s, d, bwd);
+      std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" + body;
+      std::string name = std::string(bwd ? "qb_" : "qf_") + hex64(fnv1a(key));
+      if (!units.count(name)) {
+        std::ostringstream u;
+        u << "struct S_" << name << " {\n" << body << "};\n";
+        u << "extern \"C\" __global__ void __launch_bounds__(" << NTHR << ") " << name
+          << "(const qj::Args a) { qj::" << (bwd ? "bwd_pass" : "fwd_pass") << "<" << T << ", " << K << ", " << R
+          << ", " << NTHR << ", S_" << name << ">(a); }\n";
+        units[name] = u.str();
+      }
+      (bwd ? bnames : fnames).push_back(name);
+    }
+  }
+}
+
+std::string jit_generate(const Schedule& s, std::vector<std::string>& fnames, std::vector<std::string>& bnames) {
+  std::map<std::string, std::string> units;
+  jit_units(s, fnames, bnames, units);
+  std::ostringstream prog;
+  prog << kJitDeviceSource << "\n";
+  for (auto& kv : units) prog << "// ---- " << kv.first << "\n" << kv.second;
+  return prog.str();
+}
+
+static int nvrtc_compile_unit(const std::string& src, std::string& cubin, std::string& err) {
+  Nvrtc& nv = nvrtc();
+  if (!nv.h) {
+    err = nv.error;
+    return QSIM_ERR_UNSUPPORTED;
+  }
+  nvrtcProgram_t prog = nullptr;
+  if (nv.create(&prog, src.c_str(), "qsim_pass.cu", 0, nullptr, nullptr) != 0) {
+    err = "nvrtcCreateProgram failed";
+    return QSIM_ERR_UNSUPPORTED;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--fmad=true"};
+  const int rc = nv.compile(prog, 4, opts);
+  size_t ls = 0;
+  nv.log_size(prog, &ls);
+  std::string log(ls, '\0');
+  if (ls) nv.log(prog, &log[0]);
+  if (rc != 0) {
+    nv.destroy(&prog);
+    err = "NVRTC compilation of a pass kernel failed:\n" + log.substr(0, 6000);
+    return QSIM_ERR_UNSUPPORTED;
+  }
+  size_t cs = 0;
+  nv.cubin_size(prog, &cs);
+  cubin.resize(cs);
+  nv.cubin(prog, &cubin[0]);
+  nv.destroy(&prog);
+  return QSIM_OK;
+}
+
+int jit_compile(const Schedule& s, std::map<std::string, std::string>& cubins, std::vector<std::string>& fn,
+                std::vector<std::string>& bn, std::string& err) {
+  std::map<std::string, std::string> units;
+  jit_units(s, fn, bn, units);
+  Nvrtc& nv = nvrtc();
+  int maj = 0, min = 0;
+  if (nv.h) nv.version(&maj, &min);
+  const std::string tag = "_sm103a_" + std::to_string(maj) + "." + std::to_string(min) + "_" +
+                          hex64(fnv1a(kJitDeviceSource)).substr(0, 8);
+  const std::string dir = cache_dir();
+  std::vector<std::string> todo;
+  for (auto& kv : units) {
+    std::string bin;
+    if (read_file(dir + "/" + kv.first + tag + ".cubin", bin)) cubins[kv.first] = bin;
+    else todo.push_back(kv.first);
+  }
+  if (todo.empty()) return QSIM_OK;
+  std::vector<std::string> bins(todo.size()), errs(todo.size());
+  std::vector<int> rcs(todo.size(), 0);
+  std::atomic<size_t> next{0};
+  auto worker = [&]() {
+    for (size_t i = next++; i < todo.size(); i = next++) {
+      const std::string src = std::string(kJitDeviceSource) + "\n" + units[todo[i]];
+      rcs[i] = nvrtc_compile_unit(src, bins[i], errs[i]);
+    }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 4;
+  nt = std::min<unsigned>(nt, (unsigned)todo.size());
+  std::vector<std::thread> pool;
+  for (unsigned t = 0; t < nt; t++) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  for (size_t i = 0; i < todo.size(); i++) {
+    if (rcs[i]) {
+      err = errs[i];
+      return rcs[i];
+    }
+    cubins[todo[i]] = bins[i];
+    write_file_atomic(dir, dir + "/" + todo[i] + tag + ".cubin", bins[i]);
+  }
+  return QSIM_OK;
+}
+
+int jit_build(const Schedule& s, JitPlan& jp, std::string& err) {
+  std::vector<std::string> fn, bn;
+  std::map<std::string, std::string> cubins;
+  int rc = jit_compile(s, cubins, fn, bn, err);
+  if (rc) return rc;
+  std::map<std::string, cudaKernel_t> loaded;
+  for (auto& kv : cubins) {
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, kv.second.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) {
+      err = std::string("loading the pass kernels: ") + cudaGetErrorString(e);
+      return QSIM_ERR_CUDA;
+    }
+    jp.libs.push_back(lib);
+    cudaKernel_t k = nullptr;
+    e = cudaLibraryGetKernel(&k, lib, kv.first.c_str());
+    if (e != cudaSuccess) {
+      err = "kernel " + kv.first + " missing: " + cudaGetErrorString(e);
+      return QSIM_ERR_CUDA;
+    }
+    loaded[kv.first] = k;
+  }
+  jp.fwd.resize(fn.size());
+  jp.bwd.resize(bn.size());
+  for (int dir = 0; dir < 2; dir++) {
+    auto& names = dir == 0 ? fn : bn;
+    auto& ks = dir == 0 ? jp.fwd : jp.bwd;
+    for (size_t p = 0; p < names.size(); p++) {
+      const DevPass& d = dir == 0 ? s.passes[p].dev : s.passes[p].devb;
+      cudaKernel_t k = loaded[names[p]];
+      ks[p].fn = reinterpret_cast<void*>(k);
+      ks[p].smem = jit_smem_bytes(d, s.dtype, dir == 1);
+      ks[p].nthr = 1 << (d.k - d.R);
+      if (ks[p].smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks[p].smem);
+        if (e != cudaSuccess) {
+          err = std::string("shared memory attribute: ") + cudaGetErrorString(e);
+          return QSIM_ERR_CUDA;
+        }
+      }
+    }
+  }
+  return QSIM_OK;
+}
+
+void jit_free(JitPlan& jp) {
+  for (auto l : jp.libs) cudaLibraryUnload(l);
+  jp.libs.clear();
+  jp.fwd.clear();
+  jp.bwd.clear();
+}
+
+cudaError_t jit_launch(const JitKernel& k, int64_t blocks, const JitArgs& a, cudaStream_t st) {
+  if (blocks <= 0 || blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  void* args[] = {const_cast<JitArgs*>(&a)};
+  cudaError_t e = cudaLaunchKernel(k.fn, dim3((unsigned)blocks), dim3((unsigned)k.nthr), args, k.smem, st);
+  if (e == cudaSuccess) g_kernel_launches++;
+  return e;
+}
+
+}  // namespace qsim

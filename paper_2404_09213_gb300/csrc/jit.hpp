@@ -1,0 +1,59 @@
+// Specialised fused-pass kernels compiled at plan time (see jit.cpp).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "planner.hpp"
+
+namespace qsim {
+
+// Host mirror of qj::Args in jit_device.cuh (same field order and types).
+struct JitArgs {
+  const void* in;
+  void* out;
+  const void* lam_in;
+  void* lam_out;
+  const void* coef;
+  const uint8_t* form;
+  const int* op_gate;
+  const void* scale;
+  double* zpart;
+  double* gpart;
+  const double* grad_out;
+  const uint8_t* L;
+  const uint8_t* nonlocal;
+  int64_t tps;
+  int64_t gpart_offset;
+  int n_nonlocal, n, B, pad;
+};
+
+struct JitKernel {
+  void* fn = nullptr;   // cudaKernel_t
+  size_t smem = 0;
+  int nthr = 0;
+};
+
+struct JitPlan {
+  std::vector<JitKernel> fwd, bwd;   // one per pass
+  std::vector<cudaLibrary_t> libs;   // one per distinct kernel
+};
+
+int fwd_R_for(int k, int dtype);
+int bwd_R_for(int k, int dtype);
+int max_k_for(int dtype);
+
+// Full NVRTC program text and the kernel name of every pass (forward, backward).
+std::string jit_generate(const Schedule& s, std::vector<std::string>& fwd_names, std::vector<std::string>& bwd_names);
+size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd);
+// NVRTC-compile (or fetch from the on-disk cache) the plan's kernels; host only, no CUDA calls.
+int jit_compile(const Schedule& s, std::map<std::string, std::string>& cubins, std::vector<std::string>& fwd_names,
+                std::vector<std::string>& bwd_names, std::string& err);
+int jit_build(const Schedule& s, JitPlan& jp, std::string& err);
+void jit_free(JitPlan& jp);
+cudaError_t jit_launch(const JitKernel& k, int64_t blocks, const JitArgs& a, cudaStream_t st);
+
+}  // namespace qsim

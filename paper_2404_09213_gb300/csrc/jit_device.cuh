@@ -1,0 +1,627 @@
+// Device code of the specialised fused-pass kernels. This file is compiled at plan time by NVRTC
+// together with a generated "Spec" struct per distinct pass structure (register phases, op list
+// and shared-memory layouts as compile-time constants); it includes no host or std headers.
+//
+// A CTA owns one tile: the 2^K amplitudes of one sample whose index bits outside the pass's local
+// set are fixed (the reshape to (rest, group) of the paper's Section III-B, with the group axis held
+// in shared memory). Load: 16-byte cp.async copies of runs of 2^c contiguous amplitudes. Compute:
+// register phases of 2^R amplitudes per thread; rotations use the scaled one-FMA forms
+//   RY: [[1,-t],[t,1]] / [[u,-1],[1,u]],  RX: [[1,-it],[-it,1]] / [[u,-i],[-i,u]],
+//   RZ: diag(1-it, 1+it) / diag(u-i, u+i),   t = tan(theta/2), u = cot(theta/2),
+// (the factored cos / sin is applied once per pass as the tile is stored), H as [[1,1],[1,-1]].
+// The backward reverses every op with the negated coefficient and accumulates Im<lambda|P|psi>.
+
+namespace qj {
+
+typedef unsigned int u32;
+typedef long long i64;
+typedef unsigned char u8;
+
+struct Args {
+  const void* in;        // forward: states in (nullptr -> |0...0>); backward: psi in
+  void* out;             // forward: states out; backward: psi out (nullptr -> not stored)
+  const void* lam_in;    // backward: lambda in (nullptr -> lambda = (sum_i g_i Z_i) psi)
+  void* lam_out;         // backward: lambda out
+  const void* coef;      // [G * B] scaled-rotation coefficients
+  const u8* form;        // [G * B] 0: tangent form, 1: cotangent form
+  const int* op_gate;    // [n_ops] gate index of every op of this pass (-1: no coefficient)
+  const void* scale;     // [B] this pass's scale (forward) or inverse scale (backward)
+  double* zpart;         // forward <Z> partials [(B * tps) x (K + 1)] or nullptr
+  double* gpart;         // backward gradient partials
+  const double* grad_out;   // backward: dL/d<Z> (B x n)
+  const u8* L;           // physical bit of every tile bit
+  const u8* nonlocal;    // physical bits outside the tile, ascending
+  i64 tps;               // tiles per sample
+  i64 gpart_offset;      // first gradient slot of this pass
+  int n_nonlocal, n, B, pad;
+};
+
+__device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fm(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+  const u32 sa = (u32)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// ---------------------------------------------------------------- register gates (stride S = 1 << bit)
+template <int N, int S, typename T>
+__device__ __forceinline__ void ry(T* re, T* im, T c, int f) {
+  if (f == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      if (!(i & S)) {
+        const int j = i | S;
+        const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
+        re[i] = fm(-c, br, ar); im[i] = fm(-c, bi, ai);
+        re[j] = fm(c, ar, br);  im[j] = fm(c, ai, bi);
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      if (!(i & S)) {
+        const int j = i | S;
+        const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
+        re[i] = fm(c, ar, -br); im[i] = fm(c, ai, -bi);
+        re[j] = fm(c, br, ar);  im[j] = fm(c, bi, ai);
+      }
+  }
+}
+
+template <int N, int S, typename T>
+__device__ __forceinline__ void rx(T* re, T* im, T c, int f) {
+  if (f == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      if (!(i & S)) {
+        const int j = i | S;
+        const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
+        re[i] = fm(c, bi, ar);  im[i] = fm(-c, br, ai);
+        re[j] = fm(c, ai, br);  im[j] = fm(-c, ar, bi);
+      }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++)
+      if (!(i & S)) {
+        const int j = i | S;
+        const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
+        re[i] = fm(c, ar, bi);  im[i] = fm(c, ai, -br);
+        re[j] = fm(c, br, ai);  im[j] = fm(c, bi, -ar);
+      }
+  }
+}
+
+template <int N, int S, typename T>
+__device__ __forceinline__ void rz(T* re, T* im, T c, int f) {
+  if (f == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const T cs = (i & S) ? -c : c;
+      const T r = re[i], m = im[i];
+      re[i] = fm(cs, m, r);
+      im[i] = fm(-cs, r, m);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const T r = re[i], m = im[i];
+      if (i & S) { re[i] = fm(c, r, -m); im[i] = fm(c, m, r); }
+      else       { re[i] = fm(c, r, m);  im[i] = fm(c, m, -r); }
+    }
+  }
+}
+
+// RZ on a thread bit: s = +1 (bit 0) or -1 (bit 1) for all of the thread's elements
+template <int N, typename T>
+__device__ __forceinline__ void rz_t(T* re, T* im, T c, int f, T s) {
+  if (f == 0) {
+    const T cs = s * c;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const T r = re[i], m = im[i];
+      re[i] = fm(cs, m, r);
+      im[i] = fm(-cs, r, m);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const T r = re[i], m = im[i];
+      re[i] = fm(c, r, s * m);
+      im[i] = fm(c, m, -s * r);
+    }
+  }
+}
+
+template <int N, int S, typename T>
+__device__ __forceinline__ void hd(T* re, T* im) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;
+      const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
+      re[i] = ar + br; im[i] = ai + bi;
+      re[j] = ar - br; im[j] = ai - bi;
+    }
+}
+
+// X and CNOT with both operands in registers: swaps (register renaming after inlining)
+template <int N, int SA, int SB, typename T>
+__device__ __forceinline__ void swp(T* re, T* im) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if ((i & SB) == SB && !(i & SA)) {
+      const int j = i | SA;
+      const T tr = re[i], ti = im[i];
+      re[i] = re[j]; im[i] = im[j];
+      re[j] = tr; im[j] = ti;
+    }
+}
+
+template <int N, int SA, typename T>
+__device__ __forceinline__ void cnot_t(T* re, T* im, bool ctl) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & SA)) {
+      const int j = i | SA;
+      const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
+      re[i] = ctl ? br : ar; im[i] = ctl ? bi : ai;
+      re[j] = ctl ? ar : br; im[j] = ctl ? ai : bi;
+    }
+}
+
+template <int N, int SA, int SB, typename T>
+__device__ __forceinline__ void cz(T* re, T* im) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if ((i & SA) && (i & SB)) { re[i] = -re[i]; im[i] = -im[i]; }
+}
+
+template <int N, int SA, typename T>
+__device__ __forceinline__ void cz_t(T* re, T* im, bool o) {
+  const T sg = o ? T(-1) : T(1);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (i & SA) { re[i] *= sg; im[i] *= sg; }
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void scal(T* re, T* im, T s) {
+#pragma unroll
+  for (int i = 0; i < N; i++) { re[i] *= s; im[i] *= s; }
+}
+
+// ---------------------------------------------------------------- gradient partials (before undoing)
+template <typename T> struct Acc { typedef float t; };
+template <> struct Acc<double> { typedef double t; };
+
+template <int N, int S, typename T>
+__device__ __forceinline__ typename Acc<T>::t g_ry(const T* pr, const T* pi, const T* lr, const T* li) {
+  typedef typename Acc<T>::t A;
+  A g = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;   // Re(l1* p0) - Re(l0* p1)
+      g = fm((A)lr[j], (A)pr[i], g);
+      g = fm((A)li[j], (A)pi[i], g);
+      g = fm(-(A)lr[i], (A)pr[j], g);
+      g = fm(-(A)li[i], (A)pi[j], g);
+    }
+  return g;
+}
+
+template <int N, int S, typename T>
+__device__ __forceinline__ typename Acc<T>::t g_rx(const T* pr, const T* pi, const T* lr, const T* li) {
+  typedef typename Acc<T>::t A;
+  A g = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;   // Im(l0* p1) + Im(l1* p0)
+      g = fm((A)lr[i], (A)pi[j], g);
+      g = fm(-(A)li[i], (A)pr[j], g);
+      g = fm((A)lr[j], (A)pi[i], g);
+      g = fm(-(A)li[j], (A)pr[i], g);
+    }
+  return g;
+}
+
+template <int N, int S, typename T>
+__device__ __forceinline__ typename Acc<T>::t g_rz(const T* pr, const T* pi, const T* lr, const T* li) {
+  typedef typename Acc<T>::t A;
+  A g0 = 0, g1 = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    if (i & S) { g1 = fm((A)lr[i], (A)pi[i], g1); g1 = fm(-(A)li[i], (A)pr[i], g1); }
+    else       { g0 = fm((A)lr[i], (A)pi[i], g0); g0 = fm(-(A)li[i], (A)pr[i], g0); }
+  }
+  return g0 - g1;
+}
+
+template <int N, typename T>
+__device__ __forceinline__ typename Acc<T>::t g_im(const T* pr, const T* pi, const T* lr, const T* li) {
+  typedef typename Acc<T>::t A;
+  A g = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++) { g = fm((A)lr[i], (A)pi[i], g); g = fm(-(A)li[i], (A)pr[i], g); }
+  return g;
+}
+
+template <int NTHR, typename A>
+__device__ __forceinline__ A warp_sum(A v) {
+  constexpr unsigned mask = NTHR >= 32 ? 0xffffffffu : ((1u << NTHR) - 1u);
+#pragma unroll
+  for (int off = (NTHR >= 32 ? 16 : NTHR / 2); off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+  return v;
+}
+
+// ---------------------------------------------------------------- pair access in shared memory
+__device__ __forceinline__ void ldp(const void* tile, u32 w, float& r0, float& i0, float& r1, float& i1) {
+  const float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
+  r0 = v.x; i0 = v.y; r1 = v.z; i1 = v.w;
+}
+__device__ __forceinline__ void stp(void* tile, u32 w, float r0, float i0, float r1, float i1) {
+  reinterpret_cast<float4*>(tile)[w >> 1] = make_float4(r0, i0, r1, i1);
+}
+__device__ __forceinline__ void ldp(const void* tile, u32 w, double& r0, double& i0, double& r1, double& i1) {
+  const double2 a = reinterpret_cast<const double2*>(tile)[w], b = reinterpret_cast<const double2*>(tile)[w ^ 1u];
+  r0 = a.x; i0 = a.y; r1 = b.x; i1 = b.y;
+}
+__device__ __forceinline__ void stp(void* tile, u32 w, double r0, double i0, double r1, double i1) {
+  reinterpret_cast<double2*>(tile)[w] = make_double2(r0, i0);
+  reinterpret_cast<double2*>(tile)[w ^ 1u] = make_double2(r1, i1);
+}
+
+// ---------------------------------------------------------------- tile context
+// EPC: amplitudes per 16-byte chunk; NB: chunk-index bits owned by the loop (i) per thread.
+template <typename T, int K, int R, int NTHR>
+struct Geo {
+  static constexpr int EPC = sizeof(T) == 4 ? 2 : 1;
+  static constexpr int LOGT = K - R;
+  static constexpr int LO = LOGT + (EPC == 2 ? 1 : 0);   // first tile bit driven by the chunk loop
+  static constexpr int NB = K - LO;                       // chunk loop bits
+  static constexpr int NCH = 1 << NB;                     // chunks per thread
+  static constexpr int EL = 2 * sizeof(T);                // bytes per amplitude
+  static constexpr int TILE = EL << K;                    // bytes per tile
+};
+
+// Tile base (element offset in the batched state) and the thread's chunk offsets.
+template <typename T, int K, int R, int NTHR>
+struct Chunks {
+  typedef Geo<T, K, R, NTHR> G;
+  i64 gb;            // global offset (within the tile) of the thread's chunk 0
+  i64 gu[G::NB > 0 ? G::NB : 1];
+  __device__ __forceinline__ void init(const u8* L, u32 tid) {
+    const u32 e0 = (u32)G::EPC * tid;
+    gb = 0;
+#pragma unroll
+    for (int j = 0; j < G::LO; j++)
+      if ((e0 >> j) & 1u) gb |= (i64)1 << L[j];
+#pragma unroll
+    for (int r = 0; r < G::NB; r++) gu[r] = (i64)1 << L[G::LO + r];
+  }
+  template <int I>
+  __device__ __forceinline__ i64 g() const {
+    i64 x = gb;
+#pragma unroll
+    for (int r = 0; r < G::NB; r++)
+      if ((I >> r) & 1) x |= gu[r];
+    return x;
+  }
+};
+
+template <int I, int LO, int NB>
+struct ChunkElem {   // tile element offset of loop index I (compile time)
+  static constexpr u32 v = (u32)I << LO;
+};
+
+__device__ __forceinline__ i64 tile_base(const Args& a, i64& b_out, i64& t_out) {
+  const i64 b = (i64)blockIdx.x / a.tps;
+  const i64 t = (i64)blockIdx.x - b * a.tps;
+  i64 base = b << a.n;
+  for (int j = 0; j < a.n_nonlocal; j++)
+    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
+  b_out = b;
+  t_out = t;
+  return base;
+}
+
+// Compile-time loop helper
+template <int I, int END>
+struct Unroll {
+  template <typename F>
+  __device__ __forceinline__ static void run(F& f) {
+    f.template step<I>();
+    Unroll<I + 1, END>::run(f);
+  }
+};
+template <int END>
+struct Unroll<END, END> {
+  template <typename F>
+  __device__ __forceinline__ static void run(F&) {}
+};
+
+// ---------------------------------------------------------------- forward pass
+template <typename T, int K, int R, int NTHR, class Spec>
+struct FwdLoad {
+  typedef Geo<T, K, R, NTHR> G;
+  const T* in; void* tile; const Chunks<T, K, R, NTHR>* ch; u32 s0;
+  template <int I>
+  __device__ __forceinline__ void step() {
+    const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
+    cp16(reinterpret_cast<char*>(tile) + (size_t)w * G::EL, in + 2 * ch->template g<I>());
+  }
+};
+
+template <typename T, int K, int R, int NTHR, class Spec>
+struct FwdZero {
+  typedef Geo<T, K, R, NTHR> G;
+  void* tile; u32 s0;
+  template <int I>
+  __device__ __forceinline__ void step() {
+    const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
+    if (G::EPC == 2) reinterpret_cast<float4*>(tile)[w >> 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    else reinterpret_cast<double2*>(tile)[w] = make_double2(0.0, 0.0);
+  }
+};
+
+template <typename T, int K, int R, int NTHR, class Spec, bool Z>
+struct FwdStore {
+  typedef Geo<T, K, R, NTHR> G;
+  typedef typename Acc<T>::t A;
+  T* out; const void* tile; const Chunks<T, K, R, NTHR>* ch; u32 s0; T scale;
+  A zt; A zs[G::NB + 1];
+  template <int I>
+  __device__ __forceinline__ void step() {
+    const u32 w = s0 ^ Spec::lay_last(ChunkElem<I, G::LO, G::NB>::v);
+    const i64 g = ch->template g<I>();
+    if (G::EPC == 2) {
+      float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
+      v.x *= (float)scale; v.y *= (float)scale; v.z *= (float)scale; v.w *= (float)scale;
+      *reinterpret_cast<float4*>(out + 2 * g) = v;
+      if (Z) {
+        const A p0 = fm((A)v.x, (A)v.x, (A)v.y * (A)v.y), p1 = fm((A)v.z, (A)v.z, (A)v.w * (A)v.w);
+        zt += p0 + p1;
+        zs[0] += p0 - p1;
+#pragma unroll
+        for (int r = 0; r < G::NB; r++) zs[1 + r] += ((I >> r) & 1) ? -(p0 + p1) : (p0 + p1);
+      }
+    } else {
+      double2 v = reinterpret_cast<const double2*>(tile)[w];
+      v.x *= (double)scale; v.y *= (double)scale;
+      *reinterpret_cast<double2*>(out + 2 * g) = v;
+      if (Z) {
+        const A p = (A)(v.x * v.x + v.y * v.y);
+        zt += p;
+#pragma unroll
+        for (int r = 0; r < G::NB; r++) zs[r] += ((I >> r) & 1) ? -p : p;
+      }
+    }
+  }
+};
+
+// Block reduction of the <Z> partials into zpart[tile][0..K] (tile bit j signed sums, K = total).
+template <typename T, int K, int R, int NTHR>
+__device__ __forceinline__ void z_reduce(void* smem, const typename Acc<T>::t zt, const typename Acc<T>::t* zs,
+                                         double* zrow) {
+  typedef Geo<T, K, R, NTHR> G;
+  typedef typename Acc<T>::t A;
+  constexpr int NZ = G::NB + 2;
+  A* red = reinterpret_cast<A*>(smem);
+  const u32 tid = threadIdx.x;
+  __syncthreads();
+  red[tid * NZ] = zt;
+#pragma unroll
+  for (int r = 0; r < G::NB + 1; r++) red[tid * NZ + 1 + r] = zs[r];
+  __syncthreads();
+  constexpr int TID_LO = G::EPC == 2 ? 1 : 0;
+  for (int j = tid; j <= K; j += NTHR) {
+    double acc = 0.0;
+    if (j == K) {
+      for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ];
+    } else if (j >= TID_LO && j < TID_LO + G::LOGT) {
+      const int bit = j - TID_LO;
+      for (int u = 0; u < NTHR; u++) acc += ((u >> bit) & 1) ? -(double)red[u * NZ] : (double)red[u * NZ];
+    } else {
+      const int slot = (G::EPC == 2 && j == 0) ? 0 : (G::EPC == 2 ? 1 : 0) + (j - G::LO);
+      for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ + 1 + slot];
+    }
+    zrow[j] = acc;
+  }
+}
+
+template <typename T, int K, int R, int NTHR, class Spec>
+__device__ __forceinline__ void fwd_pass(const Args& a) {
+  typedef Geo<T, K, R, NTHR> G;
+  typedef typename Acc<T>::t A;
+  extern __shared__ __align__(16) unsigned char smem[];
+  void* tile = smem;
+  T* cf = reinterpret_cast<T*>(smem + G::TILE);
+  u8* fmv = reinterpret_cast<u8*>(cf + (Spec::NOPS > 0 ? Spec::NOPS : 1));
+  const u32 tid = threadIdx.x;
+  i64 b, t;
+  const i64 base = tile_base(a, b, t);
+  for (int i = tid; i < Spec::NOPS; i += NTHR) {
+    const int g = a.op_gate[i];
+    if (g >= 0) {
+      cf[i] = reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + b];
+      fmv[i] = a.form[(i64)g * a.B + b];
+    }
+  }
+  Chunks<T, K, R, NTHR> ch;
+  ch.init(a.L, tid);
+  if (a.in == nullptr) {
+    FwdZero<T, K, R, NTHR, Spec> f{tile, Spec::lay_first((u32)G::EPC * tid)};
+    Unroll<0, G::NCH>::run(f);
+    __syncthreads();
+    if (tid == 0 && t == 0) reinterpret_cast<T*>(tile)[0] = T(1);
+  } else {
+    FwdLoad<T, K, R, NTHR, Spec> f{reinterpret_cast<const T*>(a.in) + 2 * base, tile, &ch,
+                                   Spec::lay_first((u32)G::EPC * tid)};
+    Unroll<0, G::NCH>::run(f);
+    cp_wait_all();
+  }
+  __syncthreads();
+  Spec::template fwd_phases<T>(tile, cf, fmv, tid);
+  FwdStore<T, K, R, NTHR, Spec, true> st;
+  st.out = reinterpret_cast<T*>(a.out) + 2 * base;
+  st.tile = tile;
+  st.ch = &ch;
+  st.s0 = Spec::lay_last((u32)G::EPC * tid);
+  st.scale = reinterpret_cast<const T*>(a.scale)[b];
+  if (a.zpart) {
+    st.zt = 0;
+#pragma unroll
+    for (int r = 0; r < G::NB + 1; r++) st.zs[r] = 0;
+    Unroll<0, G::NCH>::run(st);
+    z_reduce<T, K, R, NTHR>(smem, st.zt, st.zs, a.zpart + (b * a.tps + t) * (K + 1));
+  } else {
+    FwdStore<T, K, R, NTHR, Spec, false> s2;
+    s2.out = st.out; s2.tile = tile; s2.ch = &ch; s2.s0 = st.s0; s2.scale = st.scale;
+    Unroll<0, G::NCH>::run(s2);
+  }
+}
+
+// ---------------------------------------------------------------- backward pass
+template <typename T, int K, int R, int NTHR, class Spec>
+struct BwdLoad {
+  typedef Geo<T, K, R, NTHR> G;
+  const T* pin; const T* lin; void* tp; void* tl; const Chunks<T, K, R, NTHR>* ch; u32 s0;
+  template <int I>
+  __device__ __forceinline__ void step() {
+    const u32 w = s0 ^ Spec::lay_last(ChunkElem<I, G::LO, G::NB>::v);
+    const i64 g = ch->template g<I>();
+    cp16(reinterpret_cast<char*>(tp) + (size_t)w * G::EL, pin + 2 * g);
+    if (lin) cp16(reinterpret_cast<char*>(tl) + (size_t)w * G::EL, lin + 2 * g);
+  }
+};
+
+// lambda = (sum_i g_i Z_i) psi at load: d(e) = dconst + sum_j (bit_j(e) ? -g_j : g_j)
+template <typename T, int K, int R, int NTHR, class Spec>
+struct BwdLambda {
+  typedef Geo<T, K, R, NTHR> G;
+  void* tp; void* tl; u32 s0; double dtid; const double* gq;
+  template <int I>
+  __device__ __forceinline__ void step() {
+    const u32 e = ChunkElem<I, G::LO, G::NB>::v;
+    double d = dtid;
+#pragma unroll
+    for (int r = 0; r < G::NB; r++) d += ((I >> r) & 1) ? -gq[G::LO + r] : gq[G::LO + r];
+#pragma unroll
+    for (int h = 0; h < G::EPC; h++) {
+      const double dh = (G::EPC == 2) ? (h ? d - gq[0] : d + gq[0]) : d;
+      const u32 w = s0 ^ Spec::lay_last(e) ^ (u32)h;
+      typedef typename Acc<T>::t A;
+      T* P = reinterpret_cast<T*>(tp) + 2 * w;
+      T* Lm = reinterpret_cast<T*>(tl) + 2 * w;
+      Lm[0] = (T)(dh * (double)P[0]);
+      Lm[1] = (T)(dh * (double)P[1]);
+    }
+  }
+};
+
+template <typename T, int K, int R, int NTHR, class Spec>
+struct BwdStore {
+  typedef Geo<T, K, R, NTHR> G;
+  T* pout; T* lout; const void* tp; const void* tl; const Chunks<T, K, R, NTHR>* ch; u32 s0; T scale;
+  template <int I>
+  __device__ __forceinline__ void step() {
+    const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
+    const i64 g = ch->template g<I>();
+    if (G::EPC == 2) {
+      float4 v = reinterpret_cast<const float4*>(tp)[w >> 1];
+      float4 l = reinterpret_cast<const float4*>(tl)[w >> 1];
+      const float s = (float)scale;
+      v.x *= s; v.y *= s; v.z *= s; v.w *= s;
+      l.x *= s; l.y *= s; l.z *= s; l.w *= s;
+      *reinterpret_cast<float4*>(pout + 2 * g) = v;
+      *reinterpret_cast<float4*>(lout + 2 * g) = l;
+    } else {
+      double2 v = reinterpret_cast<const double2*>(tp)[w], l = reinterpret_cast<const double2*>(tl)[w];
+      const double s = (double)scale;
+      v.x *= s; v.y *= s; l.x *= s; l.y *= s;
+      *reinterpret_cast<double2*>(pout + 2 * g) = v;
+      *reinterpret_cast<double2*>(lout + 2 * g) = l;
+    }
+  }
+};
+
+template <typename T, int K, int R, int NTHR, class Spec>
+__device__ __forceinline__ void bwd_pass(const Args& a) {
+  typedef Geo<T, K, R, NTHR> G;
+  typedef typename Acc<T>::t A;
+  constexpr int NW = (NTHR + 31) / 32;
+  constexpr int NG = Spec::NGS > 0 ? Spec::NGS : 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  void* tp = smem;
+  void* tl = smem + G::TILE;
+  A* red = reinterpret_cast<A*>(smem + 2 * G::TILE);                  // [NW][NG]
+  double* gq = reinterpret_cast<double*>(red + NW * NG + (NW * NG) % 2 + 2);  // [K + 1]
+  T* cf = reinterpret_cast<T*>(gq + K + 2);
+  u8* fmv = reinterpret_cast<u8*>(cf + (Spec::NOPS > 0 ? Spec::NOPS : 1));
+  const u32 tid = threadIdx.x;
+  i64 b, t;
+  const i64 base = tile_base(a, b, t);
+  for (int i = tid; i < Spec::NOPS; i += NTHR) {
+    const int g = a.op_gate[i];
+    if (g >= 0) {
+      cf[i] = -reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + b];   // inverse: negated coefficient
+      fmv[i] = a.form[(i64)g * a.B + b];
+    }
+  }
+  const bool init_lambda = a.lam_in == nullptr;
+  if (init_lambda) {
+    for (int j = tid; j <= K; j += NTHR) {
+      if (j < K) {
+        gq[j] = a.grad_out[b * a.n + (a.n - 1 - a.L[j])];
+      } else {
+        double dc = 0.0;
+        for (int q = 0; q < a.n_nonlocal; q++) {
+          const double g = a.grad_out[b * a.n + (a.n - 1 - a.nonlocal[q])];
+          dc += ((t >> q) & 1) ? -g : g;
+        }
+        gq[K] = dc;
+      }
+    }
+  }
+  Chunks<T, K, R, NTHR> ch;
+  ch.init(a.L, tid);
+  const u32 sl = Spec::lay_last((u32)G::EPC * tid);
+  BwdLoad<T, K, R, NTHR, Spec> ld{reinterpret_cast<const T*>(a.in) + 2 * base,
+                                  init_lambda ? nullptr : reinterpret_cast<const T*>(a.lam_in) + 2 * base,
+                                  tp, tl, &ch, sl};
+  Unroll<0, G::NCH>::run(ld);
+  cp_wait_all();
+  __syncthreads();
+  if (init_lambda) {
+    // thread part of d: tile bits below LO come from the thread id (bit 0 handled per element)
+    double dt = gq[K];
+    const u32 e0 = (u32)G::EPC * tid;
+#pragma unroll
+    for (int j = (G::EPC == 2 ? 1 : 0); j < G::LO; j++) dt += ((e0 >> j) & 1u) ? -gq[j] : gq[j];
+    if (G::EPC == 1) {
+      // tile bit 0 belongs to the thread id as well
+    }
+    BwdLambda<T, K, R, NTHR, Spec> lf{tp, tl, sl, dt, gq};
+    Unroll<0, G::NCH>::run(lf);
+    __syncthreads();
+  }
+  Spec::template bwd_phases<T>(tp, tl, cf, fmv, red, tid);
+  __syncthreads();
+  for (int s = tid; s < Spec::NGS; s += NTHR) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) acc += (double)red[w * NG + s];
+    a.gpart[((a.gpart_offset + s) * a.B + b) * a.tps + t] = acc;
+  }
+  if (a.out == nullptr) return;
+  BwdStore<T, K, R, NTHR, Spec> st{reinterpret_cast<T*>(a.out) + 2 * base, reinterpret_cast<T*>(a.lam_out) + 2 * base,
+                                   tp, tl, &ch, Spec::lay_first((u32)G::EPC * tid),
+                                   reinterpret_cast<const T*>(a.scale)[b]};
+  Unroll<0, G::NCH>::run(st);
+}
+
+}  // namespace qj

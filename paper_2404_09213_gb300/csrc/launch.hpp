@@ -13,37 +13,6 @@ namespace qsim {
 // Number of kernels this library has launched in the process (for launch accounting).
 extern std::atomic<long long> g_kernel_launches;
 
-struct PassLaunch {
-  const DevPass* h_pass;     // host copy (for sizes)
-  const DevPass* d_pass;     // device copy
-  const DevPhase* d_phases;
-  const DevOp* d_ops;
-  const DevLayout* d_layouts;
-  int n, B;
-  const void* coef;          // [G * B] scaled-rotation coefficients
-  const uint8_t* form;       // [G * B] 0: tangent form, 1: cotangent form
-  const void* scale;         // [B] this pass's scale (forward or backward)
-};
-
-// Forward pass over all tiles: in == nullptr starts from |0...0>; zpart != nullptr adds the
-// <Z> epilogue (per-tile partial sums, (B * tiles) x (k+1) doubles).
-cudaError_t launch_fwd_pass(const PassLaunch& L, int dtype, const void* in, void* out, double* zpart,
-                            cudaStream_t st);
-
-// Backward pass: psi_in/lam_in -> psi_out/lam_out (out == nullptr: no store); lam_in == nullptr
-// initialises lambda = (sum_i g_{b,i} Z_i) psi from grad_out. Gradient partials go to gpart.
-cudaError_t launch_bwd_pass(const PassLaunch& L, int dtype, const void* psi_in, void* psi_out,
-                            const void* lam_in, void* lam_out, const double* grad_out, double* gpart,
-                            cudaStream_t st);
-
-size_t fwd_pass_smem(const DevPass& p, int dtype, int nthr);
-size_t bwd_pass_smem(const DevPass& p, int dtype, int nthr);
-cudaError_t prepare_pass_kernels(int dtype, size_t max_fwd_smem, size_t max_bwd_smem);
-int bwd_R(int k);
-int fwd_R_for(int k, int dtype);
-int bwd_R_for(int k, int dtype);
-int max_k_for(int dtype);
-
 // ---- coefficients: one thread per (pass, sample)
 struct CoefArgs {
   const int32_t* gate_type;     // [G]

@@ -81,3 +81,17 @@ def test_plan_info_and_defaults(q):
     assert p2.info()["k"] == 11
     p3 = q.Plan(W.ring_ansatz(5, 2), 5, mode="per_gate")
     assert p3.info()["n_passes"] == len(W.ring_ansatz(5, 2))
+
+
+@pytest.mark.parametrize("gates,n,kw", [
+    (W.ring_ansatz(10, 2), 10, {"k": 8}),
+    (W.hea_cz_ansatz(9, 2), 9, {"k": 7, "contiguous_bits": 2}),
+    (W.ring_ansatz(4, 2), 4, {"dtype": "c128"}),
+    ([W.gate(W.H, (0,)), W.gate(W.X, (1,)), W.gate(W.CZ, (2,), (0,)), W.gate(W.RX, (1,), param=0)], 3, {"k": 3, "contiguous_bits": 1}),
+])
+def test_specialised_kernels_compile_on_host(q, gates, n, kw):
+    # NVRTC runs without a GPU: the generated pass kernels must compile for sm_103a
+    p = q.Plan(gates, n, **kw)
+    src = p.kernel_source()
+    assert src.count('extern "C" __global__') >= 2
+    p.compile_kernels()
