@@ -81,39 +81,59 @@ struct qsim_plan_s {
   int B = 0;
   cudaStream_t last_stream = nullptr;
   // optional per-pass event timing
-  int prof_depth = 0;            // 0 = off; else event sets kept for this many calls
+  // optional per-launch event timing (a log of launches; read_profile sums them per pass)
+  int prof_depth = 0;            // 0 = off; else number of forward + backward calls to log
   bool profiling = false;
-  std::vector<cudaEvent_t> ev_f0, ev_f1, ev_b0, ev_b1;   // [depth][P]
+  struct ProfRec {
+    int dir, pass;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof_log;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
   int64_t n_fwd_calls = 0, n_bwd_calls = 0;
-  int fslot(int q) const { return (int)((n_fwd_calls % prof_depth) * P() + q); }
-  int bslot(int q) const { return (int)((n_bwd_calls % prof_depth) * P() + q); }
 
-  int ensure_events() {
-    const size_t n = (size_t)P() * prof_depth;
-    auto mk = [&](std::vector<cudaEvent_t>& v) -> cudaError_t {
-      while (v.size() < n) {
-        cudaEvent_t e;
-        cudaError_t r = cudaEventCreate(&e);
-        if (r != cudaSuccess) return r;
-        v.push_back(e);
-      }
-      return cudaSuccess;
-    };
-    cudaError_t e = mk(ev_f0);
-    if (e == cudaSuccess) e = mk(ev_f1);
-    if (e == cudaSuccess) e = mk(ev_b0);
-    if (e == cudaSuccess) e = mk(ev_b1);
-    if (e != cudaSuccess) return cuda_fail(e, "creating profiling events");
-    return QSIM_OK;
+  cudaEvent_t next_event() {
+    if (ev_used == ev_pool.size()) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+      ev_pool.push_back(e);
+    }
+    return ev_pool[ev_used++];
+  }
+  bool calls_left(int dir) const {
+    return profiling && (dir == 0 ? n_fwd_calls : n_bwd_calls) < prof_depth;
+  }
+  // record an event before a launch; returns the log index (or -1)
+  int prof_begin(int dir, int pass, cudaStream_t st) {
+    if (!calls_left(dir)) return -1;
+    cudaEvent_t a = next_event(), b = next_event();
+    if (!a || !b) return -1;
+    cudaEventRecord(a, st);
+    prof_log.push_back({dir, pass, a, b});
+    return (int)prof_log.size() - 1;
+  }
+  void prof_end(int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(prof_log[idx].b, st);
   }
   void destroy_events() {
-    for (auto* v : {&ev_f0, &ev_f1, &ev_b0, &ev_b1}) {
-      for (auto e : *v) cudaEventDestroy(e);
-      v->clear();
-    }
+    for (auto e : ev_pool) cudaEventDestroy(e);
+    ev_pool.clear();
+    prof_log.clear();
+    ev_used = 0;
   }
 
   int P() const { return (int)s.passes.size(); }
+  // samples per L2-resident group
+  int group_size(int B_) const {
+    if (opts.sample_block > 0) return std::min(opts.sample_block, B_);
+    if (opts.sample_block < 0 || s.mode != QSIM_FUSED) return B_;
+    const int64_t per_sample = ((int64_t)1 << s.n) * el;
+    const int64_t budget = 48ll << 20;   // part of the 126 MB L2 kept for one group's working set
+    int64_t g = budget / (2 * per_sample);
+    if (g < 1) g = 1;
+    return (int)std::min<int64_t>(g, B_);
+  }
   int64_t tps() const {
     return s.mode == QSIM_PER_GATE ? pg_blocks_per_sample(s.n) : s.passes.empty() ? 1 : s.passes[0].dev.tiles_per_sample;
   }
@@ -377,7 +397,12 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
     if (o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   }
   p->opts = o;
-  rc = build_schedule(gv, n_qubits, o, fwd_R_for(16, o.dtype), bwd_R_for(16, o.dtype), p->s, err);
+  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.sample_block < -1) {
+    delete p;
+    return fail(QSIM_ERR_ARG, "bwd_reg_bits must be in [0, 5] and sample_block >= -1");
+  }
+  const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
+  rc = build_schedule(gv, n_qubits, o, fwd_R_for(16, o.dtype), Rb, p->s, err);
   if (rc) {
     delete p;
     return fail(rc, err);
@@ -502,36 +527,41 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
     e = launch_pg_init(d_states, d_init, s.n, batch, s.dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "init kernel");
     for (int g = 0; g < (int)s.gates.size(); g++) {
-      if (p->profiling) cudaEventRecord(p->ev_f0[p->fslot(g)], st);
+      const int rec = p->prof_begin(0, g, st);
       e = launch_pg_gate(p->pg_args(g, sf + (size_t)g * batch * p->sc), d_states, false, st);
       if (e != cudaSuccess) return cuda_fail(e, "per-gate kernel");
-      if (p->profiling) cudaEventRecord(p->ev_f1[p->fslot(g)], st);
+      p->prof_end(rec, st);
     }
     e = launch_expval_z(d_states, s.n, batch, s.dtype, p->zpart, d_z, st);
     if (e != cudaSuccess) return cuda_fail(e, "<Z> kernel");
   } else {
     const int P_ = p->P();
-    for (int q = 0; q < P_; q++) {
-      const int seg = p->seg_of(q);
-      void* out = (seg == p->n_segments - 1) ? d_states : p->ckpt[seg];
-      const void* in;
-      if (q == p->seg_begin[seg]) in = (seg == 0) ? d_init : p->ckpt[seg - 1];
-      else in = out;
-      JitArgs ja = p->jit_args(q, false, sf + (size_t)q * batch * p->sc);
-      ja.in = in;
-      ja.out = out;
-      ja.zpart = (q == P_ - 1) ? p->zpart : nullptr;
-      if (p->profiling) cudaEventRecord(p->ev_f0[p->fslot(q)], st);
-      e = jit_launch(p->jit.fwd[q], s.passes[q].dev.tiles_per_sample * batch, ja, st);
-      if (e != cudaSuccess) return cuda_fail(e, "fused forward pass");
-      if (p->profiling) cudaEventRecord(p->ev_f1[p->fslot(q)], st);
+    const int G = p->group_size(batch);
+    for (int b0 = 0; b0 < batch; b0 += G) {
+      const int nb = std::min(G, batch - b0);
+      for (int q = 0; q < P_; q++) {
+        const int seg = p->seg_of(q);
+        void* out = (seg == p->n_segments - 1) ? d_states : p->ckpt[seg];
+        const void* in;
+        if (q == p->seg_begin[seg]) in = (seg == 0) ? d_init : p->ckpt[seg - 1];
+        else in = out;
+        JitArgs ja = p->jit_args(q, false, sf + (size_t)q * batch * p->sc);
+        ja.in = in;
+        ja.out = out;
+        ja.zpart = (q == P_ - 1) ? p->zpart : nullptr;
+        ja.b0 = b0;
+        const int rec = p->prof_begin(0, q, st);
+        e = jit_launch(p->jit.fwd[q], s.passes[q].dev.tiles_per_sample * nb, ja, st);
+        if (e != cudaSuccess) return cuda_fail(e, "fused forward pass");
+        p->prof_end(rec, st);
+      }
     }
     const DevPass& last = s.passes.back().dev;
     e = launch_z_final(p->zpart, last.k, p->d_Lnl_last, last.n_nonlocal, last.tiles_per_sample, s.n, batch, d_z, st);
     if (e != cudaSuccess) return cuda_fail(e, "<Z> reduction");
   }
   p->has_fwd = true;
-  if (p->profiling) p->n_fwd_calls++;
+  if (p->calls_left(0)) p->n_fwd_calls++;
   return QSIM_OK;
 }
 
@@ -552,31 +582,36 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
     const int bps = pg_blocks_per_sample(s.n);
     for (int g = (int)s.gates.size() - 1; g >= 0; g--) {
       double* gp = p->gpart + s.passes[g].dev.gpart_offset * (int64_t)B * bps;
-      if (p->profiling) cudaEventRecord(p->ev_b0[p->bslot(g)], st);
+      const int rec = p->prof_begin(1, g, st);
       e = launch_pg_bwd_gate(p->pg_args(g, sbk + (size_t)g * B * p->sc), p->W, p->Lam, gp, bps, st);
       if (e != cudaSuccess) return cuda_fail(e, "per-gate backward kernel");
-      if (p->profiling) cudaEventRecord(p->ev_b1[p->bslot(g)], st);
+      p->prof_end(rec, st);
     }
   } else {
     const int P_ = p->P();
-    for (int q = P_ - 1; q >= 0; q--) {
-      const int seg = p->seg_of(q);
-      const bool seg_last = (q == p->seg_begin[seg + 1] - 1);
-      const void* pin = seg_last ? ((seg == p->n_segments - 1) ? p->states : p->ckpt[seg]) : p->W;
-      const void* lin = (q == P_ - 1) ? nullptr : p->Lam;
-      void* pout = q == 0 ? nullptr : p->W;
-      void* lout = q == 0 ? nullptr : p->Lam;
-      JitArgs ja = p->jit_args(q, true, sbk + (size_t)q * B * p->sc);
-      ja.in = pin;
-      ja.out = pout;
-      ja.lam_in = lin;
-      ja.lam_out = lout;
-      ja.grad_out = d_grad_out;
-      ja.gpart = p->gpart;
-      if (p->profiling) cudaEventRecord(p->ev_b0[p->bslot(q)], st);
-      e = jit_launch(p->jit.bwd[q], s.passes[q].devb.tiles_per_sample * B, ja, st);
-      if (e != cudaSuccess) return cuda_fail(e, "fused backward pass");
-      if (p->profiling) cudaEventRecord(p->ev_b1[p->bslot(q)], st);
+    const int G = p->group_size(B);
+    for (int b0 = 0; b0 < B; b0 += G) {
+      const int nb = std::min(G, B - b0);
+      for (int q = P_ - 1; q >= 0; q--) {
+        const int seg = p->seg_of(q);
+        const bool seg_last = (q == p->seg_begin[seg + 1] - 1);
+        const void* pin = seg_last ? ((seg == p->n_segments - 1) ? p->states : p->ckpt[seg]) : p->W;
+        const void* lin = (q == P_ - 1) ? nullptr : p->Lam;
+        void* pout = q == 0 ? nullptr : p->W;
+        void* lout = q == 0 ? nullptr : p->Lam;
+        JitArgs ja = p->jit_args(q, true, sbk + (size_t)q * B * p->sc);
+        ja.in = pin;
+        ja.out = pout;
+        ja.lam_in = lin;
+        ja.lam_out = lout;
+        ja.grad_out = d_grad_out;
+        ja.gpart = p->gpart;
+        ja.b0 = b0;
+        const int rec = p->prof_begin(1, q, st);
+        e = jit_launch(p->jit.bwd[q], s.passes[q].devb.tiles_per_sample * nb, ja, st);
+        if (e != cudaSuccess) return cuda_fail(e, "fused backward pass");
+        p->prof_end(rec, st);
+      }
     }
   }
   GradReduceArgs ga{};
@@ -598,26 +633,19 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
   ga.dinputs = d_dinputs;
   e = launch_grad_reduce(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction");
-  if (p->profiling) p->n_bwd_calls++;
+  if (p->calls_left(1)) p->n_bwd_calls++;
   return QSIM_OK;
 }
 
 int qsim_set_profiling(qsim_plan_t p, int32_t depth) {
   if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
   if (depth < 0) return fail(QSIM_ERR_ARG, "depth < 0");
-  if (p->last_stream || p->n_fwd_calls || p->n_bwd_calls) cudaStreamSynchronize(p->last_stream);
-  p->destroy_events();
+  if (p->uploaded) cudaStreamSynchronize(p->last_stream);
+  p->prof_log.clear();
+  p->ev_used = 0;
   p->n_fwd_calls = p->n_bwd_calls = 0;
   p->prof_depth = depth;
   p->profiling = depth > 0;
-  if (depth > 0) {
-    int rc = p->ensure_events();
-    if (rc) {
-      p->profiling = false;
-      p->prof_depth = 0;
-      return rc;
-    }
-  }
   return QSIM_OK;
 }
 
@@ -625,30 +653,22 @@ int qsim_read_profile(qsim_plan_t p, float* fwd, float* bwd, int32_t cap, int32_
   if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
   const int P_ = p->P();
   if (n_passes) *n_passes = P_;
-  const int64_t nf = p->prof_depth ? std::min<int64_t>(p->n_fwd_calls, p->prof_depth) : 0;
-  const int64_t nb = p->prof_depth ? std::min<int64_t>(p->n_bwd_calls, p->prof_depth) : 0;
   if (n_calls) {
-    n_calls[0] = (int32_t)nf;
-    n_calls[1] = (int32_t)nb;
+    n_calls[0] = (int32_t)std::min<int64_t>(p->n_fwd_calls, p->prof_depth);
+    n_calls[1] = (int32_t)std::min<int64_t>(p->n_bwd_calls, p->prof_depth);
   }
   for (int q = 0; q < P_ && q < cap; q++) {
     if (fwd) fwd[q] = 0.f;
     if (bwd) bwd[q] = 0.f;
-    for (int64_t c = 0; c < nf && fwd; c++) {
-      float ms = 0.f;
-      const int i = (int)(c * P_ + q);
-      cudaError_t e = cudaEventSynchronize(p->ev_f1[i]);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev_f0[i], p->ev_f1[i]);
-      if (e != cudaSuccess) return cuda_fail(e, "reading forward events");
-      fwd[q] += ms;
-    }
-    for (int64_t c = 0; c < nb && bwd; c++) {
-      float ms = 0.f;
-      const int i = (int)(c * P_ + q);
-      cudaError_t e = cudaEventSynchronize(p->ev_b1[i]);
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p->ev_b0[i], p->ev_b1[i]);
-      if (e != cudaSuccess) return cuda_fail(e, "reading backward events");
-      bwd[q] += ms;
+  }
+  for (auto& r : p->prof_log) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "reading profiling events");
+    if (r.pass < cap) {
+      float* dst = r.dir == 0 ? fwd : bwd;
+      if (dst) dst[r.pass] += ms;
     }
   }
   return QSIM_OK;

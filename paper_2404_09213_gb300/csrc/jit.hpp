@@ -28,7 +28,7 @@ struct JitArgs {
   const uint8_t* nonlocal;
   int64_t tps;
   int64_t gpart_offset;
-  int n_nonlocal, n, B, pad;
+  int n_nonlocal, n, B, b0;   // b0: first sample of this launch (tiles cover samples b0, b0+1, ...)
 };
 
 struct JitKernel {
