@@ -149,27 +149,20 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 // ------------------------------------------------------------------ generation
 static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) {
   const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
-  const bool packed = s.dtype != QSIM_C128;   // complex64: float2 SIMD over the register-bit-0 pair
-  const int N2 = N / 2;
   std::ostringstream o;
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
-  o << "  static constexpr bool PLANAR = " << ((packed && d.n_phases > 0) ? "true" : "false") << ";\n";
   for (int i = 0; i <= d.n_phases; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
   o << "  static __device__ __forceinline__ qj::u32 lay_first(qj::u32 e) { return L0(e); }\n";
   o << "  static __device__ __forceinline__ qj::u32 lay_last(qj::u32 e) { return L" << d.n_phases << "(e); }\n";
-  const char* RE = packed ? "R" : "re";
-  const char* IM = packed ? "I" : "im";
   if (!bwd) {
     o << "  template <typename T> static __device__ __forceinline__ void fwd_phases(void* tile, const T* cf, "
          "const qj::u8* fm, qj::u32 tid) {\n";
-    if (packed) o << "    float2 R[" << N2 << "], I[" << N2 << "];\n";
-    else o << "    T re[" << N << "], im[" << N << "];\n";
+    o << "    T re[" << N << "], im[" << N << "];\n";
   } else {
     o << "  template <typename T, typename A> static __device__ __forceinline__ void bwd_phases(void* tp, void* tl, "
          "const T* cf, const qj::u8* fm, A* red, qj::u32 tid) {\n";
-    if (packed) o << "    float2 PR[" << N2 << "], PI[" << N2 << "], LR[" << N2 << "], LI[" << N2 << "];\n";
-    else o << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n";
+    o << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n";
     o << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n";
     o << "    (void)lane; (void)warp;\n";
   }
@@ -177,7 +170,6 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) 
     const int ph = bwd ? d.n_phases - 1 - step : step;
     const DevPhase& P = s.phases[d.phase0 + ph];
     const int lin = bwd ? ph + 1 : ph, lout = bwd ? ph : ph + 1;
-    const bool in_interleaved = bwd ? (lin == d.n_phases) : (lin == 0);   // the load stage's words
     const DevLayout& Li = s.layouts[d.lay0 + lin];
     const DevLayout& Lo = s.layouts[d.lay0 + lout];
     o << "    { // phase " << ph << "\n";
@@ -191,18 +183,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) 
         if ((i >> r) & 1) e |= 1u << P.rbit[r];
       return e;
     };
-    const char* LD = in_interleaved ? "qj::ldp_inter" : "qj::ldp_planar";
     for (int i = 0; i < N; i += 2) {
       const uint32_t c = lay_eval(Li, K, dep(i));
-      const int k2 = i / 2;
-      if (packed) {
-        if (!bwd) {
-          o << "      " << LD << "(tile, si ^ " << c << "u, R[" << k2 << "], I[" << k2 << "]);\n";
-        } else {
-          o << "      " << LD << "(tp, si ^ " << c << "u, PR[" << k2 << "], PI[" << k2 << "]);\n";
-          o << "      " << LD << "(tl, si ^ " << c << "u, LR[" << k2 << "], LI[" << k2 << "]);\n";
-        }
-      } else if (!bwd) {
+      if (!bwd) {
         o << "      qj::ldp(tile, si ^ " << c << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
       } else {
         o << "      qj::ldp(tp, si ^ " << c << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
@@ -212,62 +195,56 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) 
     std::vector<int> order;
     for (int oi = P.op_begin; oi < P.op_end; oi++) order.push_back(oi);
     if (bwd) std::reverse(order.begin(), order.end());
-    const std::string NS = packed ? std::to_string(N2) : std::to_string(N);
-    const char* SFX = packed ? "2" : "";
     for (int oi : order) {
       const DevOp& op = s.ops[oi];
       const int li = oi - d.op0;
-      const std::string SA = std::to_string(1 << op.a), SB = std::to_string(1 << op.b);
-      const std::string C = "cf[" + std::to_string(li) + "], fm[" + std::to_string(li) + "]";
-      const std::string tbit_a = "((tb >> " + std::to_string(op.a) + ") & 1u)";
-      const std::string tbit_b = "((tb >> " + std::to_string(op.b) + ") & 1u)";
+      const int SA = 1 << op.a, SB = 1 << op.b;
+      std::string C = "cf[" + std::to_string(li) + "], fm[" + std::to_string(li) + "]";
       std::string call;
-      std::string g;   // gradient expression (backward, rotations)
-      const std::string GA = packed ? "(PR, PI, LR, LI)" : "(pr, pq, lr, lq)";
+      std::ostringstream g;   // gradient expression (backward, rotations)
       switch (op.kind) {
         case K_RY_R:
-          call = std::string(packed ? "qj::ry2<" : "qj::ry<") + NS + ", " + SA + ">(%R, %I, " + C + ");";
-          g = std::string(packed ? "qj::g2_ry<" : "qj::g_ry<") + NS + ", " + SA + ">" + GA;
+          call = "qj::ry<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
+          g << "qj::g_ry<" << N << ", " << SA << ">(pr, pq, lr, lq)";
           break;
         case K_RX_R:
-          call = std::string(packed ? "qj::rx2<" : "qj::rx<") + NS + ", " + SA + ">(%R, %I, " + C + ");";
-          g = std::string(packed ? "qj::g2_rx<" : "qj::g_rx<") + NS + ", " + SA + ">" + GA;
+          call = "qj::rx<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
+          g << "qj::g_rx<" << N << ", " << SA << ">(pr, pq, lr, lq)";
           break;
         case K_RZ_R:
-          call = std::string(packed ? "qj::rz2<" : "qj::rz<") + NS + ", " + SA + ">(%R, %I, " + C + ");";
-          g = std::string(packed ? "qj::g2_rz<" : "qj::g_rz<") + NS + ", " + SA + ">" + GA;
+          call = "qj::rz<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
+          g << "qj::g_rz<" << N << ", " << SA << ">(pr, pq, lr, lq)";
           break;
         case K_H_R:
-          call = std::string(packed ? "qj::hd2<" : "qj::hd<") + NS + ", " + SA + ">(%R, %I);";
+          call = "qj::hd<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I);";
           break;
         case K_X_R:
-          call = std::string(packed ? "qj::swp2<" : "qj::swp<") + NS + ", " + SA + ", 0>(%R, %I);";
+          call = "qj::swp<" + std::to_string(N) + ", " + std::to_string(SA) + ", 0>(%R, %I);";
           break;
         case K_RZ_T:
-          if (packed)
-            call = "qj::rz2_t<" + NS + ">(%R, %I, " + C + ", " + tbit_a + " ? -1.f : 1.f);";
-          else
-            call = "qj::rz_t<" + NS + ">(%R, %I, " + C + ", " + tbit_a + " ? T(-1) : T(1));";
-          g = "((" + tbit_a + " ? A(-1) : A(1)) * " + (packed ? "qj::g2_im<" : "qj::g_im<") + NS + ">" + GA + ")";
+          call = "qj::rz_t<" + std::to_string(N) + ">(%R, %I, " + C + ", ((tb >> " + std::to_string(op.a) +
+                 ") & 1u) ? T(-1) : T(1));";
+          g << "((((tb >> " << (int)op.a << ") & 1u) ? A(-1) : A(1)) * qj::g_im<" << N << ">(pr, pq, lr, lq))";
           break;
         case K_CNOT_RR:
-          call = std::string(packed ? "qj::swp2<" : "qj::swp<") + NS + ", " + SA + ", " + SB + ">(%R, %I);";
+          call = "qj::swp<" + std::to_string(N) + ", " + std::to_string(SA) + ", " + std::to_string(SB) + ">(%R, %I);";
           break;
         case K_CNOT_RT:
-          call = std::string(packed ? "qj::cnot2_t<" : "qj::cnot_t<") + NS + ", " + SA + ">(%R, %I, " + tbit_b + " != 0u);";
+          call = "qj::cnot_t<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, ((tb >> " +
+                 std::to_string(op.b) + ") & 1u) != 0u);";
           break;
         case K_CZ_RR:
-          call = std::string(packed ? "qj::cz2<" : "qj::cz<") + NS + ", " + SA + ", " + SB + ">(%R, %I);";
+          call = "qj::cz<" + std::to_string(N) + ", " + std::to_string(SA) + ", " + std::to_string(SB) + ">(%R, %I);";
           break;
         case K_CZ_RT:
-          call = std::string(packed ? "qj::cz2_t<" : "qj::cz_t<") + NS + ", " + SA + ">(%R, %I, " + tbit_b + " != 0u);";
+          call = "qj::cz_t<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, ((tb >> " +
+                 std::to_string(op.b) + ") & 1u) != 0u);";
           break;
         case K_CZ_TT:
-          call = "if (" + tbit_a + " && " + tbit_b + ") " + (packed ? "qj::scal2<" : "qj::scal<") + NS +
-                 ">(%R, %I, " + (packed ? "-1.f" : "T(-1)") + ");";
+          call = "if (((tb >> " + std::to_string(op.a) + ") & 1u) && ((tb >> " + std::to_string(op.b) +
+                 ") & 1u)) qj::scal<" + std::to_string(N) + ">(%R, %I, T(-1));";
           break;
       }
-      (void)SFX;
       auto inst = [&](const char* rr, const char* ii) {
         std::string c2 = call;
         size_t p;
@@ -276,28 +253,19 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) 
         return c2;
       };
       if (!bwd) {
-        o << "      " << inst(RE, IM) << "\n";
+        o << "      " << inst("re", "im") << "\n";
       } else {
         if (op.rot) {
-          o << "      { A g = " << g << "; g = qj::warp_sum<" << NTHR << ">(g); if (lane == 0u) red[warp * "
+          o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ">(g); if (lane == 0u) red[warp * "
             << (d.n_gslots > 0 ? d.n_gslots : 1) << " + " << op.gslot << "] = g; }\n";
         }
-        if (packed) o << "      " << inst("PR", "PI") << " " << inst("LR", "LI") << "\n";
-        else o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
+        o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
       }
     }
     o << "      __syncthreads();\n";
     for (int i = 0; i < N; i += 2) {
       const uint32_t c = lay_eval(Lo, K, dep(i));
-      const int k2 = i / 2;
-      if (packed) {
-        if (!bwd) {
-          o << "      qj::stp_planar(tile, so ^ " << c << "u, R[" << k2 << "], I[" << k2 << "]);\n";
-        } else {
-          o << "      qj::stp_planar(tp, so ^ " << c << "u, PR[" << k2 << "], PI[" << k2 << "]);\n";
-          o << "      qj::stp_planar(tl, so ^ " << c << "u, LR[" << k2 << "], LI[" << k2 << "]);\n";
-        }
-      } else if (!bwd) {
+      if (!bwd) {
         o << "      qj::stp(tile, so ^ " << c << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
       } else {
         o << "      qj::stp(tp, so ^ " << c << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";

@@ -258,289 +258,6 @@ __device__ __forceinline__ A warp_sum(A v) {
   return v;
 }
 
-// ---------------------------------------------------------------- packed complex64 gates
-// float2 SIMD across the two amplitudes that differ in register bit 0 (tile bit 0): R[k] = (re[2k], re[2k+1]),
-// I[k] = (im[2k], im[2k+1]). One __ffma2_rn updates two amplitudes. S is the element stride of the gate's
-// register bit; S == 1 is the packing bit itself (the two lanes of a vector are the pair).
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sw(float2 a) { return make_float2(a.y, a.x); }
-
-template <int N2, int S>
-__device__ __forceinline__ void ry2(float2* R, float2* I, float c, int f) {
-  if constexpr (S == 1) {
-    // pair inside each vector: (a, b) -> (a - t b, b + t a) or (u a - b, a + u b)
-    const float2 k1 = f == 0 ? f2(1.f, 1.f) : f2(c, c), k2 = f == 0 ? f2(-c, c) : f2(-1.f, 1.f);
-#pragma unroll
-    for (int k = 0; k < N2; k++) {
-      R[k] = fma2(k2, sw(R[k]), mul2(k1, R[k]));
-      I[k] = fma2(k2, sw(I[k]), mul2(k1, I[k]));
-    }
-  } else {
-    constexpr int S2 = S >> 1;
-    const float2 cc = f2(c, c), nc = f2(-c, -c), m1 = f2(-1.f, -1.f);
-#pragma unroll
-    for (int k = 0; k < N2; k++)
-      if (!(k & S2)) {
-        const int j = k | S2;
-        const float2 ar = R[k], ai = I[k], br = R[j], bi = I[j];
-        if (f == 0) {
-          R[k] = fma2(nc, br, ar); I[k] = fma2(nc, bi, ai);
-          R[j] = fma2(cc, ar, br); I[j] = fma2(cc, ai, bi);
-        } else {
-          R[k] = fma2(cc, ar, mul2(m1, br)); I[k] = fma2(cc, ai, mul2(m1, bi));
-          R[j] = fma2(cc, br, ar); I[j] = fma2(cc, bi, ai);
-        }
-      }
-  }
-}
-
-template <int N2, int S>
-__device__ __forceinline__ void rx2(float2* R, float2* I, float c, int f) {
-  if constexpr (S == 1) {
-    // a' = k1 a - i k2 b, b' = k1 b - i k2 a with (k1, k2) = (1, t) or (u, 1)
-    const float k1 = f == 0 ? 1.f : c, k2 = f == 0 ? c : 1.f;
-    const float2 kk = f2(k1, k1), pk = f2(k2, k2), nk = f2(-k2, -k2);
-#pragma unroll
-    for (int k = 0; k < N2; k++) {
-      const float2 r = R[k], m = I[k];
-      R[k] = fma2(pk, sw(m), mul2(kk, r));
-      I[k] = fma2(nk, sw(r), mul2(kk, m));
-    }
-  } else {
-    constexpr int S2 = S >> 1;
-    const float2 cc = f2(c, c), nc = f2(-c, -c), m1 = f2(-1.f, -1.f);
-#pragma unroll
-    for (int k = 0; k < N2; k++)
-      if (!(k & S2)) {
-        const int j = k | S2;
-        const float2 ar = R[k], ai = I[k], br = R[j], bi = I[j];
-        if (f == 0) {
-          R[k] = fma2(cc, bi, ar); I[k] = fma2(nc, br, ai);
-          R[j] = fma2(cc, ai, br); I[j] = fma2(nc, ar, bi);
-        } else {
-          R[k] = fma2(cc, ar, bi); I[k] = fma2(cc, ai, mul2(m1, br));
-          R[j] = fma2(cc, br, ai); I[j] = fma2(cc, bi, mul2(m1, ar));
-        }
-      }
-  }
-}
-
-template <int N2, int S>
-__device__ __forceinline__ void rz2(float2* R, float2* I, float c, int f) {
-  // per element (1 - i s c) [form 0] or (u - i s), s = +1 where the bit is 0
-  constexpr int S2 = S >> 1;
-#pragma unroll
-  for (int k = 0; k < N2; k++) {
-    float2 s;
-    if constexpr (S == 1) s = f2(1.f, -1.f);
-    else s = (k & S2) ? f2(-1.f, -1.f) : f2(1.f, 1.f);
-    const float2 r = R[k], m = I[k];
-    if (f == 0) {
-      const float2 cs = mul2(f2(c, c), s), ncs = mul2(f2(-c, -c), s);
-      R[k] = fma2(cs, m, r);
-      I[k] = fma2(ncs, r, m);
-    } else {
-      const float2 uu = f2(c, c), ns = mul2(f2(-1.f, -1.f), s);
-      R[k] = fma2(s, m, mul2(uu, r));
-      I[k] = fma2(ns, r, mul2(uu, m));
-    }
-  }
-}
-
-template <int N2>
-__device__ __forceinline__ void rz2_t(float2* R, float2* I, float c, int f, float sg) {
-  const float2 s = f2(sg, sg);
-#pragma unroll
-  for (int k = 0; k < N2; k++) {
-    const float2 r = R[k], m = I[k];
-    if (f == 0) {
-      const float2 cs = f2(sg * c, sg * c), ncs = f2(-sg * c, -sg * c);
-      R[k] = fma2(cs, m, r);
-      I[k] = fma2(ncs, r, m);
-    } else {
-      const float2 uu = f2(c, c), ns = f2(-sg, -sg);
-      R[k] = fma2(s, m, mul2(uu, r));
-      I[k] = fma2(ns, r, mul2(uu, m));
-    }
-  }
-}
-
-template <int N2, int S>
-__device__ __forceinline__ void hd2(float2* R, float2* I) {
-  if constexpr (S == 1) {
-    const float2 k = f2(1.f, -1.f);
-#pragma unroll
-    for (int q = 0; q < N2; q++) {
-      R[q] = fma2(k, R[q], sw(R[q]));   // (a + b, a - b) with lanes (a, b): (b + a, a - b)
-      I[q] = fma2(k, I[q], sw(I[q]));
-    }
-  } else {
-    constexpr int S2 = S >> 1;
-    const float2 m1 = f2(-1.f, -1.f);
-#pragma unroll
-    for (int k = 0; k < N2; k++)
-      if (!(k & S2)) {
-        const int j = k | S2;
-        const float2 ar = R[k], ai = I[k], br = R[j], bi = I[j];
-        R[k] = add2(ar, br); I[k] = add2(ai, bi);
-        R[j] = fma2(m1, br, ar); I[j] = fma2(m1, bi, ai);
-      }
-  }
-}
-
-// permutation: for elements with bit SB set (SB == 0: all), swap bit SA
-template <int N2, int SA, int SB>
-__device__ __forceinline__ void swp2(float2* R, float2* I) {
-  float re[2 * N2], im[2 * N2];
-#pragma unroll
-  for (int k = 0; k < N2; k++) { re[2 * k] = R[k].x; re[2 * k + 1] = R[k].y; im[2 * k] = I[k].x; im[2 * k + 1] = I[k].y; }
-#pragma unroll
-  for (int i = 0; i < 2 * N2; i++)
-    if ((i & SB) == SB && !(i & SA)) {
-      const int j = i | SA;
-      const float tr = re[i], ti = im[i];
-      re[i] = re[j]; im[i] = im[j];
-      re[j] = tr; im[j] = ti;
-    }
-#pragma unroll
-  for (int k = 0; k < N2; k++) { R[k] = f2(re[2 * k], re[2 * k + 1]); I[k] = f2(im[2 * k], im[2 * k + 1]); }
-}
-
-template <int N2, int SA>
-__device__ __forceinline__ void cnot2_t(float2* R, float2* I, bool ctl) {
-  if constexpr (SA == 1) {
-#pragma unroll
-    for (int k = 0; k < N2; k++) {
-      R[k] = ctl ? sw(R[k]) : R[k];
-      I[k] = ctl ? sw(I[k]) : I[k];
-    }
-  } else {
-    constexpr int S2 = SA >> 1;
-#pragma unroll
-    for (int k = 0; k < N2; k++)
-      if (!(k & S2)) {
-        const int j = k | S2;
-        const float2 ar = R[k], ai = I[k], br = R[j], bi = I[j];
-        R[k] = ctl ? br : ar; I[k] = ctl ? bi : ai;
-        R[j] = ctl ? ar : br; I[j] = ctl ? ai : bi;
-      }
-  }
-}
-
-template <int N2, int SA, int SB>
-__device__ __forceinline__ void cz2(float2* R, float2* I) {
-#pragma unroll
-  for (int k = 0; k < N2; k++) {
-    const int i0 = 2 * k, i1 = 2 * k + 1;
-    const float s0 = ((i0 & SA) && (i0 & SB)) ? -1.f : 1.f, s1 = ((i1 & SA) && (i1 & SB)) ? -1.f : 1.f;
-    if (s0 < 0.f || s1 < 0.f) { R[k] = mul2(f2(s0, s1), R[k]); I[k] = mul2(f2(s0, s1), I[k]); }
-  }
-}
-
-template <int N2, int SA>
-__device__ __forceinline__ void cz2_t(float2* R, float2* I, bool o) {
-  const float sg = o ? -1.f : 1.f;
-#pragma unroll
-  for (int k = 0; k < N2; k++) {
-    const int i0 = 2 * k, i1 = 2 * k + 1;
-    const float s0 = (i0 & SA) ? sg : 1.f, s1 = (i1 & SA) ? sg : 1.f;
-    if ((i0 & SA) || (i1 & SA)) { R[k] = mul2(f2(s0, s1), R[k]); I[k] = mul2(f2(s0, s1), I[k]); }
-  }
-}
-
-template <int N2>
-__device__ __forceinline__ void scal2(float2* R, float2* I, float s) {
-#pragma unroll
-  for (int k = 0; k < N2; k++) { R[k] = mul2(f2(s, s), R[k]); I[k] = mul2(f2(s, s), I[k]); }
-}
-
-// gradients: Im<lambda|P|psi> partial sums (before the gate is undone)
-template <int N2, int S>
-__device__ __forceinline__ float g2_ry(const float2* PR, const float2* PI, const float2* LR, const float2* LI) {
-  // sum over pairs of Re(l1* p0) - Re(l0* p1)
-  float2 gp = f2(0.f, 0.f), gn = f2(0.f, 0.f);
-  if constexpr (S == 1) {
-#pragma unroll
-    for (int k = 0; k < N2; k++) {   // lanes: x = element 0, y = element 1
-      gp = fma2(sw(LR[k]), PR[k], gp);   // (l1r p0r, l0r p1r)
-      gp = fma2(sw(LI[k]), PI[k], gp);
-    }
-    return gp.x - gp.y;
-  } else {
-    constexpr int S2 = S >> 1;
-#pragma unroll
-    for (int k = 0; k < N2; k++)
-      if (!(k & S2)) {
-        const int j = k | S2;
-        gp = fma2(LR[j], PR[k], gp); gp = fma2(LI[j], PI[k], gp);
-        gn = fma2(LR[k], PR[j], gn); gn = fma2(LI[k], PI[j], gn);
-      }
-    return (gp.x + gp.y) - (gn.x + gn.y);
-  }
-}
-
-template <int N2, int S>
-__device__ __forceinline__ float g2_rx(const float2* PR, const float2* PI, const float2* LR, const float2* LI) {
-  // sum over pairs of Im(l0* p1) + Im(l1* p0), Im(l* p) = lr pi - li pr
-  float2 gp = f2(0.f, 0.f), gn = f2(0.f, 0.f);
-  if constexpr (S == 1) {
-#pragma unroll
-    for (int k = 0; k < N2; k++) {
-      gp = fma2(LR[k], sw(PI[k]), gp);
-      gn = fma2(LI[k], sw(PR[k]), gn);
-    }
-  } else {
-    constexpr int S2 = S >> 1;
-#pragma unroll
-    for (int k = 0; k < N2; k++)
-      if (!(k & S2)) {
-        const int j = k | S2;
-        gp = fma2(LR[k], PI[j], gp); gp = fma2(LR[j], PI[k], gp);
-        gn = fma2(LI[k], PR[j], gn); gn = fma2(LI[j], PR[k], gn);
-      }
-  }
-  return (gp.x + gp.y) - (gn.x + gn.y);
-}
-
-template <int N2, int S>
-__device__ __forceinline__ float g2_rz(const float2* PR, const float2* PI, const float2* LR, const float2* LI) {
-  // sum over elements of s(e) Im(l* p)
-  float2 a0 = f2(0.f, 0.f), b0 = f2(0.f, 0.f), a1 = f2(0.f, 0.f), b1 = f2(0.f, 0.f);
-  constexpr int S2 = S >> 1;
-#pragma unroll
-  for (int k = 0; k < N2; k++) {
-    if (S != 1 && (k & S2)) { a1 = fma2(LR[k], PI[k], a1); b1 = fma2(LI[k], PR[k], b1); }
-    else { a0 = fma2(LR[k], PI[k], a0); b0 = fma2(LI[k], PR[k], b0); }
-  }
-  if constexpr (S == 1) return (a0.x - b0.x) - (a0.y - b0.y);
-  else return ((a0.x + a0.y) - (b0.x + b0.y)) - ((a1.x + a1.y) - (b1.x + b1.y));
-}
-
-template <int N2>
-__device__ __forceinline__ float g2_im(const float2* PR, const float2* PI, const float2* LR, const float2* LI) {
-  float2 a = f2(0.f, 0.f), b = f2(0.f, 0.f);
-#pragma unroll
-  for (int k = 0; k < N2; k++) { a = fma2(LR[k], PI[k], a); b = fma2(LI[k], PR[k], b); }
-  return (a.x + a.y) - (b.x + b.y);
-}
-
-// Pair-planar 16-byte words (re0, re1, im0, im1) inside phases; the load stage leaves interleaved
-// words (re0, im0, re1, im1) as they are in global memory.
-__device__ __forceinline__ void ldp_planar(const void* tile, u32 w, float2& R, float2& I) {
-  const float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
-  R = f2(v.x, v.y); I = f2(v.z, v.w);
-}
-__device__ __forceinline__ void ldp_inter(const void* tile, u32 w, float2& R, float2& I) {
-  const float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
-  R = f2(v.x, v.z); I = f2(v.y, v.w);
-}
-__device__ __forceinline__ void stp_planar(void* tile, u32 w, float2 R, float2 I) {
-  reinterpret_cast<float4*>(tile)[w >> 1] = make_float4(R.x, R.y, I.x, I.y);
-}
-
 // ---------------------------------------------------------------- pair access in shared memory
 __device__ __forceinline__ void ldp(const void* tile, u32 w, float& r0, float& i0, float& r1, float& i1) {
   const float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
@@ -662,9 +379,7 @@ struct FwdStore {
     const u32 w = s0 ^ Spec::lay_last(ChunkElem<I, G::LO, G::NB>::v);
     const i64 g = ch->template g<I>();
     if (G::EPC == 2) {
-      const float4 pw = reinterpret_cast<const float4*>(tile)[w >> 1];
-      // planar (r0, r1, i0, i1) after any register phase; interleaved if the pass has none
-      float4 v = Spec::PLANAR ? make_float4(pw.x, pw.z, pw.y, pw.w) : pw;
+      float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
       v.x *= (float)scale; v.y *= (float)scale; v.z *= (float)scale; v.w *= (float)scale;
       *reinterpret_cast<float4*>(out + 2 * g) = v;
       if (Z) {
@@ -751,6 +466,7 @@ __device__ __forceinline__ void fwd_pass(const Args& a) {
   }
   __syncthreads();
   Spec::template fwd_phases<T>(tile, cf, fmv, tid);
+  ch.init(a.L, tid);
   FwdStore<T, K, R, NTHR, Spec, true> st;
   st.out = reinterpret_cast<T*>(a.out) + 2 * base;
   st.tile = tile;
@@ -817,10 +533,8 @@ struct BwdStore {
     const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
     const i64 g = ch->template g<I>();
     if (G::EPC == 2) {
-      const float4 pv = reinterpret_cast<const float4*>(tp)[w >> 1];   // planar (r0, r1, i0, i1)
-      const float4 pl = reinterpret_cast<const float4*>(tl)[w >> 1];
-      float4 v = Spec::PLANAR ? make_float4(pv.x, pv.z, pv.y, pv.w) : pv;
-      float4 l = Spec::PLANAR ? make_float4(pl.x, pl.z, pl.y, pl.w) : pl;
+      float4 v = reinterpret_cast<const float4*>(tp)[w >> 1];
+      float4 l = reinterpret_cast<const float4*>(tl)[w >> 1];
       const float s = (float)scale;
       v.x *= s; v.y *= s; v.z *= s; v.w *= s;
       l.x *= s; l.y *= s; l.z *= s; l.w *= s;
@@ -898,6 +612,7 @@ __device__ __forceinline__ void bwd_pass(const Args& a) {
   }
   Spec::template bwd_phases<T>(tp, tl, cf, fmv, red, tid);
   __syncthreads();
+  ch.init(a.L, tid);
   for (int s = tid; s < Spec::NGS; s += NTHR) {
     double acc = 0.0;
 #pragma unroll
