@@ -164,6 +164,24 @@ int qsim_read_profile(qsim_plan_t plan, float* h_fwd_ms, float* h_bwd_ms, int32_
 /* Number of CUDA kernels this library has launched in the calling process so far. */
 int64_t qsim_kernel_launches(void);
 
+/* <Z_i>_b like qsim_expval_z, but allocating nothing: for callers that cannot call cudaMalloc, for
+ * example code whose device memory is entirely owned by another allocator (a framework that reserves
+ * the GPU's memory up front) or a steady-state loop that must not let a library call allocate, fail
+ * for lack of memory, or synchronise the device. The paper has no counterpart; this is an interface
+ * convenience of this library.
+ *   The partial sums go to one fixed device array inside the library (4 MiB: at most 524288 partial
+ *   sums, i.e. batch * 2^(n-12) * 13 <= 524288 for n >= 12, batch * (n+1) <= 524288 below). Larger
+ *   requests return QSIM_ERR_UNSUPPORTED and leave d_z untouched; use qsim_expval_z for them.
+ *   Every GPU that loads the library holds that array until the process exits.
+ *   The first call on each device looks up the array's device address (a one-time set-up with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents: calls that can overlap on the
+ *   GPU (other streams, other host threads) race and must be ordered by the caller. No entry of the
+ *   array has to start at zero (each call writes every partial it reads).
+ *   Arguments, layout and errors otherwise as qsim_expval_z. */
+int qsim_expval_z_noalloc(const void* d_states, int32_t batch, int32_t n_qubits, int32_t dtype, double* d_z,
+                          void* stream);
+
 /* Free the plan and its device workspace (synchronizes the plan's last stream). NULL is a no-op. */
 void qsim_plan_destroy(qsim_plan_t plan);
 

@@ -71,6 +71,8 @@ SIGNATURES = {
                                          ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "qsim_kernel_launches": (ctypes.c_int64, []),
+    "qsim_expval_z_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
     "qsim_plan_destroy": (None, [ctypes.c_void_p]),
     "qsim_last_error": (ctypes.c_char_p, []),
 }

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -698,6 +699,28 @@ int qsim_expval_z(const void* d_states, int32_t batch, int32_t n, int32_t dtype,
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return cuda_fail(e, "<Z> kernels");
   if (e2 != cudaSuccess) return cuda_fail(e2, "scratch free");
+  return QSIM_OK;
+}
+
+int qsim_expval_z_noalloc(const void* d_states, int32_t batch, int32_t n, int32_t dtype, double* d_z,
+                          void* stream) {
+  g_err.clear();
+  if (n < 1 || n > kMaxQubits) return fail(QSIM_ERR_UNSUPPORTED, "n_qubits outside [1, 34]");
+  if (batch < 0) return fail(QSIM_ERR_ARG, "batch < 0");
+  if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "bad dtype");
+  if (batch == 0) return QSIM_OK;
+  if (!d_states || !d_z) return fail(QSIM_ERR_ARG, "NULL buffer");
+  const int64_t need = z_partials_count(n, batch);
+  if (need > kNoAllocZPartials) {
+    char buf[256];
+    snprintf(buf, sizeof buf,
+             "batch %d x %d qubits needs %lld partial sums; the fixed scratch holds %lld "
+             "(at 12+ qubits: batch * 2^(n-12) <= 40329); use qsim_expval_z",
+             batch, n, (long long)need, (long long)kNoAllocZPartials);
+    return fail(QSIM_ERR_UNSUPPORTED, buf);
+  }
+  cudaError_t e = launch_expval_z_noalloc(d_states, n, batch, dtype, d_z, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "<Z> kernels (no-allocation variant)");
   return QSIM_OK;
 }
 

@@ -69,6 +69,11 @@ cudaError_t launch_pg_lambda_init(const void* states, void* psi, void* lam, cons
                                   int B, int dtype, cudaStream_t st);
 int pg_blocks_per_sample(int n);
 
+// ---- standalone <Z> with the partials in a fixed device array (no allocation); at most
+// kNoAllocZPartials partial sums, i.e. z_partials_count(n, B) <= kNoAllocZPartials
+constexpr int64_t kNoAllocZPartials = 524288;   // 4 MiB of doubles
+cudaError_t launch_expval_z_noalloc(const void* states, int n, int B, int dtype, double* z, cudaStream_t st);
+
 // ---- standalone <Z>: per-block partials + final reduction (scratch given by the caller)
 int64_t z_partials_count(int n, int B);   // doubles of scratch needed
 cudaError_t launch_expval_z(const void* states, int n, int B, int dtype, double* scratch, double* z,

@@ -1,6 +1,8 @@
 // Angle -> coefficient formation, and the deterministic FP64 reductions (<Z>, gradients).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "launch.hpp"
 
 namespace qsim {
@@ -232,6 +234,44 @@ __global__ void z_block_final_kernel(const double* part, int n, int zb, int B, d
 int64_t z_partials_count(int n, int B) {
   const int zb = n < kZBits ? n : kZBits;
   return (int64_t)B * ((int64_t)1 << (n - zb)) * (zb + 1);
+}
+
+cudaError_t launch_expval_z(const void* states, int n, int B, int dtype, double* scratch, double* z,
+                            cudaStream_t st);
+
+// ------------------------------------------------------------------ <Z> without allocation
+// Partial sums for callers that cannot allocate device memory live in this fixed array. It is part
+// of the library's device image, so every GPU that loads the library holds it until the process
+// exits. All calls share it: calls that overlap on the GPU (different streams, or different host
+// threads) race on it and must be serialised by the caller. Nothing in it has to start at zero: each
+// call writes every partial it later reads.
+static __device__ __align__(256) double g_noalloc_zpart[kNoAllocZPartials];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};   // per device: address of g_noalloc_zpart on that device
+}  // namespace
+
+cudaError_t launch_expval_z_noalloc(const void* states, int n, int B, int dtype, double* z, cudaStream_t st) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  void* ptr = nullptr;
+  {
+    // one-time set-up per device, with that device current: the host-side name of the array is
+    // not a device address, so its device address is looked up once and cached
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_zpart);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return e;
+      }
+    }
+    ptr = g_noalloc_ptr[dev];
+  }
+  return launch_expval_z(states, n, B, dtype, reinterpret_cast<double*>(ptr), z, st);
 }
 
 cudaError_t launch_expval_z(const void* states, int n, int B, int dtype, double* scratch, double* z,
