@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
     ap.add_argument("--k", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=64, help="samples (64 = the workload; smaller for ncu captures)")
     ap.add_argument("--contiguous-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -209,7 +210,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = W.config(3)
+    wl = W.config(3, batch=args.batch)
     plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=args.k, contiguous_bits=args.contiguous_bits)
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
