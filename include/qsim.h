@@ -73,8 +73,8 @@ typedef struct {
   int32_t contiguous_bits;   /* low index bits local in every pass (runs of 2^c amplitudes); 0 = default (4) */
   int32_t checkpoint_passes; /* >0: backward restarts psi from a stored forward state every this many passes;
                                 0: no checkpoints; -1: choose from mem_budget_bytes */
-  int32_t sample_block;      /* samples per L2-resident group: all passes run over one group of samples before the
-                                next (0 = choose from the L2 size, -1 = whole batch per pass) */
+  int32_t sample_block;      /* >0: samples per launch group; every pass runs over one group before the next
+                                group starts (keeps a group's states in L2); 0 = the whole batch per launch */
   int32_t bwd_reg_bits;      /* amplitudes per thread in backward phases = 2^bits (0 = default: 4 for complex64,
                                 3 for complex128); more bits mean fewer shared-memory round trips per pass */
   int32_t reserved;

@@ -125,15 +125,10 @@ struct qsim_plan_s {
   }
 
   int P() const { return (int)s.passes.size(); }
-  // samples per L2-resident group
+  // samples per launch group (all passes run over one group before the next); 0 = whole batch
   int group_size(int B_) const {
-    if (opts.sample_block > 0) return std::min(opts.sample_block, B_);
-    if (opts.sample_block < 0 || s.mode != QSIM_FUSED) return B_;
-    const int64_t per_sample = ((int64_t)1 << s.n) * el;
-    const int64_t budget = 48ll << 20;   // part of the 126 MB L2 kept for one group's working set
-    int64_t g = budget / (2 * per_sample);
-    if (g < 1) g = 1;
-    return (int)std::min<int64_t>(g, B_);
+    if (opts.sample_block > 0 && s.mode == QSIM_FUSED) return std::min(opts.sample_block, B_);
+    return B_ > 0 ? B_ : 1;
   }
   int64_t tps() const {
     return s.mode == QSIM_PER_GATE ? pg_blocks_per_sample(s.n) : s.passes.empty() ? 1 : s.passes[0].dev.tiles_per_sample;
@@ -398,9 +393,9 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
     if (o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   }
   p->opts = o;
-  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.sample_block < -1) {
+  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.sample_block < 0) {
     delete p;
-    return fail(QSIM_ERR_ARG, "bwd_reg_bits must be in [0, 5] and sample_block >= -1");
+    return fail(QSIM_ERR_ARG, "bwd_reg_bits must be in [0, 5] and sample_block >= 0");
   }
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
   rc = build_schedule(gv, n_qubits, o, fwd_R_for(16, o.dtype), Rb, p->s, err);
