@@ -194,7 +194,7 @@ def traffic_record(kernel):
     src = os.path.join(ROOT, "paper_2404_09213_gb300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h", ".hpp")):
+        if f.endswith((".cu", ".cuh", ".h", ".hpp", ".cpp")):
             h.update(open(os.path.join(src, f), "rb").read())
     if rec.get("source_sha256") != h.hexdigest():
         return None
