@@ -77,7 +77,8 @@ typedef struct {
                                 group starts (keeps a group's states in L2); 0 = the whole batch per launch */
   int32_t bwd_reg_bits;      /* amplitudes per thread in backward phases = 2^bits (0 = default: 4 for complex64,
                                 3 for complex128); more bits mean fewer shared-memory round trips per pass */
-  int32_t reserved;
+  int32_t graph;             /* multi-circuit plans: capture each direction's launch sequence in a CUDA graph and
+                                replay it while the caller's buffers are unchanged (0 = plain launches) */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
 } qsim_plan_opts;
 
@@ -181,6 +182,49 @@ int64_t qsim_kernel_launches(void);
  *   Arguments, layout and errors otherwise as qsim_expval_z. */
 int qsim_expval_z_noalloc(const void* d_states, int32_t batch, int32_t n_qubits, int32_t dtype, double* d_z,
                           void* stream);
+
+/* ------------------------------------------------------------------------------------------------
+ * Several circuits of uneven size in one persistent launch per direction (the batched training of
+ * many hybrid models; Section II-B's circuits, each planned as above).
+ *
+ * Every circuit gets its own k-local passes; a device work queue lists tile jobs in rounds (pass 0 of
+ * every circuit, then pass 1, ...). One persistent kernel per direction claims jobs with an atomic
+ * counter, waits until the previous pass of the same circuit is complete (a bounded wait: it gives
+ * up after a time limit and reports QSIM_ERR_TIMEOUT through qsim_multi_sync_status), runs the job's
+ * specialised pass code and signals completion. Circuits have up to 30 qubits; every circuit uses
+ * the same batch size B; initial states are |0...0>.
+ *
+ * Buffers are the per-circuit blocks concatenated in circuit order (offsets: qsim_multi_offsets):
+ *   params (sum P_c) float32/float64 | inputs: circuit c's (B, n_inputs_c) block | states: circuit c's
+ *   (B, 2^n_c) complex block | z, grad_out: circuit c's (B, n_c) float64 block | dparams, dinputs as
+ *   params, inputs (float64). */
+typedef struct qsim_multi_s* qsim_multi_t;
+
+int qsim_multi_plan(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
+                    int32_t n_circuits, const qsim_plan_opts* opts, qsim_multi_t* out);
+
+/* Element offsets of every circuit's block for batch size `batch`; each array (n_circuits + 1
+ * entries, the last = total) may be NULL. */
+int qsim_multi_offsets(qsim_multi_t plan, int32_t batch, int64_t* h_param_off, int64_t* h_input_off,
+                       int64_t* h_state_off, int64_t* h_z_off);
+
+int qsim_multi_forward(qsim_multi_t plan, const void* d_params, const void* d_inputs, int32_t batch,
+                       void* d_states, double* d_z, void* stream);
+int qsim_multi_backward(qsim_multi_t plan, const double* d_grad_out, double* d_dparams, double* d_dinputs,
+                        void* stream);
+
+/* Synchronize the last stream; QSIM_OK or QSIM_ERR_TIMEOUT if a queue wait gave up (status cleared). */
+int qsim_multi_sync_status(qsim_multi_t plan);
+
+/* Queue statistics: circuits, work items per direction, distinct specialised pass codes per direction. */
+int qsim_multi_info(qsim_multi_t plan, int32_t* n_circuits, int64_t* n_items_fwd, int64_t* n_items_bwd,
+                    int32_t* n_kernels_fwd, int32_t* n_kernels_bwd);
+
+/* Test hook for the bounded waits: the completion of queue item `withhold_item` (-1 = none) is never
+ * signalled, and waits give up after timeout_ns (<= 0: the default of 4 s). */
+int qsim_multi_set_test_hooks(qsim_multi_t plan, int64_t withhold_item, int64_t timeout_ns);
+
+void qsim_multi_destroy(qsim_multi_t plan);
 
 /* Free the plan and its device workspace (synchronizes the plan's last stream). NULL is a no-op. */
 void qsim_plan_destroy(qsim_plan_t plan);

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import QsimError, QSIM_C64, QSIM_C128, QSIM_FUSED, QSIM_PER_GATE  # noqa: F401
 
-__all__ = ["Plan", "QSimFunction", "QSimLayer", "expval_z", "QsimError", "gate_structs"]
+__all__ = ["Plan", "MultiPlan", "QSimFunction", "QSimLayer", "expval_z", "QsimError", "gate_structs"]
 
 _DT = {"c64": (QSIM_C64, torch.complex64, torch.float32), "c128": (QSIM_C128, torch.complex128, torch.float64)}
 
@@ -193,6 +193,87 @@ class Plan:
         t = t.contiguous()
         assert tuple(t.shape) == tuple(shape), (t.shape, shape)
         return t
+
+
+class MultiPlan:
+    """Several circuits run together (``qsim_multi_plan``): one persistent launch per direction.
+
+    ``circuits`` is a list of ``(gates, n_qubits)``. Buffers are the per-circuit blocks concatenated
+    in circuit order; :meth:`offsets` gives the element offsets of every block for a batch size.
+    """
+
+    def __init__(self, circuits, *, dtype="c64", k=0, graph=False):
+        L = _lib.lib()
+        self.circuits = [(list(g), int(n)) for g, n in circuits]
+        self.dtype = dtype
+        self._code, self.cdtype, self.rdtype = _DT[dtype]
+        C = len(self.circuits)
+        arrs = [gate_structs(g) for g, _ in self.circuits]
+        lists = (ctypes.POINTER(_lib.QsimGate) * C)(*[ctypes.cast(a, ctypes.POINTER(_lib.QsimGate)) for a in arrs])
+        ng = (ctypes.c_int32 * C)(*[len(g) for g, _ in self.circuits])
+        nq = (ctypes.c_int32 * C)(*[n for _, n in self.circuits])
+        opts = _lib.QsimPlanOpts()
+        L.qsim_default_opts(ctypes.byref(opts))
+        opts.k = k
+        opts.dtype = self._code
+        opts.graph = 1 if graph else 0
+        h = ctypes.c_void_p()
+        _lib.check(L.qsim_multi_plan(lists, ng, nq, C, ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self._keep = arrs
+        self._saved = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                _lib.lib().qsim_multi_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def offsets(self, batch):
+        C = len(self.circuits)
+        arrs = [np.zeros(C + 1, dtype=np.int64) for _ in range(4)]
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)) for a in arrs]
+        _lib.check(_lib.lib().qsim_multi_offsets(self._h, batch, *ptrs))
+        return dict(zip(("params", "inputs", "states", "z"), arrs))
+
+    def info(self):
+        vals = [ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()]
+        _lib.check(_lib.lib().qsim_multi_info(self._h, *[ctypes.byref(v) for v in vals]))
+        return dict(zip(("n_circuits", "items_fwd", "items_bwd", "kernels_fwd", "kernels_bwd"), [v.value for v in vals]))
+
+    def forward(self, params, inputs, batch, states=None, z=None, stream=None):
+        off = self.offsets(batch)
+        dev = params.device if params is not None and params.numel() else inputs.device
+        params = params.to(self.rdtype).contiguous() if params is not None and params.numel() else None
+        inputs = inputs.to(self.rdtype).contiguous() if inputs is not None and inputs.numel() else None
+        if states is None:
+            states = torch.empty(int(off["states"][-1]), dtype=self.cdtype, device=dev)
+        if z is None:
+            z = torch.empty(int(off["z"][-1]), dtype=torch.float64, device=dev)
+        _lib.check(_lib.lib().qsim_multi_forward(self._h, _ptr(params), _ptr(inputs), batch, _ptr(states), _ptr(z),
+                                                 _stream(stream)))
+        self._saved = (params, inputs, states, batch, off)
+        return states, z
+
+    def backward(self, grad_z, dparams=None, dinputs=None, stream=None):
+        params, inputs, states, batch, off = self._saved
+        grad_z = grad_z.to(torch.float64).contiguous()
+        if dparams is None:
+            dparams = torch.zeros(int(off["params"][-1]), dtype=torch.float64, device=states.device)
+        if dinputs is None:
+            dinputs = torch.zeros(int(off["inputs"][-1]), dtype=torch.float64, device=states.device)
+        _lib.check(_lib.lib().qsim_multi_backward(self._h, _ptr(grad_z), _ptr(dparams) if dparams.numel() else None,
+                                                  _ptr(dinputs) if dinputs.numel() else None, _stream(stream)))
+        return dparams, dinputs
+
+    def sync_status(self):
+        return _lib.lib().qsim_multi_sync_status(self._h)
+
+    def set_test_hooks(self, withhold_item=-1, timeout_ns=0):
+        _lib.check(_lib.lib().qsim_multi_set_test_hooks(self._h, withhold_item, timeout_ns))
 
 
 def kernel_launches():

@@ -28,7 +28,7 @@ class QsimPlanOpts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("dtype", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("contiguous_bits", ctypes.c_int32), ("checkpoint_passes", ctypes.c_int32),
                 ("sample_block", ctypes.c_int32), ("bwd_reg_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64)]
+                ("graph", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64)]
 
 
 class QsimPlanInfo(ctypes.Structure):
@@ -73,6 +73,19 @@ SIGNATURES = {
     "qsim_kernel_launches": (ctypes.c_int64, []),
     "qsim_expval_z_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_void_p, ctypes.c_void_p]),
+    "qsim_multi_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.POINTER(QsimGate)), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
+                                       ctypes.POINTER(ctypes.c_void_p)]),
+    "qsim_multi_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int64)] * 4),
+    "qsim_multi_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "qsim_multi_backward": (ctypes.c_int, [ctypes.c_void_p] * 5),
+    "qsim_multi_sync_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "qsim_multi_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    "qsim_multi_set_test_hooks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    "qsim_multi_destroy": (None, [ctypes.c_void_p]),
     "qsim_plan_destroy": (None, [ctypes.c_void_p]),
     "qsim_last_error": (ctypes.c_char_p, []),
 }

@@ -37,6 +37,10 @@ cudaError_t upload(T** dptr, const std::vector<T>& v) {
 }
 }  // namespace
 
+namespace qsim {
+void set_last_error(const std::string& s) { g_err = s; }
+}  // namespace qsim
+
 struct qsim_plan_s {
   Schedule s;
   qsim_plan_opts opts{};

@@ -82,6 +82,55 @@ Nvrtc& nvrtc() {
   return n;
 }
 
+typedef struct nvJitLink* nvJitLinkHandle_t;
+struct JitLinker {
+  void* h = nullptr;
+  int (*create)(nvJitLinkHandle_t*, uint32_t, const char**) = nullptr;
+  int (*destroy)(nvJitLinkHandle_t*) = nullptr;
+  int (*add_data)(nvJitLinkHandle_t, int, const void*, size_t, const char*) = nullptr;
+  int (*complete)(nvJitLinkHandle_t) = nullptr;
+  int (*cubin_size)(nvJitLinkHandle_t, size_t*) = nullptr;
+  int (*cubin)(nvJitLinkHandle_t, void*) = nullptr;
+  int (*err_size)(nvJitLinkHandle_t, size_t*) = nullptr;
+  int (*err_log)(nvJitLinkHandle_t, char*) = nullptr;
+  std::string error;
+};
+
+JitLinker& jitlink() {
+  static JitLinker n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    std::vector<std::string> cand = {"libnvJitLink.so.13", "libnvJitLink.so"};
+    if (const char* ch = getenv("CUDA_HOME")) cand.push_back(std::string(ch) + "/lib64/libnvJitLink.so.13");
+    cand.push_back("/usr/local/cuda/lib64/libnvJitLink.so.13");
+    for (auto& c : cand) {
+      n.h = dlopen(c.c_str(), RTLD_NOW | RTLD_LOCAL);
+      if (n.h) break;
+    }
+    if (!n.h) {
+      n.error = "cannot load libnvJitLink (set CUDA_HOME)";
+      return;
+    }
+#define QSIM_SYM(F, NAME)                                                       \
+  n.F = reinterpret_cast<decltype(n.F)>(dlsym(n.h, NAME));                     \
+  if (!n.F) {                                                                  \
+    n.error = std::string("libnvJitLink lacks ") + NAME;                       \
+    n.h = nullptr;                                                             \
+    return;                                                                    \
+  }
+    QSIM_SYM(create, "__nvJitLinkCreate_13_0")
+    QSIM_SYM(destroy, "__nvJitLinkDestroy_13_0")
+    QSIM_SYM(add_data, "__nvJitLinkAddData_13_0")
+    QSIM_SYM(complete, "__nvJitLinkComplete_13_0")
+    QSIM_SYM(cubin_size, "__nvJitLinkGetLinkedCubinSize_13_0")
+    QSIM_SYM(cubin, "__nvJitLinkGetLinkedCubin_13_0")
+    QSIM_SYM(err_size, "__nvJitLinkGetErrorLogSize_13_0")
+    QSIM_SYM(err_log, "__nvJitLinkGetErrorLog_13_0")
+#undef QSIM_SYM
+  });
+  return n;
+}
+
 uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ULL) {
   for (unsigned char c : s) {
     h ^= c;
@@ -147,9 +196,10 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 }  // namespace
 
 // ------------------------------------------------------------------ generation
-static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) {
+static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0) {
   const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
   std::ostringstream o;
+  o << "  static constexpr int CTA = " << (cta > 0 ? cta : NTHR) << ";\n";
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
   for (int i = 0; i <= d.n_phases; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
@@ -256,7 +306,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd) 
         o << "      " << inst("re", "im") << "\n";
       } else {
         if (op.rot) {
-          o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ">(g); if (lane == 0u) red[warp * "
+          o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ", A, CTA>(g); if (lane == 0u) red[warp * "
             << (d.n_gslots > 0 ? d.n_gslots : 1) << " + " << op.gslot << "] = g; }\n";
         }
         o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
@@ -284,14 +334,18 @@ int fwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 4 : 5; retu
 int bwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 3 : 4; return k < r ? k : r; }
 int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
 
+// Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
 size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
-  const size_t nops = d.n_ops > 0 ? d.n_ops : 1;
-  if (!bwd) return ((tile + nops * sc + d.n_ops) + 15) & ~(size_t)15;
+  const size_t no = d.n_ops > 0 ? d.n_ops : 1;
+  if (!bwd) return (tile + no * sc + no + 15) & ~(size_t)15;
   const int nthr = 1 << (d.k - d.R);
   const size_t nw = (nthr + 31) / 32, ng = d.n_gslots > 0 ? d.n_gslots : 1;
-  size_t red = nw * ng + (nw * ng) % 2 + 2;
-  return ((2 * tile + red * sc + (d.k + 2) * 8 + nops * sc + d.n_ops) + 15) & ~(size_t)15;
+  const size_t red = 2 * tile;
+  const size_t gq = (red + nw * ng * sc + 15) & ~(size_t)15;
+  const size_t cf = gq + (d.k + 2) * 8;
+  const size_t fm = cf + no * sc;
+  return (fm + no + 15) & ~(size_t)15;
 }
 
 // One NVRTC unit per distinct kernel: name -> source (device header + Spec + entry point).
@@ -330,7 +384,7 @@ std::string jit_generate(const Schedule& s, std::vector<std::string>& fnames, st
   return prog.str();
 }
 
-static int nvrtc_compile_unit(const std::string& src, std::string& cubin, std::string& err) {
+static int nvrtc_compile_unit(const std::string& src, std::string& cubin, std::string& err, bool rdc = false) {
   Nvrtc& nv = nvrtc();
   if (!nv.h) {
     err = nv.error;
@@ -341,8 +395,8 @@ static int nvrtc_compile_unit(const std::string& src, std::string& cubin, std::s
     err = "nvrtcCreateProgram failed";
     return QSIM_ERR_UNSUPPORTED;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--fmad=true"};
-  const int rc = nv.compile(prog, 4, opts);
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--fmad=true", "-rdc=true"};
+  const int rc = nv.compile(prog, rdc ? 5 : 4, opts);
   size_t ls = 0;
   nv.log_size(prog, &ls);
   std::string log(ls, '\0');
@@ -447,6 +501,224 @@ int jit_build(const Schedule& s, JitPlan& jp, std::string& err) {
     }
   }
   return QSIM_OK;
+}
+
+// ------------------------------------------------------------------ multi-circuit queue kernels
+static std::string multi_unit(const Schedule& s, const DevPass& d, bool bwd, int cta, std::string& name) {
+  const char* T = s.dtype == QSIM_C128 ? "double" : "float";
+  const int K = d.k, R = d.R, NTHR = 1 << (K - R);
+  std::string body = gen_spec_body(s, d, bwd, cta);
+  std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" + body;
+  name = std::string(bwd ? "qsb_" : "qsf_") + hex64(fnv1a(key));
+  std::ostringstream u;
+  u << "struct S_" << name << " {\n" << body << "};\n";
+  u << "extern \"C\" __device__ void " << name
+    << "(const qj::Args* a, long long tile0, long long ntiles, unsigned char* smem) {\n"
+    << "  constexpr int NTHR = " << NTHR << ";\n"
+    << "  const unsigned g = threadIdx.x / NTHR, tid = threadIdx.x % NTHR;\n"
+    << "  const long long ti = tile0 + g;\n"
+    << "  const bool valid = ti < ntiles;\n";
+  if (!bwd)
+    u << "  constexpr int GB = qj::FwdGroupSmem<" << T << ", " << K << ", S_" << name << "::NOPS>::BYTES;\n"
+      << "  qj::fwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
+      << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
+  else
+    u << "  constexpr int GB = qj::BwdGroupSmem<" << T << ", " << K << ", " << R << ", NTHR, S_" << name << "::NOPS, S_"
+      << name << "::NGS>::BYTES;\n"
+      << "  qj::bwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
+      << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
+  u << "}\n";
+  return u.str();
+}
+
+static std::string queue_kernel_unit(const std::vector<std::string>& kinds, bool bwd, int cta, std::string& kname) {
+  std::ostringstream u;
+  std::string all;
+  for (auto& k : kinds) all += k + ",";
+  kname = std::string(bwd ? "qsim_queue_bwd_" : "qsim_queue_fwd_") + hex64(fnv1a(all + std::to_string(cta)));
+  for (auto& k : kinds)
+    u << "extern \"C\" __device__ void " << k << "(const qj::Args*, long long, long long, unsigned char*);\n";
+  u << "extern \"C\" __global__ void __launch_bounds__(" << cta << ") " << kname << "(const qj::MultiArgs m) {\n"
+    << "  extern __shared__ __align__(16) unsigned char smem[];\n"
+    << "  __shared__ long long s_item;\n"
+    << "  __shared__ int s_run;\n"
+    << "  for (;;) {\n"
+    << "    __syncthreads();\n"
+    << "    if (threadIdx.x == 0) s_item = (long long)atomicAdd(m.head, 1ull);\n"
+    << "    __syncthreads();\n"
+    << "    const long long it = s_item;\n"
+    << "    if (it >= m.n_items) break;\n"
+    << "    const qj::Item item = m.items[it];\n"
+    << "    if (threadIdx.x == 0) s_run = qj::wait_dependency(m, item) ? 1 : 0;\n"
+    << "    __syncthreads();\n"
+    << "    if (s_run) {\n"
+    << "      switch (item.kind) {\n";
+  for (size_t i = 0; i < kinds.size(); i++)
+    u << "        case " << i << ": " << kinds[i] << "(m.args + item.arg, item.tile0, item.ntiles, smem); break;\n";
+  u << "        default: break;\n"
+    << "      }\n"
+    << "    }\n"
+    << "    __syncthreads();\n"
+    << "    if (threadIdx.x == 0) {\n"
+    << "      __threadfence();\n"
+    << "      if (it != m.withhold) atomicAdd(m.counters + item.done, 1);\n"
+    << "    }\n"
+    << "  }\n"
+    << "}\n";
+  return u.str();
+}
+
+int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int cta_b, JitMulti& jm,
+                    std::string& err) {
+  JitLinker& jl = jitlink();
+  Nvrtc& nv = nvrtc();
+  if (!jl.h) {
+    err = jl.error;
+    return QSIM_ERR_UNSUPPORTED;
+  }
+  int maj = 0, min = 0;
+  if (nv.h) nv.version(&maj, &min);
+  const std::string tag = "_rdc_sm103a_" + std::to_string(maj) + "." + std::to_string(min) + "_" +
+                          hex64(fnv1a(kJitDeviceSource)).substr(0, 8);
+  const std::string dir = cache_dir();
+  std::map<std::string, std::string> units[2];   // name -> source (per direction)
+  std::vector<std::string> kinds[2];
+  std::map<std::string, int> kind_id[2];
+  jm.kind.assign(scheds.size(), {});
+  jm.smem_group[0].clear();
+  jm.smem_group[1].clear();
+  size_t max_smem[2] = {0, 0};
+  for (size_t c = 0; c < scheds.size(); c++) {
+    const Schedule& s = *scheds[c];
+    jm.kind[c].resize(2 * s.passes.size());
+    for (size_t p = 0; p < s.passes.size(); p++) {
+      for (int dir = 0; dir < 2; dir++) {
+        const DevPass& d = dir == 0 ? s.passes[p].dev : s.passes[p].devb;
+        const int cta = dir == 0 ? cta_f : cta_b;
+        std::string name;
+        std::string src = multi_unit(s, d, dir == 1, cta, name);
+        if (!kind_id[dir].count(name)) {
+          kind_id[dir][name] = (int)kinds[dir].size();
+          kinds[dir].push_back(name);
+          units[dir][name] = src;
+        }
+        jm.kind[c][2 * p + dir] = kind_id[dir][name];
+        const int nthr = 1 << (d.k - d.R);
+        const size_t groups = (size_t)cta / nthr;
+        max_smem[dir] = std::max(max_smem[dir], groups * jit_smem_bytes(d, s.dtype, dir == 1));
+      }
+    }
+  }
+  // compile every unit (relocatable) in parallel, cached
+  std::vector<std::pair<std::string, std::string>> todo;   // name, source
+  std::map<std::string, std::string> bins;
+  std::string qnames[2];
+  for (int dir = 0; dir < 2; dir++) {
+    for (auto& kv : units[dir]) todo.push_back(kv);
+    std::string qn;
+    std::string qsrc = queue_kernel_unit(kinds[dir], dir == 1, dir == 0 ? cta_f : cta_b, qn);
+    qnames[dir] = qn;
+    todo.push_back({qn, qsrc});
+  }
+  std::vector<std::string> need;
+  for (auto& t : todo) {
+    std::string b;
+    if (read_file(dir + "/" + t.first + tag + ".cubin", b)) bins[t.first] = b;
+    else need.push_back(t.first);
+  }
+  std::map<std::string, std::string> srcs(todo.begin(), todo.end());
+  if (!need.empty()) {
+    std::vector<std::string> out(need.size()), errs(need.size());
+    std::vector<int> rcs(need.size(), 0);
+    std::atomic<size_t> next{0};
+    auto worker = [&]() {
+      for (size_t i = next++; i < need.size(); i = next++)
+        rcs[i] = nvrtc_compile_unit(std::string(kJitDeviceSource) + "\n" + srcs[need[i]], out[i], errs[i], true);
+    };
+    unsigned nt = std::thread::hardware_concurrency();
+    if (nt == 0) nt = 4;
+    nt = std::min<unsigned>(nt, (unsigned)need.size());
+    std::vector<std::thread> pool;
+    for (unsigned t = 0; t < nt; t++) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    for (size_t i = 0; i < need.size(); i++) {
+      if (rcs[i]) {
+        err = errs[i];
+        return rcs[i];
+      }
+      bins[need[i]] = out[i];
+      write_file_atomic(dir, dir + "/" + need[i] + tag + ".cubin", out[i]);
+    }
+  }
+  // link each direction's queue kernel with its pass functions
+  for (int dir = 0; dir < 2; dir++) {
+    nvJitLinkHandle_t h = nullptr;
+    const char* lopts[] = {"-arch=sm_103a"};
+    if (jl.create(&h, 1, lopts) != 0) {
+      err = "nvJitLinkCreate failed";
+      return QSIM_ERR_UNSUPPORTED;
+    }
+    bool ok = true;
+    for (auto& k : kinds[dir]) ok = ok && jl.add_data(h, 1 /*CUBIN*/, bins[k].data(), bins[k].size(), k.c_str()) == 0;
+    ok = ok && jl.add_data(h, 1, bins[qnames[dir]].data(), bins[qnames[dir]].size(), qnames[dir].c_str()) == 0;
+    ok = ok && jl.complete(h) == 0;
+    if (!ok) {
+      size_t es = 0;
+      jl.err_size(h, &es);
+      std::string log(es, '\0');
+      if (es) jl.err_log(h, &log[0]);
+      jl.destroy(&h);
+      err = "nvJitLink failed: " + log.substr(0, 4000);
+      return QSIM_ERR_UNSUPPORTED;
+    }
+    size_t cs = 0;
+    jl.cubin_size(h, &cs);
+    std::string linked(cs, '\0');
+    jl.cubin(h, &linked[0]);
+    jl.destroy(&h);
+    cudaLibrary_t lib = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, linked.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e != cudaSuccess) {
+      err = std::string("loading the queue kernel: ") + cudaGetErrorString(e);
+      return QSIM_ERR_CUDA;
+    }
+    jm.libs.push_back(lib);
+    cudaKernel_t k = nullptr;
+    e = cudaLibraryGetKernel(&k, lib, qnames[dir].c_str());
+    if (e != cudaSuccess) {
+      err = std::string("queue kernel missing: ") + cudaGetErrorString(e);
+      return QSIM_ERR_CUDA;
+    }
+    JitKernel& jk = dir == 0 ? jm.fwd : jm.bwd;
+    jk.fn = reinterpret_cast<void*>(k);
+    jk.nthr = dir == 0 ? cta_f : cta_b;
+    jk.smem = max_smem[dir];
+    if (jk.smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)jk.smem);
+      if (e != cudaSuccess) {
+        err = std::string("queue kernel shared memory (") + std::to_string(jk.smem) + " B): " + cudaGetErrorString(e);
+        return QSIM_ERR_UNSUPPORTED;
+      }
+    }
+    int per_sm = 0, devi = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(k), jk.nthr, jk.smem);
+    if (e != cudaSuccess || per_sm < 1) {
+      err = "queue kernel cannot be resident";
+      return QSIM_ERR_UNSUPPORTED;
+    }
+    cudaGetDevice(&devi);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devi);
+    jk.max_blocks = (int64_t)per_sm * sms;   // persistent grid: every block resident at once
+  }
+  jm.n_kinds[0] = (int)kinds[0].size();
+  jm.n_kinds[1] = (int)kinds[1].size();
+  return QSIM_OK;
+}
+
+void jit_free_multi(JitMulti& jm) {
+  for (auto l : jm.libs) cudaLibraryUnload(l);
+  jm.libs.clear();
 }
 
 void jit_free(JitPlan& jp) {

@@ -35,6 +35,7 @@ struct JitKernel {
   void* fn = nullptr;   // cudaKernel_t
   size_t smem = 0;
   int nthr = 0;
+  int64_t max_blocks = 0;   // resident blocks (persistent queue kernels only)
 };
 
 struct JitPlan {
@@ -45,6 +46,17 @@ struct JitPlan {
 int fwd_R_for(int k, int dtype);
 int bwd_R_for(int k, int dtype);
 int max_k_for(int dtype);
+
+// Persistent multi-circuit queue kernels (one per direction) linked from relocatable pass functions.
+struct JitMulti {
+  JitKernel fwd, bwd;                       // max_blocks = resident blocks (persistent grid)
+  std::vector<std::vector<int>> kind;       // [circuit][2*pass + dir] -> switch case
+  std::vector<size_t> smem_group[2];
+  int n_kinds[2] = {0, 0};
+  std::vector<cudaLibrary_t> libs;
+};
+int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int cta_b, JitMulti& jm, std::string& err);
+void jit_free_multi(JitMulti& jm);
 
 // Full NVRTC program text and the kernel name of every pass (forward, backward).
 std::string jit_generate(const Schedule& s, std::vector<std::string>& fwd_names, std::vector<std::string>& bwd_names);

@@ -250,9 +250,11 @@ __device__ __forceinline__ typename Acc<T>::t g_im(const T* pr, const T* pi, con
   return g;
 }
 
-template <int NTHR, typename A>
+// Sum over the NTHR threads of a tile group. Groups are aligned blocks of NTHR lanes; when several
+// groups share a warp (CTA >= 32) every lane takes part, and xor offsets below NTHR stay inside a group.
+template <int NTHR, typename A, int CTA = NTHR>
 __device__ __forceinline__ A warp_sum(A v) {
-  constexpr unsigned mask = NTHR >= 32 ? 0xffffffffu : ((1u << NTHR) - 1u);
+  constexpr unsigned mask = CTA >= 32 ? 0xffffffffu : ((1u << CTA) - 1u);
 #pragma unroll
   for (int off = (NTHR >= 32 ? 16 : NTHR / 2); off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
   return v;
@@ -372,7 +374,7 @@ template <typename T, int K, int R, int NTHR, class Spec, bool Z>
 struct FwdStore {
   typedef Geo<T, K, R, NTHR> G;
   typedef typename Acc<T>::t A;
-  T* out; const void* tile; const Chunks<T, K, R, NTHR>* ch; u32 s0; T scale;
+  T* out; const void* tile; const Chunks<T, K, R, NTHR>* ch; u32 s0; T scale; bool valid;
   A zt; A zs[G::NB + 1];
   template <int I>
   __device__ __forceinline__ void step() {
@@ -381,7 +383,7 @@ struct FwdStore {
     if (G::EPC == 2) {
       float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
       v.x *= (float)scale; v.y *= (float)scale; v.z *= (float)scale; v.w *= (float)scale;
-      *reinterpret_cast<float4*>(out + 2 * g) = v;
+      if (valid) *reinterpret_cast<float4*>(out + 2 * g) = v;
       if (Z) {
         const A p0 = fm((A)v.x, (A)v.x, (A)v.y * (A)v.y), p1 = fm((A)v.z, (A)v.z, (A)v.w * (A)v.w);
         zt += p0 + p1;
@@ -392,7 +394,7 @@ struct FwdStore {
     } else {
       double2 v = reinterpret_cast<const double2*>(tile)[w];
       v.x *= (double)scale; v.y *= (double)scale;
-      *reinterpret_cast<double2*>(out + 2 * g) = v;
+      if (valid) *reinterpret_cast<double2*>(out + 2 * g) = v;
       if (Z) {
         const A p = (A)(v.x * v.x + v.y * v.y);
         zt += p;
@@ -406,12 +408,11 @@ struct FwdStore {
 // Block reduction of the <Z> partials into zpart[tile][0..K] (tile bit j signed sums, K = total).
 template <typename T, int K, int R, int NTHR>
 __device__ __forceinline__ void z_reduce(void* smem, const typename Acc<T>::t zt, const typename Acc<T>::t* zs,
-                                         double* zrow) {
+                                         double* zrow, u32 tid, bool valid) {
   typedef Geo<T, K, R, NTHR> G;
   typedef typename Acc<T>::t A;
   constexpr int NZ = G::NB + 2;
   A* red = reinterpret_cast<A*>(smem);
-  const u32 tid = threadIdx.x;
   __syncthreads();
   red[tid * NZ] = zt;
 #pragma unroll
@@ -429,21 +430,32 @@ __device__ __forceinline__ void z_reduce(void* smem, const typename Acc<T>::t zt
       const int slot = (G::EPC == 2 && j == 0) ? 0 : (G::EPC == 2 ? 1 : 0) + (j - G::LO);
       for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ + 1 + slot];
     }
-    zrow[j] = acc;
+    if (valid) zrow[j] = acc;
   }
 }
 
+// Shared-memory bytes of one tile group (forward): tile, then coefficients and forms.
+template <typename T, int K, int NOPS>
+struct FwdGroupSmem {
+  static constexpr int NO = NOPS > 0 ? NOPS : 1;
+  static constexpr int TILE = (2 * (int)sizeof(T)) << K;
+  static constexpr int BYTES = (TILE + NO * (int)sizeof(T) + NO + 15) & ~15;
+};
+
+// One tile: tile index `tile` (sample = b0 + tile / tps) processed by the NTHR threads `tid` of a
+// group owning `smem`. Every thread of the CTA calls this together (barriers are CTA-wide); a group
+// with valid == false computes on another tile's data but writes nothing to global memory.
 template <typename T, int K, int R, int NTHR, class Spec>
-__device__ __forceinline__ void fwd_pass(const Args& a) {
+__device__ __forceinline__ void fwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
   typedef Geo<T, K, R, NTHR> G;
-  typedef typename Acc<T>::t A;
-  extern __shared__ __align__(16) unsigned char smem[];
-  void* tile = smem;
+  void* tilep = smem;
   T* cf = reinterpret_cast<T*>(smem + G::TILE);
   u8* fmv = reinterpret_cast<u8*>(cf + (Spec::NOPS > 0 ? Spec::NOPS : 1));
-  const u32 tid = threadIdx.x;
-  i64 b, t;
-  const i64 base = tile_base(a, b, t);
+  const i64 b = tile / a.tps + a.b0;
+  const i64 t = tile - (b - a.b0) * a.tps;
+  i64 base = b << a.n;
+  for (int j = 0; j < a.n_nonlocal; j++)
+    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
   for (int i = tid; i < Spec::NOPS; i += NTHR) {
     const int g = a.op_gate[i];
     if (g >= 0) {
@@ -454,36 +466,43 @@ __device__ __forceinline__ void fwd_pass(const Args& a) {
   Chunks<T, K, R, NTHR> ch;
   ch.init(a.L, tid);
   if (a.in == nullptr) {
-    FwdZero<T, K, R, NTHR, Spec> f{tile, Spec::lay_first((u32)G::EPC * tid)};
+    FwdZero<T, K, R, NTHR, Spec> f{tilep, Spec::lay_first((u32)G::EPC * tid)};
     Unroll<0, G::NCH>::run(f);
     __syncthreads();
-    if (tid == 0 && t == 0) reinterpret_cast<T*>(tile)[0] = T(1);
+    if (tid == 0 && t == 0) reinterpret_cast<T*>(tilep)[0] = T(1);
   } else {
-    FwdLoad<T, K, R, NTHR, Spec> f{reinterpret_cast<const T*>(a.in) + 2 * base, tile, &ch,
+    FwdLoad<T, K, R, NTHR, Spec> f{reinterpret_cast<const T*>(a.in) + 2 * base, tilep, &ch,
                                    Spec::lay_first((u32)G::EPC * tid)};
     Unroll<0, G::NCH>::run(f);
     cp_wait_all();
   }
   __syncthreads();
-  Spec::template fwd_phases<T>(tile, cf, fmv, tid);
+  Spec::template fwd_phases<T>(tilep, cf, fmv, tid);
   ch.init(a.L, tid);
   FwdStore<T, K, R, NTHR, Spec, true> st;
   st.out = reinterpret_cast<T*>(a.out) + 2 * base;
-  st.tile = tile;
+  st.tile = tilep;
   st.ch = &ch;
   st.s0 = Spec::lay_last((u32)G::EPC * tid);
   st.scale = reinterpret_cast<const T*>(a.scale)[b];
+  st.valid = valid;
   if (a.zpart) {
     st.zt = 0;
 #pragma unroll
     for (int r = 0; r < G::NB + 1; r++) st.zs[r] = 0;
     Unroll<0, G::NCH>::run(st);
-    z_reduce<T, K, R, NTHR>(smem, st.zt, st.zs, a.zpart + (b * a.tps + t) * (K + 1));
+    z_reduce<T, K, R, NTHR>(tilep, st.zt, st.zs, a.zpart + (b * a.tps + t) * (K + 1), tid, valid);
   } else {
     FwdStore<T, K, R, NTHR, Spec, false> s2;
-    s2.out = st.out; s2.tile = tile; s2.ch = &ch; s2.s0 = st.s0; s2.scale = st.scale;
+    s2.out = st.out; s2.tile = tilep; s2.ch = &ch; s2.s0 = st.s0; s2.scale = st.scale; s2.valid = valid;
     Unroll<0, G::NCH>::run(s2);
   }
+}
+
+template <typename T, int K, int R, int NTHR, class Spec>
+__device__ __forceinline__ void fwd_pass(const Args& a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  fwd_tile<T, K, R, NTHR, Spec>(a, (i64)blockIdx.x, true, threadIdx.x, smem);
 }
 
 // ---------------------------------------------------------------- backward pass
@@ -550,22 +569,40 @@ struct BwdStore {
   }
 };
 
+// Shared-memory bytes of one tile group (backward): psi, lambda, gradient warp partials, g per tile
+// bit, coefficients and forms.
+template <typename T, int K, int R, int NTHR, int NOPS, int NGS>
+struct BwdGroupSmem {
+  typedef typename Acc<T>::t A;
+  static constexpr int NW = (NTHR + 31) / 32;
+  static constexpr int NG = NGS > 0 ? NGS : 1;
+  static constexpr int NO = NOPS > 0 ? NOPS : 1;
+  static constexpr int TILE = (2 * (int)sizeof(T)) << K;
+  static constexpr int RED = 2 * TILE;
+  static constexpr int GQ = (RED + NW * NG * (int)sizeof(A) + 15) & ~15;
+  static constexpr int CF = GQ + (K + 2) * 8;
+  static constexpr int FM = CF + NO * (int)sizeof(T);
+  static constexpr int BYTES = (FM + NO + 15) & ~15;
+};
+
 template <typename T, int K, int R, int NTHR, class Spec>
-__device__ __forceinline__ void bwd_pass(const Args& a) {
+__device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
   typedef Geo<T, K, R, NTHR> G;
   typedef typename Acc<T>::t A;
-  constexpr int NW = (NTHR + 31) / 32;
-  constexpr int NG = Spec::NGS > 0 ? Spec::NGS : 1;
-  extern __shared__ __align__(16) unsigned char smem[];
+  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS> SM;
+  constexpr int NW = SM::NW;
+  constexpr int NG = SM::NG;
   void* tp = smem;
   void* tl = smem + G::TILE;
-  A* red = reinterpret_cast<A*>(smem + 2 * G::TILE);                  // [NW][NG]
-  double* gq = reinterpret_cast<double*>(red + NW * NG + (NW * NG) % 2 + 2);  // [K + 1]
-  T* cf = reinterpret_cast<T*>(gq + K + 2);
-  u8* fmv = reinterpret_cast<u8*>(cf + (Spec::NOPS > 0 ? Spec::NOPS : 1));
-  const u32 tid = threadIdx.x;
-  i64 b, t;
-  const i64 base = tile_base(a, b, t);
+  A* red = reinterpret_cast<A*>(smem + SM::RED);          // [NW][NG]
+  double* gq = reinterpret_cast<double*>(smem + SM::GQ);  // [K + 1]
+  T* cf = reinterpret_cast<T*>(smem + SM::CF);
+  u8* fmv = smem + SM::FM;
+  const i64 b = tile / a.tps + a.b0;
+  const i64 t = tile - (b - a.b0) * a.tps;
+  i64 base = b << a.n;
+  for (int j = 0; j < a.n_nonlocal; j++)
+    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
   for (int i = tid; i < Spec::NOPS; i += NTHR) {
     const int g = a.op_gate[i];
     if (g >= 0) {
@@ -598,14 +635,10 @@ __device__ __forceinline__ void bwd_pass(const Args& a) {
   cp_wait_all();
   __syncthreads();
   if (init_lambda) {
-    // thread part of d: tile bits below LO come from the thread id (bit 0 handled per element)
     double dt = gq[K];
     const u32 e0 = (u32)G::EPC * tid;
 #pragma unroll
     for (int j = (G::EPC == 2 ? 1 : 0); j < G::LO; j++) dt += ((e0 >> j) & 1u) ? -gq[j] : gq[j];
-    if (G::EPC == 1) {
-      // tile bit 0 belongs to the thread id as well
-    }
     BwdLambda<T, K, R, NTHR, Spec> lf{tp, tl, sl, dt, gq};
     Unroll<0, G::NCH>::run(lf);
     __syncthreads();
@@ -617,13 +650,70 @@ __device__ __forceinline__ void bwd_pass(const Args& a) {
     double acc = 0.0;
 #pragma unroll
     for (int w = 0; w < NW; w++) acc += (double)red[w * NG + s];
-    a.gpart[((a.gpart_offset + s) * a.B + b) * a.tps + t] = acc;
+    if (valid) a.gpart[((a.gpart_offset + s) * a.B + b) * a.tps + t] = acc;
   }
-  if (a.out == nullptr) return;
+  if (a.out == nullptr || !valid) return;
   BwdStore<T, K, R, NTHR, Spec> st{reinterpret_cast<T*>(a.out) + 2 * base, reinterpret_cast<T*>(a.lam_out) + 2 * base,
                                    tp, tl, &ch, Spec::lay_first((u32)G::EPC * tid),
                                    reinterpret_cast<const T*>(a.scale)[b]};
   Unroll<0, G::NCH>::run(st);
+}
+
+template <typename T, int K, int R, int NTHR, class Spec>
+__device__ __forceinline__ void bwd_pass(const Args& a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  bwd_tile<T, K, R, NTHR, Spec>(a, (i64)blockIdx.x, true, threadIdx.x, smem);
+}
+
+// ---------------------------------------------------------------- persistent multi-circuit queue
+// One work item = up to CTA/NTHR tiles of one pass of one circuit. Items are ordered so that every
+// item a CTA waits on was claimed earlier by a resident CTA, so the waits always end; they are still
+// bounded (globaltimer) and report QSIM_ERR_TIMEOUT (-8) through *status instead of hanging.
+struct Item {
+  int kind;          // pass structure (switch case of the queue kernel)
+  int arg;           // index of the pass's Args
+  i64 tile0;         // first tile of the item
+  i64 ntiles;        // tiles of the whole pass launch (B * tiles per sample)
+  int wait;          // counter to wait on (-1: none)
+  int wait_target;   // value it must reach (items of the previous pass of this circuit)
+  int done;          // counter incremented when the item is finished
+  int pad;
+};
+
+struct MultiArgs {
+  const Item* items;
+  i64 n_items;
+  unsigned long long* head;   // next item to claim
+  int* counters;
+  int* status;
+  const Args* args;
+  i64 timeout_ns;
+  i64 withhold;               // test hook: item whose completion is never signalled (-1: none)
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0: wait until the item's dependency is complete. false = gave up (status set to timeout).
+__device__ __forceinline__ bool wait_dependency(const MultiArgs& m, const Item& it) {
+  if (it.wait < 0) return true;
+  const unsigned long long t0 = gtimer();
+  while (ld_acquire(m.counters + it.wait) < it.wait_target) {
+    if ((long long)(gtimer() - t0) > m.timeout_ns) {
+      atomicExch(m.status, -8);
+      return false;
+    }
+    __nanosleep(256);
+  }
+  return true;
 }
 
 }  // namespace qj

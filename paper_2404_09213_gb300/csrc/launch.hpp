@@ -29,6 +29,11 @@ struct CoefArgs {
   void* scale_f;                // [P * B]
   void* scale_b;                // [P * B]
   double* gm;                   // [G * B] squared backward scale at each rotation
+  // several circuits (all null for a single circuit): circuit of every pass and its offsets
+  const int32_t* pass_circ;     // [P]
+  const int64_t* circ_param_off;   // [C] first parameter of the circuit
+  const int64_t* circ_col_off;     // [C] input columns before the circuit (per sample)
+  const int32_t* circ_ninputs;     // [C]
 };
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st);
 
@@ -53,6 +58,40 @@ struct GradReduceArgs {
   double* dinputs;              // may be null
 };
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st);
+
+// ---- several circuits
+struct ZCirc {
+  int64_t zp_off, tps, bits_off;
+  int32_t k, n, n_nonlocal, pad;
+};
+struct ZMultiArgs {
+  const double* zpart;
+  const ZCirc* circ;
+  const int64_t* zq_off;        // [C + 1] qubits before each circuit (per sample)
+  const uint8_t* bits;
+  double* z;
+  int C, B;
+};
+cudaError_t launch_z_final_multi(const ZMultiArgs& a, int64_t total, cudaStream_t st);
+struct GradMultiArgs {
+  const double* gpart;
+  int n_occ;
+  const int32_t* occ_gate;      // global gate index
+  const int64_t* occ_base;      // offset of the occurrence's partials for sample 0
+  const int64_t* occ_tps;       // tiles per sample of its circuit
+  const double* gm;
+  double* G;
+  int B;
+  int64_t n_params, n_cols;     // global parameter count, global input columns
+  const int32_t* p_ptr; const int32_t* p_occ;
+  const int32_t* i_ptr; const int32_t* i_occ;
+  const int64_t* col_circ_off;  // per global column: input columns before its circuit (per sample)
+  const int32_t* col_stride;    // per global column: its circuit's n_inputs
+  const int32_t* col_index;     // per global column: column within its circuit
+  double* dparams;
+  double* dinputs;
+};
+cudaError_t launch_grad_reduce_multi(const GradMultiArgs& a, cudaStream_t st);
 
 // ---- per-gate (plain) path
 struct PerGateArgs {

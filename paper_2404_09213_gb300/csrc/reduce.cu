@@ -21,6 +21,13 @@ __global__ void coef_kernel(CoefArgs a) {
   const int p = (int)(id / a.B), b = (int)(id - (int64_t)p * a.B);
   const T* params = reinterpret_cast<const T*>(a.params);
   const T* inputs = reinterpret_cast<const T*>(a.inputs);
+  int n_inputs = a.n_inputs;
+  if (a.pass_circ) {   // several circuits: parameters and inputs of this pass's circuit
+    const int c = a.pass_circ[p];
+    if (params) params += a.circ_param_off[c];
+    if (inputs) inputs += (int64_t)a.B * a.circ_col_off[c];
+    n_inputs = a.circ_ninputs[c];
+  }
   T* coef = reinterpret_cast<T*>(a.coef);
   const int e0 = a.exec_begin[p], e1 = a.exec_begin[p + 1];
   double fs = 1.0;
@@ -29,7 +36,7 @@ __global__ void coef_kernel(CoefArgs a) {
     const int ty = a.gate_type[g];
     if (ty <= QSIM_RZ) {
       const int pr = a.gate_param[g];
-      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * a.n_inputs + (-2 - pr)];
+      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
       double s, c;
       sincos(0.5 * th, &s, &c);
       const int64_t gi = (int64_t)g * a.B + b;
@@ -57,7 +64,7 @@ __global__ void coef_kernel(CoefArgs a) {
       const int64_t gi = (int64_t)g * a.B + b;
       a.gm[gi] = bs * bs;
       const int pr = a.gate_param[g];
-      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * a.n_inputs + (-2 - pr)];
+      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
       double s, c;
       sincos(0.5 * th, &s, &c);
       bs *= (a.form[gi] == 0) ? c : -s;
@@ -167,6 +174,93 @@ cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st) {
   const int64_t total = (a.dparams ? a.n_params : 0) + (a.dinputs ? (int64_t)a.B * a.n_inputs : 0);
   if (total > 0) {
     grad_scatter_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
+    g_kernel_launches++;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ several circuits
+// <Z>: block per (circuit, sample, qubit), flattened in circuit order; circuit found by bisection.
+__global__ void z_final_multi_kernel(ZMultiArgs a) {
+  __shared__ double sh[32];
+  const int64_t gz = blockIdx.x;
+  int lo = 0, hi = a.C;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if ((int64_t)a.B * a.zq_off[mid] <= gz) lo = mid;
+    else hi = mid;
+  }
+  const int c = lo;
+  const ZCirc d = a.circ[c];
+  const int64_t r = gz - (int64_t)a.B * a.zq_off[c];
+  const int b = (int)(r / d.n), q = (int)(r - (int64_t)b * d.n);
+  const int pos = d.n - 1 - q;
+  const uint8_t* Lnl = a.bits + d.bits_off;
+  int tbit = -1, nlbit = -1;
+  for (int j = 0; j < d.k; j++)
+    if (Lnl[j] == pos) tbit = j;
+  for (int j = 0; j < d.n_nonlocal; j++)
+    if (Lnl[d.k + j] == pos) nlbit = j;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < d.tps; t += blockDim.x) {
+    const double* row = a.zpart + d.zp_off + ((int64_t)b * d.tps + t) * (d.k + 1);
+    if (tbit >= 0) acc += row[tbit];
+    else acc += ((t >> nlbit) & 1) ? -row[d.k] : row[d.k];
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) a.z[gz] = acc;
+}
+
+cudaError_t launch_z_final_multi(const ZMultiArgs& a, int64_t total, cudaStream_t st) {
+  if (total <= 0) return cudaSuccess;
+  z_final_multi_kernel<<<(unsigned)total, 256, 0, st>>>(a);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+// gradients: G[j][b] = gm * sum over tiles of the occurrence's partials (block per (j, b))
+__global__ void grad_gather_multi_kernel(GradMultiArgs a) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x / a.B, b = blockIdx.x - (blockIdx.x / a.B) * a.B;
+  const int64_t tps = a.occ_tps[j];
+  const double* src = a.gpart + a.occ_base[j] + (int64_t)b * tps;
+  double acc = 0.0;
+  for (int64_t t = threadIdx.x; t < tps; t += blockDim.x) acc += src[t];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) a.G[(int64_t)j * a.B + b] = acc * a.gm[(int64_t)a.occ_gate[j] * a.B + b];
+}
+
+__global__ void grad_scatter_multi_kernel(GradMultiArgs a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t np = a.dparams ? a.n_params : 0;
+  const int64_t ni = a.dinputs ? (int64_t)a.n_cols * a.B : 0;
+  if (id < np) {
+    double acc = 0.0;
+    for (int o = a.p_ptr[id]; o < a.p_ptr[id + 1]; o++) {
+      const double* row = a.G + (int64_t)a.p_occ[o] * a.B;
+      for (int b = 0; b < a.B; b++) acc += row[b];
+    }
+    a.dparams[id] = acc;
+  } else if (id < np + ni) {
+    const int64_t r = id - np;
+    const int64_t gc = r / a.B;
+    const int b = (int)(r - gc * a.B);
+    double acc = 0.0;
+    for (int o = a.i_ptr[gc]; o < a.i_ptr[gc + 1]; o++) acc += a.G[(int64_t)a.i_occ[o] * a.B + b];
+    a.dinputs[(int64_t)a.B * a.col_circ_off[gc] + (int64_t)b * a.col_stride[gc] + a.col_index[gc]] = acc;
+  }
+}
+
+cudaError_t launch_grad_reduce_multi(const GradMultiArgs& a, cudaStream_t st) {
+  if (a.n_occ > 0 && a.B > 0) {
+    grad_gather_multi_kernel<<<(unsigned)(a.n_occ * a.B), 256, 0, st>>>(a);
+    g_kernel_launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t total = (a.dparams ? a.n_params : 0) + (a.dinputs ? (int64_t)a.n_cols * a.B : 0);
+  if (total > 0) {
+    grad_scatter_multi_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
     g_kernel_launches++;
   }
   return cudaGetLastError();
