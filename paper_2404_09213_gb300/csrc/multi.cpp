@@ -113,6 +113,12 @@ struct qsim_multi_s {
   cudaGraphExec_t gx_f = nullptr, gx_b = nullptr;
   std::vector<const void*> key_f, key_b;
   std::vector<JitArgs> host_args_f, host_args_b;   // last uploaded argument blocks
+  cudaStream_t cap = nullptr;   // plan-owned stream the graphs are captured on (the caller's may be the legacy stream)
+
+  cudaError_t capture_stream() {
+    if (cap) return cudaSuccess;
+    return cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  }
 
   int64_t tps(int c) const { return sch[c].passes[0].dev.tiles_per_sample; }
   int P(int c) const { return (int)sch[c].passes.size(); }
@@ -149,6 +155,8 @@ struct qsim_multi_s {
     for (void* p : ps)
       if (p) cudaFree(p);
     jit_free_multi(jm);
+    if (cap) cudaStreamDestroy(cap);
+    cap = nullptr;
     uploaded = false;
   }
 
@@ -524,10 +532,11 @@ int qsim_multi_forward(qsim_multi_t m, const void* d_params, const void* d_input
       if (m->gx_f) cudaGraphExecDestroy(m->gx_f);
       m->gx_f = nullptr;
       cudaGraph_t g = nullptr;
-      e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      e = m->capture_stream();
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t e2 = multi_enqueue_fwd(m, d_params, d_inputs, d_states, d_z, st);
-        e = cudaStreamEndCapture(st, &g);
+        cudaError_t e2 = multi_enqueue_fwd(m, d_params, d_inputs, d_states, d_z, m->cap);
+        e = cudaStreamEndCapture(m->cap, &g);
         if (e == cudaSuccess) e = e2;
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gx_f, g, 0);
@@ -607,10 +616,11 @@ int qsim_multi_backward(qsim_multi_t m, const double* d_grad_out, double* d_dpar
       if (m->gx_b) cudaGraphExecDestroy(m->gx_b);
       m->gx_b = nullptr;
       cudaGraph_t g = nullptr;
-      e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+      e = m->capture_stream();
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        cudaError_t e2 = multi_enqueue_bwd(m, d_dparams, d_dinputs, st);
-        e = cudaStreamEndCapture(st, &g);
+        cudaError_t e2 = multi_enqueue_bwd(m, d_dparams, d_dinputs, m->cap);
+        e = cudaStreamEndCapture(m->cap, &g);
         if (e == cudaSuccess) e = e2;
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gx_b, g, 0);
