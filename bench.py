@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64, help="samples (64 = the workload; smaller for ncu captures)")
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5"],
+                    help="c3 (default): 20 qubits x 64, fwd+bwd; c2: 12 qubits x 1024 forward; "
+                         "c4: 256 circuits (8..22 qubits) x 4 in one persistent launch, fwd+bwd; "
+                         "c5: 30 qubits x 1, fwd + checkpointed bwd")
     ap.add_argument("--contiguous-bits", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -318,6 +322,106 @@ def run_ours(args, world, rank, local):
     return out, wl
 
 
+def run_other(args, world, rank, local):
+    """Secondary workloads (one JSON line each): C2 forward, C4 multi-circuit, C5 30 qubits."""
+    import torch
+    import workloads as W
+    from paper_2404_09213_gb300 import build as qbuild
+    qbuild.build()
+    import paper_2404_09213_gb300 as q
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = load_peaks()
+    if args.workload == "c4":
+        wls = W.multi_circuit_config()
+        B = 4
+        mp = q.MultiPlan([(w.gates, w.n) for w in wls], graph=True)
+        p = torch.tensor(np.concatenate([w.params for w in wls]), dtype=torch.float32, device=dev)
+        x = torch.tensor(np.concatenate([w.inputs.ravel() for w in wls]), dtype=torch.float32, device=dev)
+        g = torch.tensor(np.concatenate([w.grad_out.ravel() for w in wls]), dtype=torch.float64, device=dev)
+        off = mp.offsets(B)
+        states = torch.empty(int(off["states"][-1]), dtype=torch.complex64, device=dev)
+        z = torch.empty(int(off["z"][-1]), dtype=torch.float64, device=dev)
+        dp = torch.zeros(int(off["params"][-1]), dtype=torch.float64, device=dev)
+        di = torch.zeros(int(off["inputs"][-1]), dtype=torch.float64, device=dev)
+
+        def step():
+            mp.forward(p, x, B, states=states, z=z, stream=stream)
+            mp.backward(g, dparams=dp, dinputs=di, stream=stream)
+        samples = B * len(wls)
+        # algorithmic bytes of every pass (complex64): forward 16 B/amp (8 for the |0> start),
+        # backward 32 B/amp (24 for the first, 16 for the last)
+        tot = 0
+        for w in wls:
+            P = q.Plan(w.gates, w.n).info()["n_passes"]
+            amps = B * (1 << w.n)
+            tot += amps * (8 + 16 * (P - 1))
+            tot += amps * (8 if P == 1 else 24 + 16 + 32 * (P - 2))
+        name = "C4: 256 circuits, 8..22 qubits (log-uniform), depth 4..16, HEA (RY,RZ + CZ ladder), batch 4, c64, fwd+bwd"
+        extra = {"circuits": len(wls), "batch_per_circuit": B, "queue": mp.info(), "graph": True}
+    elif args.workload == "c5":
+        wl = W.config(5)
+        B = 1
+        plan = q.Plan(wl.gates, wl.n, checkpoint_passes=8)
+        p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
+        x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
+        g = torch.tensor(wl.grad_out, dtype=torch.float64, device=dev)
+
+        def step():
+            plan.forward(p, x, stream=stream)
+            plan.backward(g, stream=stream)
+        samples = B
+        P = plan.info()["n_passes"]
+        amps = 1 << wl.n
+        tot = amps * (8 + 16 * (P - 1)) + amps * (24 + 16 + 32 * (P - 2))
+        name = "C5: 30 qubits, batch 1, c64, RX encoding + 8 x (RY,RZ + CNOT ring), fwd + checkpointed bwd"
+        extra = {"passes": P, "checkpoint_passes": 8}
+    else:
+        wl = W.config(2)
+        B = wl.batch
+        plan = q.Plan(wl.gates, wl.n, mode=args.mode)
+        p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
+        x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
+        states = torch.empty((B, 1 << wl.n), dtype=torch.complex64, device=dev)
+        z = torch.empty((B, wl.n), dtype=torch.float64, device=dev)
+
+        def step():
+            plan.forward(p, x, states=states, z=z, stream=stream)
+        samples = B
+        P = plan.info()["n_passes"]
+        tot = B * (1 << wl.n) * (8 + 16 * (P - 1)) if args.mode == "fused" else B * (1 << wl.n) * 16 * len(wl.gates)
+        name = f"C2: 12 qubits, batch 1024, c64, RX encoding + 6 x (RY,RZ + CNOT ring), forward only, {args.mode}"
+        extra = {"passes": P, "mode": args.mode}
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    time.sleep(0.3)
+    launches0 = q.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.stop()
+    launches = q.kernel_launches() - launches0
+    gbs = tot * args.steps / (ms / 1e3) / 1e9
+    metric = "fwd+adjoint-bwd samples/s" if args.workload != "c2" else "forward samples/s"
+    out = {"metric": metric, "value": samples * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 state, fp64 reductions)",
+           "data": "synthetic (seeded splitmix64)", "config": dict(workload=name, **extra),
+           "roofline": {"bound": "hbm", "kernel": "whole step (all pass kernels)", "achieved": gbs, "peak": peak,
+                        "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                        "algorithmic_bytes_per_step": tot, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
+           "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     world, rank, local = dist_init(args.gpus)
@@ -344,6 +448,10 @@ def main():
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "wall_s": dt}
         print(json.dumps(line))
+        return
+    if args.workload != "c3":
+        if rank == 0:
+            run_other(args, world, rank, local)
         return
     out, wl = run_ours(args, world, rank, local)
     if rank == 0:
