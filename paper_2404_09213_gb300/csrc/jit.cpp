@@ -198,60 +198,118 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 // ------------------------------------------------------------------ generation
 static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0) {
   const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
+  const int P = d.n_phases;
   std::ostringstream o;
   o << "  static constexpr int CTA = " << (cta > 0 ? cta : NTHR) << ";\n";
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
-  for (int i = 0; i <= d.n_phases; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
-  o << "  static __device__ __forceinline__ qj::u32 lay_first(qj::u32 e) { return L0(e); }\n";
-  o << "  static __device__ __forceinline__ qj::u32 lay_last(qj::u32 e) { return L" << d.n_phases << "(e); }\n";
+  for (int i = 0; i <= P; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
+  auto dep_of = [&](const DevPhase& ph, int i) {
+    uint32_t e = 0;
+    for (int r = 0; r < R; r++)
+      if ((i >> r) & 1) e |= 1u << ph.rbit[r];
+    return e;
+  };
+  // <Z> bit map of the phase that stores to global memory (forward: the last phase)
   if (!bwd) {
-    o << "  template <typename T> static __device__ __forceinline__ void fwd_phases(void* tile, const T* cf, "
-         "const qj::u8* fm, qj::u32 tid) {\n";
-    o << "    T re[" << N << "], im[" << N << "];\n";
-  } else {
-    o << "  template <typename T, typename A> static __device__ __forceinline__ void bwd_phases(void* tp, void* tl, "
-         "const T* cf, const qj::u8* fm, A* red, qj::u32 tid) {\n";
-    o << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n";
-    o << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n";
-    o << "    (void)lane; (void)warp;\n";
+    const DevPhase& lp = s.phases[d.phase0 + P - 1];
+    o << "  static __device__ __forceinline__ int zmap(int j) {\n    switch (j) {\n";
+    for (int r = 0; r < R; r++) o << "      case " << (int)lp.rbit[r] << ": return " << r << ";\n";
+    for (int p = 0; p < lp.n_tbits; p++) o << "      case " << (int)lp.tbit[p] << ": return " << -1 - p << ";\n";
+    o << "      default: return 0;\n    }\n  }\n";
   }
-  for (int step = 0; step < d.n_phases; step++) {
-    const int ph = bwd ? d.n_phases - 1 - step : step;
-    const DevPhase& P = s.phases[d.phase0 + ph];
+  // global offset of the thread's base element and of the register bits, for a phase
+  auto gaddr = [&](const DevPhase& ph, const char* var) {
+    std::ostringstream g;
+    g << "      qj::i64 " << var << " = c.base;\n";
+    for (int jb = 0; jb < ph.n_tbits; jb++)
+      g << "      if ((tid >> " << jb << ") & 1u) " << var << " |= (qj::i64)1 << a.L[" << (int)ph.tbit[jb] << "];\n";
+    for (int r = 1; r < R; r++) g << "      const qj::i64 " << var << "u" << r << " = (qj::i64)1 << a.L[" << (int)ph.rbit[r] << "];\n";
+    return g.str();
+  };
+  auto goff = [&](const char* var, int i) {
+    std::string e = var;
+    for (int r = 1; r < R; r++)
+      if ((i >> r) & 1) e += std::string(" | ") + var + "u" + std::to_string(r);
+    return "(" + e + ")";
+  };
+  if (!bwd) {
+    o << "  template <typename T> static __device__ __forceinline__ void fwd_phases(qj::Ctx<T>& c) {\n"
+      << "    const qj::Args& a = *c.a;\n    const qj::u32 tid = c.tid;\n"
+      << "    T re[" << N << "], im[" << N << "];\n";
+  } else {
+    o << "  template <typename T, typename A> static __device__ __forceinline__ void bwd_phases(qj::Ctx<T>& c, A* red) {\n"
+      << "    const qj::Args& a = *c.a;\n    const qj::u32 tid = c.tid;\n"
+      << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n"
+      << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n    (void)lane; (void)warp;\n";
+  }
+  for (int step = 0; step < P; step++) {
+    const int ph = bwd ? P - 1 - step : step;
+    const DevPhase& Ph = s.phases[d.phase0 + ph];
     const int lin = bwd ? ph + 1 : ph, lout = bwd ? ph : ph + 1;
+    const bool first = step == 0, last = step == P - 1;
     const DevLayout& Li = s.layouts[d.lay0 + lin];
     const DevLayout& Lo = s.layouts[d.lay0 + lout];
-    o << "    { // phase " << ph << "\n";
+    o << "    { // phase " << ph << (first ? " (loads from global)" : "") << (last ? " (stores to global)" : "") << "\n";
     o << "      const qj::u32 tb = 0u";
-    for (int j = 0; j < P.n_tbits; j++) o << " | (((tid >> " << j << ") & 1u) << " << (int)P.tbit[j] << ")";
+    for (int jb = 0; jb < Ph.n_tbits; jb++) o << " | (((tid >> " << jb << ") & 1u) << " << (int)Ph.tbit[jb] << ")";
     o << ";\n      (void)tb;\n";
-    o << "      const qj::u32 si = L" << lin << "(tb), so = L" << lout << "(tb);\n";
-    auto dep = [&](int i) {
-      uint32_t e = 0;
-      for (int r = 0; r < R; r++)
-        if ((i >> r) & 1) e |= 1u << P.rbit[r];
-      return e;
-    };
-    for (int i = 0; i < N; i += 2) {
-      const uint32_t c = lay_eval(Li, K, dep(i));
+    if (first || last) o << gaddr(Ph, "gb");
+    // ---- load
+    if (first) {
       if (!bwd) {
-        o << "      qj::ldp(tile, si ^ " << c << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+        o << "      if (a.in == nullptr) {\n";
+        for (int i = 0; i < N; i++) o << "        re[" << i << "] = T(0); im[" << i << "] = T(0);\n";
+        o << "        if (tb == 0u && c.t == 0) re[0] = T(1);\n      } else {\n"
+          << "        const T* in = reinterpret_cast<const T*>(a.in);\n";
+        for (int i = 0; i < N; i += 2)
+          o << "        qj::ldg_pair(in + 2 * " << goff("gb", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
+            << "], im[" << i + 1 << "]);\n";
+        o << "      }\n";
       } else {
-        o << "      qj::ldp(tp, si ^ " << c << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
-        o << "      qj::ldp(tl, si ^ " << c << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+        o << "      {\n        const T* in = reinterpret_cast<const T*>(a.in);\n";
+        for (int i = 0; i < N; i += 2)
+          o << "        qj::ldg_pair(in + 2 * " << goff("gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
+            << "], pq[" << i + 1 << "]);\n";
+        o << "      }\n      if (a.lam_in != nullptr) {\n        const T* li = reinterpret_cast<const T*>(a.lam_in);\n";
+        for (int i = 0; i < N; i += 2)
+          o << "        qj::ldg_pair(li + 2 * " << goff("gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
+            << "], lq[" << i + 1 << "]);\n";
+        // lambda = d(e) psi, d(e) = gq[K] + sum_j (bit_j(e) ? -g_j : g_j)
+        o << "      } else {\n        double dt = c.gq[" << K << "];\n";
+        for (int jb = 0; jb < Ph.n_tbits; jb++)
+          o << "        dt += ((tid >> " << jb << ") & 1u) ? -c.gq[" << (int)Ph.tbit[jb] << "] : c.gq[" << (int)Ph.tbit[jb] << "];\n";
+        for (int r = 0; r < R; r++) o << "        const double g" << r << " = c.gq[" << (int)Ph.rbit[r] << "];\n";
+        for (int i = 0; i < N; i++) {
+          o << "        { const double dd = dt";
+          for (int r = 0; r < R; r++) o << (((i >> r) & 1) ? " - g" : " + g") << r;
+          o << "; lr[" << i << "] = (T)(dd * (double)pr[" << i << "]); lq[" << i << "] = (T)(dd * (double)pq[" << i << "]); }\n";
+        }
+        o << "      }\n";
+      }
+    } else {
+      o << "      const qj::u32 si = L" << lin << "(tb);\n";
+      for (int i = 0; i < N; i += 2) {
+        const uint32_t cc = lay_eval(Li, K, dep_of(Ph, i));
+        if (!bwd) {
+          o << "      qj::ldp(c.tile, si ^ " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+        } else {
+          o << "      qj::ldp(c.tile, si ^ " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
+          o << "      qj::ldp(c.tile2, si ^ " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+        }
       }
     }
+    // ---- ops
     std::vector<int> order;
-    for (int oi = P.op_begin; oi < P.op_end; oi++) order.push_back(oi);
+    for (int oi = Ph.op_begin; oi < Ph.op_end; oi++) order.push_back(oi);
     if (bwd) std::reverse(order.begin(), order.end());
     for (int oi : order) {
       const DevOp& op = s.ops[oi];
       const int li = oi - d.op0;
       const int SA = 1 << op.a, SB = 1 << op.b;
-      std::string C = "cf[" + std::to_string(li) + "], fm[" + std::to_string(li) + "]";
+      std::string C = "c.cf[" + std::to_string(li) + "], c.fm[" + std::to_string(li) + "]";
       std::string call;
-      std::ostringstream g;   // gradient expression (backward, rotations)
+      std::ostringstream g;
       switch (op.kind) {
         case K_RY_R:
           call = "qj::ry<" + std::to_string(N) + ", " + std::to_string(SA) + ">(%R, %I, " + C + ");";
@@ -305,24 +363,56 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       if (!bwd) {
         o << "      " << inst("re", "im") << "\n";
       } else {
-        if (op.rot) {
+        if (op.rot)
           o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ", A, CTA>(g); if (lane == 0u) red[warp * "
             << (d.n_gslots > 0 ? d.n_gslots : 1) << " + " << op.gslot << "] = g; }\n";
-        }
         o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
       }
     }
-    o << "      __syncthreads();\n";
-    for (int i = 0; i < N; i += 2) {
-      const uint32_t c = lay_eval(Lo, K, dep(i));
+    // ---- store
+    if (last) {
+      o << "      const T sc = reinterpret_cast<const T*>(a.scale)[c.b];\n";
       if (!bwd) {
-        o << "      qj::stp(tile, so ^ " << c << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+        o << "      qj::scal<" << N << ">(re, im, sc);\n"
+          << "      if (c.valid) {\n        T* out = reinterpret_cast<T*>(a.out);\n";
+        for (int i = 0; i < N; i += 2)
+          o << "        qj::stg_pair(out + 2 * " << goff("gb", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
+            << "], im[" << i + 1 << "]);\n";
+        o << "      }\n      if (a.zpart != nullptr) {\n        typedef typename qj::Acc<T>::t A;\n        A zt = 0, zs[" << R << "];\n";
+        for (int r = 0; r < R; r++) o << "        zs[" << r << "] = 0;\n";
+        for (int i = 0; i < N; i++) {
+          o << "        { const A p = (A)re[" << i << "] * (A)re[" << i << "] + (A)im[" << i << "] * (A)im[" << i << "]; zt += p;";
+          for (int r = 0; r < R; r++) o << " zs[" << r << "] " << (((i >> r) & 1) ? "-=" : "+=") << " p;";
+          o << " }\n";
+        }
+        o << "        qj::z_reduce_regs<T, " << K << ", " << R << ", " << NTHR
+          << ", S_SELF>(c.tile, zt, zs, a.zpart + (c.b * a.tps + c.t) * " << K + 1 << ", tid, c.valid);\n      }\n";
       } else {
-        o << "      qj::stp(tp, so ^ " << c << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
-        o << "      qj::stp(tl, so ^ " << c << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+        o << "      if (a.out != nullptr && c.valid) {\n"
+          << "        qj::scal<" << N << ">(pr, pq, sc); qj::scal<" << N << ">(lr, lq, sc);\n"
+          << "        T* po = reinterpret_cast<T*>(a.out);\n        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
+        for (int i = 0; i < N; i += 2) {
+          o << "        qj::stg_pair(po + 2 * " << goff("gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
+            << "], pq[" << i + 1 << "]);\n";
+          o << "        qj::stg_pair(lo + 2 * " << goff("gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
+            << "], lq[" << i + 1 << "]);\n";
+        }
+        o << "      }\n";
       }
+    } else {
+      o << "      __syncthreads();\n      const qj::u32 so = L" << lout << "(tb);\n";
+      for (int i = 0; i < N; i += 2) {
+        const uint32_t cc = lay_eval(Lo, K, dep_of(Ph, i));
+        if (!bwd) {
+          o << "      qj::stp(c.tile, so ^ " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+        } else {
+          o << "      qj::stp(c.tile, so ^ " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
+          o << "      qj::stp(c.tile2, so ^ " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+        }
+      }
+      o << "      __syncthreads();\n";
     }
-    o << "      __syncthreads();\n    }\n";
+    o << "    }\n";
   }
   o << "  }\n";
   return o.str();
@@ -364,7 +454,9 @@ static void jit_units(const Schedule& s, std::vector<std::string>& fnames, std::
       std::string name = std::string(bwd ? "qb_" : "qf_") + hex64(fnv1a(key));
       if (!units.count(name)) {
         std::ostringstream u;
-        u << "struct S_" << name << " {\n" << body << "};\n";
+        std::string b2 = body;
+        for (size_t p; (p = b2.find("S_SELF")) != std::string::npos;) b2.replace(p, 6, "S_" + name);
+        u << "struct S_" << name << " {\n" << b2 << "};\n";
         u << "extern \"C\" __global__ void __launch_bounds__(" << NTHR << ") " << name
           << "(const qj::Args a) { qj::" << (bwd ? "bwd_pass" : "fwd_pass") << "<" << T << ", " << K << ", " << R
           << ", " << NTHR << ", S_" << name << ">(a); }\n";
@@ -511,6 +603,7 @@ static std::string multi_unit(const Schedule& s, const DevPass& d, bool bwd, int
   std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" + body;
   name = std::string(bwd ? "qsb_" : "qsf_") + hex64(fnv1a(key));
   std::ostringstream u;
+  for (size_t p; (p = body.find("S_SELF")) != std::string::npos;) body.replace(p, 6, "S_" + name);
   u << "struct S_" << name << " {\n" << body << "};\n";
   u << "extern \"C\" __device__ void " << name
     << "(const qj::Args* a, long long tile0, long long ntiles, unsigned char* smem) {\n"

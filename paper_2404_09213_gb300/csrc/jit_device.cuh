@@ -277,164 +277,89 @@ __device__ __forceinline__ void stp(void* tile, u32 w, double r0, double i0, dou
   reinterpret_cast<double2*>(tile)[w ^ 1u] = make_double2(r1, i1);
 }
 
-// ---------------------------------------------------------------- tile context
-// EPC: amplitudes per 16-byte chunk; NB: chunk-index bits owned by the loop (i) per thread.
-template <typename T, int K, int R, int NTHR>
-struct Geo {
-  static constexpr int EPC = sizeof(T) == 4 ? 2 : 1;
-  static constexpr int LOGT = K - R;
-  static constexpr int LO = LOGT + (EPC == 2 ? 1 : 0);   // first tile bit driven by the chunk loop
-  static constexpr int NB = K - LO;                       // chunk loop bits
-  static constexpr int NCH = 1 << NB;                     // chunks per thread
-  static constexpr int EL = 2 * sizeof(T);                // bytes per amplitude
-  static constexpr int TILE = EL << K;                    // bytes per tile
-};
-
-// Tile base (element offset in the batched state) and the thread's chunk offsets.
-template <typename T, int K, int R, int NTHR>
-struct Chunks {
-  typedef Geo<T, K, R, NTHR> G;
-  i64 gb;            // global offset (within the tile) of the thread's chunk 0
-  i64 gu[G::NB > 0 ? G::NB : 1];
-  __device__ __forceinline__ void init(const u8* L, u32 tid) {
-    const u32 e0 = (u32)G::EPC * tid;
-    gb = 0;
-#pragma unroll
-    for (int j = 0; j < G::LO; j++)
-      if ((e0 >> j) & 1u) gb |= (i64)1 << L[j];
-#pragma unroll
-    for (int r = 0; r < G::NB; r++) gu[r] = (i64)1 << L[G::LO + r];
-  }
-  template <int I>
-  __device__ __forceinline__ i64 g() const {
-    i64 x = gb;
-#pragma unroll
-    for (int r = 0; r < G::NB; r++)
-      if ((I >> r) & 1) x |= gu[r];
-    return x;
-  }
-};
-
-template <int I, int LO, int NB>
-struct ChunkElem {   // tile element offset of loop index I (compile time)
-  static constexpr u32 v = (u32)I << LO;
-};
-
-__device__ __forceinline__ i64 tile_base(const Args& a, i64& b_out, i64& t_out) {
-  const i64 b = (i64)blockIdx.x / a.tps + a.b0;
-  const i64 t = (i64)blockIdx.x - (b - a.b0) * a.tps;
-  i64 base = b << a.n;
-  for (int j = 0; j < a.n_nonlocal; j++)
-    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
-  b_out = b;
-  t_out = t;
-  return base;
+// ---------------------------------------------------------------- direct global <-> register I/O
+// The first register phase loads its amplitudes straight from global memory and the last one stores
+// them straight back; the planner keeps tile bits 1..3 as thread bits there, so lanes 0..7 of a warp
+// cover one contiguous run of 16 amplitudes (128 bytes for complex64).
+__device__ __forceinline__ void ldg_pair(const float* p, float& r0, float& i0, float& r1, float& i1) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  r0 = v.x; i0 = v.y; r1 = v.z; i1 = v.w;
+}
+__device__ __forceinline__ void ldg_pair(const double* p, double& r0, double& i0, double& r1, double& i1) {
+  const double2 a = __ldcg(reinterpret_cast<const double2*>(p)), b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+  r0 = a.x; i0 = a.y; r1 = b.x; i1 = b.y;
+}
+__device__ __forceinline__ void stg_pair(float* p, float r0, float i0, float r1, float i1) {
+  *reinterpret_cast<float4*>(p) = make_float4(r0, i0, r1, i1);
+}
+__device__ __forceinline__ void stg_pair(double* p, double r0, double i0, double r1, double i1) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(r0, i0);
+  reinterpret_cast<double2*>(p)[1] = make_double2(r1, i1);
 }
 
-// Compile-time loop helper
-template <int I, int END>
-struct Unroll {
-  template <typename F>
-  __device__ __forceinline__ static void run(F& f) {
-    f.template step<I>();
-    Unroll<I + 1, END>::run(f);
-  }
-};
-template <int END>
-struct Unroll<END, END> {
-  template <typename F>
-  __device__ __forceinline__ static void run(F&) {}
-};
-
-// ---------------------------------------------------------------- forward pass
-template <typename T, int K, int R, int NTHR, class Spec>
-struct FwdLoad {
-  typedef Geo<T, K, R, NTHR> G;
-  const T* in; void* tile; const Chunks<T, K, R, NTHR>* ch; u32 s0;
-  template <int I>
-  __device__ __forceinline__ void step() {
-    const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
-    cp16(reinterpret_cast<char*>(tile) + (size_t)w * G::EL, in + 2 * ch->template g<I>());
-  }
+// Per-tile context handed to the generated phase code.
+template <typename T>
+struct Ctx {
+  const Args* a;
+  void* tile;            // forward: the tile; backward: psi
+  void* tile2;           // backward: lambda
+  const T* cf;
+  const u8* fm;
+  const double* gq;      // backward, lambda init: g of every tile bit, [K] = fixed-bit part
+  i64 base;              // element offset of the tile (bits outside the tile) in the batched state
+  i64 b, t;              // sample, tile within the sample
+  u32 tid;
+  bool valid;
 };
 
-template <typename T, int K, int R, int NTHR, class Spec>
-struct FwdZero {
-  typedef Geo<T, K, R, NTHR> G;
-  void* tile; u32 s0;
-  template <int I>
-  __device__ __forceinline__ void step() {
-    const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
-    if (G::EPC == 2) reinterpret_cast<float4*>(tile)[w >> 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    else reinterpret_cast<double2*>(tile)[w] = make_double2(0.0, 0.0);
-  }
-};
-
-template <typename T, int K, int R, int NTHR, class Spec, bool Z>
-struct FwdStore {
-  typedef Geo<T, K, R, NTHR> G;
-  typedef typename Acc<T>::t A;
-  T* out; const void* tile; const Chunks<T, K, R, NTHR>* ch; u32 s0; T scale; bool valid;
-  A zt; A zs[G::NB + 1];
-  template <int I>
-  __device__ __forceinline__ void step() {
-    const u32 w = s0 ^ Spec::lay_last(ChunkElem<I, G::LO, G::NB>::v);
-    const i64 g = ch->template g<I>();
-    if (G::EPC == 2) {
-      float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
-      v.x *= (float)scale; v.y *= (float)scale; v.z *= (float)scale; v.w *= (float)scale;
-      if (valid) *reinterpret_cast<float4*>(out + 2 * g) = v;
-      if (Z) {
-        const A p0 = fm((A)v.x, (A)v.x, (A)v.y * (A)v.y), p1 = fm((A)v.z, (A)v.z, (A)v.w * (A)v.w);
-        zt += p0 + p1;
-        zs[0] += p0 - p1;
+// element offset of tile element e: bits of e deposited onto the physical positions L
+template <int NT>
+__device__ __forceinline__ i64 deposit_thread(const u8* L, const u8* tbit, u32 tid) {
+  i64 g = 0;
 #pragma unroll
-        for (int r = 0; r < G::NB; r++) zs[1 + r] += ((I >> r) & 1) ? -(p0 + p1) : (p0 + p1);
-      }
-    } else {
-      double2 v = reinterpret_cast<const double2*>(tile)[w];
-      v.x *= (double)scale; v.y *= (double)scale;
-      if (valid) *reinterpret_cast<double2*>(out + 2 * g) = v;
-      if (Z) {
-        const A p = (A)(v.x * v.x + v.y * v.y);
-        zt += p;
-#pragma unroll
-        for (int r = 0; r < G::NB; r++) zs[r] += ((I >> r) & 1) ? -p : p;
-      }
-    }
-  }
-};
+  for (int j = 0; j < NT; j++)
+    if ((tid >> j) & 1u) g |= (i64)1 << L[tbit[j]];
+  return g;
+}
 
-// Block reduction of the <Z> partials into zpart[tile][0..K] (tile bit j signed sums, K = total).
-template <typename T, int K, int R, int NTHR>
-__device__ __forceinline__ void z_reduce(void* smem, const typename Acc<T>::t zt, const typename Acc<T>::t* zs,
-                                         double* zrow, u32 tid, bool valid) {
-  typedef Geo<T, K, R, NTHR> G;
+// Block reduction of the <Z> partials of the last forward phase into zrow[0..K]: row[j] is the
+// signed sum over tile bit j, row[K] the tile total. zmap[j] >= 0: register bit; else thread bit -1-zmap[j].
+template <typename T, int K, int R, int NTHR, class Spec>
+__device__ __forceinline__ void z_reduce_regs(void* smem, typename Acc<T>::t zt, const typename Acc<T>::t* zs,
+                                              double* zrow, u32 tid, bool valid) {
   typedef typename Acc<T>::t A;
-  constexpr int NZ = G::NB + 2;
+  constexpr int NZ = R + 1;
   A* red = reinterpret_cast<A*>(smem);
   __syncthreads();
   red[tid * NZ] = zt;
 #pragma unroll
-  for (int r = 0; r < G::NB + 1; r++) red[tid * NZ + 1 + r] = zs[r];
+  for (int r = 0; r < R; r++) red[tid * NZ + 1 + r] = zs[r];
   __syncthreads();
-  constexpr int TID_LO = G::EPC == 2 ? 1 : 0;
   for (int j = tid; j <= K; j += NTHR) {
     double acc = 0.0;
     if (j == K) {
       for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ];
-    } else if (j >= TID_LO && j < TID_LO + G::LOGT) {
-      const int bit = j - TID_LO;
-      for (int u = 0; u < NTHR; u++) acc += ((u >> bit) & 1) ? -(double)red[u * NZ] : (double)red[u * NZ];
+    } else if (Spec::zmap(j) >= 0) {
+      const int r = Spec::zmap(j);
+      for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ + 1 + r];
     } else {
-      const int slot = (G::EPC == 2 && j == 0) ? 0 : (G::EPC == 2 ? 1 : 0) + (j - G::LO);
-      for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ + 1 + slot];
+      const int bit = -1 - Spec::zmap(j);
+      for (int u = 0; u < NTHR; u++) acc += ((u >> bit) & 1) ? -(double)red[u * NZ] : (double)red[u * NZ];
     }
     if (valid) zrow[j] = acc;
   }
 }
 
-// Shared-memory bytes of one tile group (forward): tile, then coefficients and forms.
+__device__ __forceinline__ void tile_coords(const Args& a, i64 tile, i64& b, i64& t, i64& base) {
+  b = tile / a.tps + a.b0;
+  t = tile - (b - a.b0) * a.tps;
+  base = b << a.n;
+  for (int j = 0; j < a.n_nonlocal; j++)
+    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
+}
+
+// ---------------------------------------------------------------- forward pass
+// Shared-memory bytes of one tile group (forward): tile (also the <Z> reduction area), coefficients, forms.
 template <typename T, int K, int NOPS>
 struct FwdGroupSmem {
   static constexpr int NO = NOPS > 0 ? NOPS : 1;
@@ -442,61 +367,33 @@ struct FwdGroupSmem {
   static constexpr int BYTES = (TILE + NO * (int)sizeof(T) + NO + 15) & ~15;
 };
 
-// One tile: tile index `tile` (sample = b0 + tile / tps) processed by the NTHR threads `tid` of a
-// group owning `smem`. Every thread of the CTA calls this together (barriers are CTA-wide); a group
-// with valid == false computes on another tile's data but writes nothing to global memory.
+// One tile (sample b0 + tile / tps) processed by the NTHR threads `tid` of a group owning `smem`.
+// Every thread of the CTA calls this together (barriers are CTA-wide); a group with valid == false
+// computes on another tile's data but writes nothing to global memory.
 template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void fwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
-  typedef Geo<T, K, R, NTHR> G;
-  void* tilep = smem;
-  T* cf = reinterpret_cast<T*>(smem + G::TILE);
-  u8* fmv = reinterpret_cast<u8*>(cf + (Spec::NOPS > 0 ? Spec::NOPS : 1));
-  const i64 b = tile / a.tps + a.b0;
-  const i64 t = tile - (b - a.b0) * a.tps;
-  i64 base = b << a.n;
-  for (int j = 0; j < a.n_nonlocal; j++)
-    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
+  typedef FwdGroupSmem<T, K, Spec::NOPS> SM;
+  T* cf = reinterpret_cast<T*>(smem + SM::TILE);
+  u8* fmv = reinterpret_cast<u8*>(cf + SM::NO);
+  Ctx<T> c;
+  c.a = &a;
+  c.tile = smem;
+  c.tile2 = nullptr;
+  c.cf = cf;
+  c.fm = fmv;
+  c.gq = nullptr;
+  c.tid = tid;
+  c.valid = valid;
+  tile_coords(a, tile, c.b, c.t, c.base);
   for (int i = tid; i < Spec::NOPS; i += NTHR) {
     const int g = a.op_gate[i];
     if (g >= 0) {
-      cf[i] = reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + b];
-      fmv[i] = a.form[(i64)g * a.B + b];
+      cf[i] = reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + c.b];
+      fmv[i] = a.form[(i64)g * a.B + c.b];
     }
   }
-  Chunks<T, K, R, NTHR> ch;
-  ch.init(a.L, tid);
-  if (a.in == nullptr) {
-    FwdZero<T, K, R, NTHR, Spec> f{tilep, Spec::lay_first((u32)G::EPC * tid)};
-    Unroll<0, G::NCH>::run(f);
-    __syncthreads();
-    if (tid == 0 && t == 0) reinterpret_cast<T*>(tilep)[0] = T(1);
-  } else {
-    FwdLoad<T, K, R, NTHR, Spec> f{reinterpret_cast<const T*>(a.in) + 2 * base, tilep, &ch,
-                                   Spec::lay_first((u32)G::EPC * tid)};
-    Unroll<0, G::NCH>::run(f);
-    cp_wait_all();
-  }
   __syncthreads();
-  Spec::template fwd_phases<T>(tilep, cf, fmv, tid);
-  ch.init(a.L, tid);
-  FwdStore<T, K, R, NTHR, Spec, true> st;
-  st.out = reinterpret_cast<T*>(a.out) + 2 * base;
-  st.tile = tilep;
-  st.ch = &ch;
-  st.s0 = Spec::lay_last((u32)G::EPC * tid);
-  st.scale = reinterpret_cast<const T*>(a.scale)[b];
-  st.valid = valid;
-  if (a.zpart) {
-    st.zt = 0;
-#pragma unroll
-    for (int r = 0; r < G::NB + 1; r++) st.zs[r] = 0;
-    Unroll<0, G::NCH>::run(st);
-    z_reduce<T, K, R, NTHR>(tilep, st.zt, st.zs, a.zpart + (b * a.tps + t) * (K + 1), tid, valid);
-  } else {
-    FwdStore<T, K, R, NTHR, Spec, false> s2;
-    s2.out = st.out; s2.tile = tilep; s2.ch = &ch; s2.s0 = st.s0; s2.scale = st.scale; s2.valid = valid;
-    Unroll<0, G::NCH>::run(s2);
-  }
+  Spec::template fwd_phases<T>(c);
 }
 
 template <typename T, int K, int R, int NTHR, class Spec>
@@ -506,69 +403,6 @@ __device__ __forceinline__ void fwd_pass(const Args& a) {
 }
 
 // ---------------------------------------------------------------- backward pass
-template <typename T, int K, int R, int NTHR, class Spec>
-struct BwdLoad {
-  typedef Geo<T, K, R, NTHR> G;
-  const T* pin; const T* lin; void* tp; void* tl; const Chunks<T, K, R, NTHR>* ch; u32 s0;
-  template <int I>
-  __device__ __forceinline__ void step() {
-    const u32 w = s0 ^ Spec::lay_last(ChunkElem<I, G::LO, G::NB>::v);
-    const i64 g = ch->template g<I>();
-    cp16(reinterpret_cast<char*>(tp) + (size_t)w * G::EL, pin + 2 * g);
-    if (lin) cp16(reinterpret_cast<char*>(tl) + (size_t)w * G::EL, lin + 2 * g);
-  }
-};
-
-// lambda = (sum_i g_i Z_i) psi at load: d(e) = dconst + sum_j (bit_j(e) ? -g_j : g_j)
-template <typename T, int K, int R, int NTHR, class Spec>
-struct BwdLambda {
-  typedef Geo<T, K, R, NTHR> G;
-  void* tp; void* tl; u32 s0; double dtid; const double* gq;
-  template <int I>
-  __device__ __forceinline__ void step() {
-    const u32 e = ChunkElem<I, G::LO, G::NB>::v;
-    double d = dtid;
-#pragma unroll
-    for (int r = 0; r < G::NB; r++) d += ((I >> r) & 1) ? -gq[G::LO + r] : gq[G::LO + r];
-#pragma unroll
-    for (int h = 0; h < G::EPC; h++) {
-      const double dh = (G::EPC == 2) ? (h ? d - gq[0] : d + gq[0]) : d;
-      const u32 w = s0 ^ Spec::lay_last(e) ^ (u32)h;
-      typedef typename Acc<T>::t A;
-      T* P = reinterpret_cast<T*>(tp) + 2 * w;
-      T* Lm = reinterpret_cast<T*>(tl) + 2 * w;
-      Lm[0] = (T)(dh * (double)P[0]);
-      Lm[1] = (T)(dh * (double)P[1]);
-    }
-  }
-};
-
-template <typename T, int K, int R, int NTHR, class Spec>
-struct BwdStore {
-  typedef Geo<T, K, R, NTHR> G;
-  T* pout; T* lout; const void* tp; const void* tl; const Chunks<T, K, R, NTHR>* ch; u32 s0; T scale;
-  template <int I>
-  __device__ __forceinline__ void step() {
-    const u32 w = s0 ^ Spec::lay_first(ChunkElem<I, G::LO, G::NB>::v);
-    const i64 g = ch->template g<I>();
-    if (G::EPC == 2) {
-      float4 v = reinterpret_cast<const float4*>(tp)[w >> 1];
-      float4 l = reinterpret_cast<const float4*>(tl)[w >> 1];
-      const float s = (float)scale;
-      v.x *= s; v.y *= s; v.z *= s; v.w *= s;
-      l.x *= s; l.y *= s; l.z *= s; l.w *= s;
-      *reinterpret_cast<float4*>(pout + 2 * g) = v;
-      *reinterpret_cast<float4*>(lout + 2 * g) = l;
-    } else {
-      double2 v = reinterpret_cast<const double2*>(tp)[w], l = reinterpret_cast<const double2*>(tl)[w];
-      const double s = (double)scale;
-      v.x *= s; v.y *= s; l.x *= s; l.y *= s;
-      *reinterpret_cast<double2*>(pout + 2 * g) = v;
-      *reinterpret_cast<double2*>(lout + 2 * g) = l;
-    }
-  }
-};
-
 // Shared-memory bytes of one tile group (backward): psi, lambda, gradient warp partials, g per tile
 // bit, coefficients and forms.
 template <typename T, int K, int R, int NTHR, int NOPS, int NGS>
@@ -587,76 +421,53 @@ struct BwdGroupSmem {
 
 template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
-  typedef Geo<T, K, R, NTHR> G;
   typedef typename Acc<T>::t A;
   typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS> SM;
-  constexpr int NW = SM::NW;
-  constexpr int NG = SM::NG;
-  void* tp = smem;
-  void* tl = smem + G::TILE;
   A* red = reinterpret_cast<A*>(smem + SM::RED);          // [NW][NG]
   double* gq = reinterpret_cast<double*>(smem + SM::GQ);  // [K + 1]
   T* cf = reinterpret_cast<T*>(smem + SM::CF);
   u8* fmv = smem + SM::FM;
-  const i64 b = tile / a.tps + a.b0;
-  const i64 t = tile - (b - a.b0) * a.tps;
-  i64 base = b << a.n;
-  for (int j = 0; j < a.n_nonlocal; j++)
-    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
+  Ctx<T> c;
+  c.a = &a;
+  c.tile = smem;
+  c.tile2 = smem + SM::TILE;
+  c.cf = cf;
+  c.fm = fmv;
+  c.gq = gq;
+  c.tid = tid;
+  c.valid = valid;
+  tile_coords(a, tile, c.b, c.t, c.base);
   for (int i = tid; i < Spec::NOPS; i += NTHR) {
     const int g = a.op_gate[i];
     if (g >= 0) {
-      cf[i] = -reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + b];   // inverse: negated coefficient
-      fmv[i] = a.form[(i64)g * a.B + b];
+      cf[i] = -reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + c.b];   // inverse: negated coefficient
+      fmv[i] = a.form[(i64)g * a.B + c.b];
     }
   }
-  const bool init_lambda = a.lam_in == nullptr;
-  if (init_lambda) {
+  if (a.lam_in == nullptr) {
     for (int j = tid; j <= K; j += NTHR) {
       if (j < K) {
-        gq[j] = a.grad_out[b * a.n + (a.n - 1 - a.L[j])];
+        gq[j] = a.grad_out[c.b * a.n + (a.n - 1 - a.L[j])];
       } else {
         double dc = 0.0;
         for (int q = 0; q < a.n_nonlocal; q++) {
-          const double g = a.grad_out[b * a.n + (a.n - 1 - a.nonlocal[q])];
-          dc += ((t >> q) & 1) ? -g : g;
+          const double g = a.grad_out[c.b * a.n + (a.n - 1 - a.nonlocal[q])];
+          dc += ((c.t >> q) & 1) ? -g : g;
         }
         gq[K] = dc;
       }
     }
   }
-  Chunks<T, K, R, NTHR> ch;
-  ch.init(a.L, tid);
-  const u32 sl = Spec::lay_last((u32)G::EPC * tid);
-  BwdLoad<T, K, R, NTHR, Spec> ld{reinterpret_cast<const T*>(a.in) + 2 * base,
-                                  init_lambda ? nullptr : reinterpret_cast<const T*>(a.lam_in) + 2 * base,
-                                  tp, tl, &ch, sl};
-  Unroll<0, G::NCH>::run(ld);
-  cp_wait_all();
   __syncthreads();
-  if (init_lambda) {
-    double dt = gq[K];
-    const u32 e0 = (u32)G::EPC * tid;
-#pragma unroll
-    for (int j = (G::EPC == 2 ? 1 : 0); j < G::LO; j++) dt += ((e0 >> j) & 1u) ? -gq[j] : gq[j];
-    BwdLambda<T, K, R, NTHR, Spec> lf{tp, tl, sl, dt, gq};
-    Unroll<0, G::NCH>::run(lf);
-    __syncthreads();
-  }
-  Spec::template bwd_phases<T>(tp, tl, cf, fmv, red, tid);
+  Spec::template bwd_phases<T>(c, red);
   __syncthreads();
-  ch.init(a.L, tid);
-  for (int s = tid; s < Spec::NGS; s += NTHR) {
+  constexpr int NW = SM::NW, NG = SM::NG;
+  for (int sl = tid; sl < Spec::NGS; sl += NTHR) {
     double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; w++) acc += (double)red[w * NG + s];
-    if (valid) a.gpart[((a.gpart_offset + s) * a.B + b) * a.tps + t] = acc;
+    for (int w = 0; w < NW; w++) acc += (double)red[w * NG + sl];
+    if (valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = acc;
   }
-  if (a.out == nullptr || !valid) return;
-  BwdStore<T, K, R, NTHR, Spec> st{reinterpret_cast<T*>(a.out) + 2 * base, reinterpret_cast<T*>(a.lam_out) + 2 * base,
-                                   tp, tl, &ch, Spec::lay_first((u32)G::EPC * tid),
-                                   reinterpret_cast<const T*>(a.scale)[b]};
-  Unroll<0, G::NCH>::run(st);
 }
 
 template <typename T, int K, int R, int NTHR, class Spec>

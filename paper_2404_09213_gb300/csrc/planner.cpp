@@ -161,41 +161,19 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
   d.lay0 = (int)s.layouts.size();
   std::vector<int> remaining = pp.gates;
   int gslot = 0;
-  while (!remaining.empty()) {
-    std::vector<int> regs = {0};   // tile bit 0 is always a register bit
-    std::set<int> blocked;
-    std::vector<int> taken, rest;
-    for (int gi : remaining) {
-      const Gate& g = s.gates[gi];
-      int q[2], nq;
-      gate_qubits(g, q, nq);
-      bool blk = false;
-      for (int i = 0; i < nq; i++) blk |= blocked.count(q[i]) > 0;
-      if (blk) {
-        for (int i = 0; i < nq; i++) blocked.insert(q[i]);
-        rest.push_back(gi);
-        continue;
-      }
-      std::vector<int> need;
-      if (g.type == QSIM_RX || g.type == QSIM_RY || g.type == QSIM_H || g.type == QSIM_X || g.type == QSIM_CNOT)
-        need.push_back(tb_of_q[g.t0]);
-      std::vector<int> merged = regs;
-      for (int t : need)
-        if (std::find(merged.begin(), merged.end(), t) == merged.end()) merged.push_back(t);
-      if ((int)merged.size() <= R) {
-        regs = merged;
-        taken.push_back(gi);
-      } else {
-        for (int i = 0; i < nq; i++) blocked.insert(q[i]);
-        rest.push_back(gi);
-      }
-    }
-    if (taken.empty()) {
-      err = "internal: register phase could not take any op";
-      return QSIM_ERR_ARG;
-    }
-    // pad the register set with the highest unused tile bits
+  // The first and the last register phase move their amplitudes straight between registers and global
+  // memory; keeping tile bits 1..3 (the low index bits of a contiguous run) out of their register sets
+  // makes lanes 0..7 of a warp cover one contiguous 128-byte run.
+  std::vector<int> edge_excl;
+  if (k - R >= 3)
+    for (int j = 1; j <= 3 && j < s.c; j++) edge_excl.push_back(j);
+  auto excluded = [&](int tb, bool edge) {
+    return edge && std::find(edge_excl.begin(), edge_excl.end(), tb) != edge_excl.end();
+  };
+  auto make_phase = [&](std::vector<int> regs, const std::vector<int>& taken, bool edge) {
     for (int j = k - 1; j >= 0 && (int)regs.size() < R; j--)
+      if (std::find(regs.begin(), regs.end(), j) == regs.end() && !excluded(j, edge)) regs.push_back(j);
+    for (int j = k - 1; j >= 0 && (int)regs.size() < R; j--)   // small tiles: any bit
       if (std::find(regs.begin(), regs.end(), j) == regs.end()) regs.push_back(j);
     std::sort(regs.begin() + 1, regs.end());
     DevPhase ph{};
@@ -255,7 +233,57 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
     }
     ph.op_end = (int)s.ops.size();
     s.phases.push_back(ph);
+  };
+  bool first = true;
+  while (!remaining.empty() || first) {
+    std::vector<int> regs = {0};   // tile bit 0 is always a register bit
+    std::set<int> blocked;
+    std::vector<int> taken, rest;
+    for (int gi : remaining) {
+      const Gate& g = s.gates[gi];
+      int q[2], nq;
+      gate_qubits(g, q, nq);
+      bool blk = false;
+      for (int i = 0; i < nq; i++) blk |= blocked.count(q[i]) > 0;
+      if (blk) {
+        for (int i = 0; i < nq; i++) blocked.insert(q[i]);
+        rest.push_back(gi);
+        continue;
+      }
+      std::vector<int> need;
+      if (g.type == QSIM_RX || g.type == QSIM_RY || g.type == QSIM_H || g.type == QSIM_X || g.type == QSIM_CNOT)
+        need.push_back(tb_of_q[g.t0]);
+      bool ok = true;
+      for (int t : need) ok = ok && !excluded(t, first);
+      std::vector<int> merged = regs;
+      for (int t : need)
+        if (std::find(merged.begin(), merged.end(), t) == merged.end()) merged.push_back(t);
+      if (ok && (int)merged.size() <= R) {
+        regs = merged;
+        taken.push_back(gi);
+      } else {
+        for (int i = 0; i < nq; i++) blocked.insert(q[i]);
+        rest.push_back(gi);
+      }
+    }
+    const bool last = rest.empty();
+    // a phase that is both first and last must respect the constraint; otherwise only the first does here
+    bool edge = first;
+    if (last && !first) {
+      bool viol = false;
+      for (int t : regs) viol = viol || excluded(t, true);
+      edge = !viol;   // respects the store constraint if it can; else an extra phase is added below
+    }
+    make_phase(regs, taken, first || (last && edge));
+    first = false;
     remaining = rest;
+  }
+  // the last phase stores to global memory: add an op-free phase if its register set breaks the rule
+  if (!edge_excl.empty()) {
+    const DevPhase& lp = s.phases.back();
+    bool viol = false;
+    for (int i = 0; i < R; i++) viol = viol || excluded(lp.rbit[i], true);
+    if (viol) make_phase({0}, {}, true);
   }
   d.n_phases = (int)s.phases.size() - d.phase0;
   d.n_ops = (int)s.ops.size() - d.op0;

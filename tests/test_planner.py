@@ -149,3 +149,17 @@ def test_empty_circuit_and_single_qubit(q):
     assert len(d["passes"]) == 1 and d["passes"][0]["gates"] == []
     d1 = q.Plan([W.gate(W.RX, (0,), param=0), W.gate(W.H, (0,))], 1).describe()
     assert d1["k"] == 1 and [ps["gates"] for ps in d1["passes"]] == [[0, 1]]
+
+
+@pytest.mark.parametrize("n,kw", [(20, {}), (16, {"dtype": "c128"}), (14, {"k": 10}), (13, {"k": 12})])
+def test_edge_phases_keep_the_contiguous_run_in_threads(q, n, kw):
+    # first and last register phase move data straight between registers and global memory: tile bits
+    # 1..3 (the low bits of a contiguous run) must be thread bits there so a warp's accesses coalesce
+    d = q.Plan(W.ring_ansatz(n, 3), n, **kw).describe()
+    for ps in d["passes"]:
+        for key, R in (("phases", d["R"]), ("bwd_phases", d["Rb"])):
+            if d["k"] - R < 3:
+                continue
+            for ph in (ps[key][0], ps[key][-1]):
+                assert not ({1, 2, 3} & set(ph["rbits"])), (key, ph["rbits"])
+                assert ph["tbits"][:3] == [1, 2, 3]
