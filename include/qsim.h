@@ -77,6 +77,9 @@ typedef struct {
                                 group starts (keeps a group's states in L2); 0 = the whole batch per launch */
   int32_t bwd_reg_bits;      /* amplitudes per thread in backward phases = 2^bits (0 = default: 4 for complex64,
                                 3 for complex128); more bits mean fewer shared-memory round trips per pass */
+  int32_t fwd_reg_bits;      /* amplitudes per thread in forward phases = 2^bits (0 = default: 5 for complex64,
+                                4 for complex128); fewer bits mean fewer registers and more resident warps */
+  int32_t reserved;          /* must be 0 */
   int32_t graph;             /* multi-circuit plans: capture each direction's launch sequence in a CUDA graph and
                                 replay it while the caller's buffers are unchanged (0 = plain launches) */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */

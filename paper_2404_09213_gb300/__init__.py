@@ -55,7 +55,8 @@ class Plan:
     """
 
     def __init__(self, gates, n_qubits, *, dtype="c64", mode="fused", k=0, contiguous_bits=0,
-                 checkpoint_passes=0, mem_budget_bytes=0, sample_block=0, bwd_reg_bits=0):
+                 checkpoint_passes=0, mem_budget_bytes=0, sample_block=0, bwd_reg_bits=0,
+                 fwd_reg_bits=0):
         L = _lib.lib()
         self.gates = list(gates)
         self.n = int(n_qubits)
@@ -71,6 +72,7 @@ class Plan:
         opts.mem_budget_bytes = mem_budget_bytes
         opts.sample_block = sample_block
         opts.bwd_reg_bits = bwd_reg_bits
+        opts.fwd_reg_bits = fwd_reg_bits
         h = ctypes.c_void_p()
         arr = gate_structs(self.gates)
         _lib.check(L.qsim_plan(arr, len(self.gates), self.n, ctypes.byref(opts), ctypes.byref(h)))

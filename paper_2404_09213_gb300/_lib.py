@@ -28,6 +28,7 @@ class QsimPlanOpts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("dtype", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("contiguous_bits", ctypes.c_int32), ("checkpoint_passes", ctypes.c_int32),
                 ("sample_block", ctypes.c_int32), ("bwd_reg_bits", ctypes.c_int32),
+                ("fwd_reg_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64)]
 
 

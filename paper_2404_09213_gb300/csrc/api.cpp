@@ -49,9 +49,7 @@ struct qsim_plan_s {
   bool uploaded = false;
   int32_t* d_exec_gates_b = nullptr;
   int32_t* d_exec_begin_b = nullptr;
-  uint8_t* d_bits = nullptr;            // per pass: L[k] then nonlocal[n-k]
-  int32_t* d_op_gate = nullptr;         // per pass: forward ops' gates, then backward ops' gates (-1: none)
-  std::vector<int64_t> off_bits, off_opf, off_opb;
+  std::vector<int32_t> h_exec_begin, h_exec_begin_b;   // first op of every pass in the packed coefficients
   JitPlan jit;
   int32_t* d_gate_type = nullptr;
   int32_t* d_gate_param = nullptr;
@@ -68,6 +66,10 @@ struct qsim_plan_s {
   std::vector<int> seg_begin;   // pass index where each checkpoint segment starts (+ end sentinel)
   void* coef = nullptr;
   uint8_t* form = nullptr;
+  void* cfp_f = nullptr;     // packed per-pass op coefficients [exec_begin[p] * B + b * n_ops + i] (forward)
+  uint8_t* fmp_f = nullptr;
+  void* cfp_b = nullptr;     // the same for the backward op lists, coefficients negated
+  uint8_t* fmp_b = nullptr;
   void* scale_f = nullptr;
   void* scale_b = nullptr;
   double* gm = nullptr;
@@ -140,12 +142,13 @@ struct qsim_plan_s {
   int64_t state_bytes(int B_) const { return (int64_t)B_ * ((int64_t)1 << s.n) * el; }
 
   void free_ws() {
-    void* ptrs[] = {coef, form, scale_f, scale_b, gm, zpart, gpart, G, W, Lam};
+    void* ptrs[] = {coef, form, cfp_f, fmp_f, cfp_b, fmp_b, scale_f, scale_b, gm, zpart, gpart, G, W, Lam};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     for (void* p : ckpt)
       if (p) cudaFree(p);
-    coef = form = nullptr;
+    coef = cfp_f = cfp_b = nullptr;
+    form = fmp_f = fmp_b = nullptr;
     scale_f = scale_b = nullptr;
     gm = zpart = gpart = G = nullptr;
     W = Lam = nullptr;
@@ -156,7 +159,7 @@ struct qsim_plan_s {
   void free_all() {
     free_ws();
     destroy_events();
-    void* ptrs[] = {d_bits, d_op_gate, d_gate_type, d_gate_param, d_exec_gates, d_exec_begin, d_exec_gates_b,
+    void* ptrs[] = {d_gate_type, d_gate_param, d_exec_gates, d_exec_begin, d_exec_gates_b,
                     d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Lnl_last};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -167,28 +170,12 @@ struct qsim_plan_s {
   int upload_schedule() {
     if (uploaded) return QSIM_OK;
     cudaError_t e = cudaSuccess;
-    std::vector<int32_t> gtype, gparam, exec, exec_begin, exec_b, exec_begin_b, op_gate;
-    std::vector<uint8_t> bits;
+    std::vector<int32_t> gtype, gparam, exec, exec_begin, exec_b, exec_begin_b;
     for (auto& g : s.gates) {
       gtype.push_back(g.type);
       gparam.push_back(g.param);
     }
     for (auto& pp : s.passes) {
-      off_bits.push_back((int64_t)bits.size());
-      for (int j = 0; j < pp.dev.k; j++) bits.push_back(pp.dev.L[j]);
-      for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.nonlocal[j]);
-      bits.push_back(0);
-      off_opf.push_back((int64_t)op_gate.size());
-      for (int i = 0; i < pp.dev.n_ops; i++) {
-        const DevOp& op = s.ops[pp.dev.op0 + i];
-        op_gate.push_back(op.rot ? op.gate : -1);
-      }
-      off_opb.push_back((int64_t)op_gate.size());
-      for (int i = 0; i < pp.devb.n_ops; i++) {
-        const DevOp& op = s.ops[pp.devb.op0 + i];
-        op_gate.push_back(op.rot ? op.gate : -1);
-      }
-      op_gate.push_back(-1);
       exec_begin.push_back((int32_t)exec.size());
       exec_begin_b.push_back((int32_t)exec_b.size());
       if (s.mode == QSIM_PER_GATE) {
@@ -201,6 +188,8 @@ struct qsim_plan_s {
     }
     exec_begin.push_back((int32_t)exec.size());
     exec_begin_b.push_back((int32_t)exec_b.size());
+    h_exec_begin = exec_begin;
+    h_exec_begin_b = exec_begin_b;
     n_occ = (int)s.grad_gate.size();
     std::vector<int32_t> occ_gate(s.grad_gate.begin(), s.grad_gate.end());
     std::vector<int64_t> occ_slot(n_occ);
@@ -225,8 +214,6 @@ struct qsim_plan_s {
     }
 #define QSIM_UP(PTR, VEC) \
   if (e == cudaSuccess) e = upload(&PTR, VEC);
-    QSIM_UP(d_bits, bits)
-    QSIM_UP(d_op_gate, op_gate)
     QSIM_UP(d_exec_gates_b, exec_b)
     QSIM_UP(d_exec_begin_b, exec_begin_b)
     QSIM_UP(d_gate_type, gtype)
@@ -269,6 +256,8 @@ struct qsim_plan_s {
       int64_t bytes;
     } items[] = {
         {&coef, G_ * B_ * sc}, {reinterpret_cast<void**>(&form), G_ * B_},
+        {&cfp_f, (int64_t)h_exec_begin.back() * B_ * sc}, {reinterpret_cast<void**>(&fmp_f), (int64_t)h_exec_begin.back() * B_},
+        {&cfp_b, (int64_t)h_exec_begin_b.back() * B_ * sc}, {reinterpret_cast<void**>(&fmp_b), (int64_t)h_exec_begin_b.back() * B_},
         {&scale_f, P_ * B_ * sc}, {&scale_b, P_ * B_ * sc},
         {reinterpret_cast<void**>(&gm), G_ * B_ * 8}, {reinterpret_cast<void**>(&zpart), zcount * 8},
         {reinterpret_cast<void**>(&gpart), s.total_gslots * B_ * tps() * 8},
@@ -325,12 +314,11 @@ struct qsim_plan_s {
   JitArgs jit_args(int p, bool bwd, const void* scale) const {
     JitArgs a{};
     const DevPass& d = bwd ? s.passes[p].devb : s.passes[p].dev;
-    a.coef = coef;
-    a.form = form;
-    a.op_gate = d_op_gate + (bwd ? off_opb[p] : off_opf[p]);
+    const int64_t e0 = (int64_t)(bwd ? h_exec_begin_b[p] : h_exec_begin[p]) * B;
+    a.cfp = static_cast<const char*>(bwd ? cfp_b : cfp_f) + e0 * sc;
+    a.fmp = (bwd ? fmp_b : fmp_f) + e0;
     a.scale = scale;
-    a.L = d_bits + off_bits[p];
-    a.nonlocal = d_bits + off_bits[p] + d.k;
+    set_bits(a, d);
     a.tps = d.tiles_per_sample;
     a.gpart_offset = d.gpart_offset;
     a.n_nonlocal = d.n_nonlocal;
@@ -397,12 +385,14 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
     if (o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   }
   p->opts = o;
-  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.sample_block < 0) {
+  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
+      o.sample_block < 0 || o.reserved != 0) {
     delete p;
-    return fail(QSIM_ERR_ARG, "bwd_reg_bits must be in [0, 5] and sample_block >= 0");
+    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, reserved == 0");
   }
+  const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
-  rc = build_schedule(gv, n_qubits, o, fwd_R_for(16, o.dtype), Rb, p->s, err);
+  rc = build_schedule(gv, n_qubits, o, Rf, Rb, p->s, err);
   if (rc) {
     delete p;
     return fail(rc, err);
@@ -515,6 +505,10 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   ca.P = p->P();
   ca.coef = p->coef;
   ca.form = p->form;
+  ca.cfp_f = p->cfp_f;
+  ca.fmp_f = p->fmp_f;
+  ca.cfp_b = p->cfp_b;
+  ca.fmp_b = p->fmp_b;
   ca.scale_f = p->scale_f;
   ca.scale_b = p->scale_b;
   ca.gm = p->gm;

@@ -266,6 +266,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           o << "        qj::ldg_pair(in + 2 * " << goff("gb", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
             << "], im[" << i + 1 << "]);\n";
         o << "      }\n";
+        o << "      qj::stage_fwd<T, " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
       } else {
         o << "      {\n        const T* in = reinterpret_cast<const T*>(a.in);\n";
         for (int i = 0; i < N; i += 2)
@@ -276,7 +277,8 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           o << "        qj::ldg_pair(li + 2 * " << goff("gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
             << "], lq[" << i + 1 << "]);\n";
         // lambda = d(e) psi, d(e) = gq[K] + sum_j (bit_j(e) ? -g_j : g_j)
-        o << "      } else {\n        double dt = c.gq[" << K << "];\n";
+        o << "      }\n      qj::stage_bwd<T, " << K << ", " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
+        o << "      if (a.lam_in == nullptr) {\n        double dt = c.gq[" << K << "];\n";
         for (int jb = 0; jb < Ph.n_tbits; jb++)
           o << "        dt += ((tid >> " << jb << ") & 1u) ? -c.gq[" << (int)Ph.tbit[jb] << "] : c.gq[" << (int)Ph.tbit[jb] << "];\n";
         for (int r = 0; r < R; r++) o << "        const double g" << r << " = c.gq[" << (int)Ph.rbit[r] << "];\n";
@@ -371,7 +373,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     }
     // ---- store
     if (last) {
-      o << "      const T sc = reinterpret_cast<const T*>(a.scale)[c.b];\n";
+      o << "      const T sc = c.cf[" << d.n_ops << "];\n";
       if (!bwd) {
         o << "      qj::scal<" << N << ">(re, im, sc);\n"
           << "      if (c.valid) {\n        T* out = reinterpret_cast<T*>(a.out);\n";
@@ -427,7 +429,7 @@ int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
 // Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
 size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
-  const size_t no = d.n_ops > 0 ? d.n_ops : 1;
+  const size_t no = (size_t)d.n_ops + 1;   // op coefficients + the pass scale
   if (!bwd) return (tile + no * sc + no + 15) & ~(size_t)15;
   const int nthr = 1 << (d.k - d.R);
   const size_t nw = (nthr + 31) / 32, ng = d.n_gslots > 0 ? d.n_gslots : 1;

@@ -17,19 +17,25 @@ struct JitArgs {
   void* out;
   const void* lam_in;
   void* lam_out;
-  const void* coef;
-  const uint8_t* form;
-  const int* op_gate;
+  const void* cfp;
+  const uint8_t* fmp;
   const void* scale;
   double* zpart;
   double* gpart;
   const double* grad_out;
-  const uint8_t* L;
-  const uint8_t* nonlocal;
   int64_t tps;
   int64_t gpart_offset;
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch (tiles cover samples b0, b0+1, ...)
+  uint8_t L[16];
+  uint8_t nonlocal[40];
 };
+static_assert(sizeof(JitArgs) == 168, "JitArgs must match qj::Args");
+
+// Physical bit positions of a pass into its kernel arguments.
+inline void set_bits(JitArgs& a, const DevPass& d) {
+  for (int j = 0; j < d.k; j++) a.L[j] = d.L[j];
+  for (int j = 0; j < d.n_nonlocal; j++) a.nonlocal[j] = d.nonlocal[j];
+}
 
 struct JitKernel {
   void* fn = nullptr;   // cudaKernel_t

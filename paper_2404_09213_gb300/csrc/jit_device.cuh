@@ -22,18 +22,17 @@ struct Args {
   void* out;             // forward: states out; backward: psi out (nullptr -> not stored)
   const void* lam_in;    // backward: lambda in (nullptr -> lambda = (sum_i g_i Z_i) psi)
   void* lam_out;         // backward: lambda out
-  const void* coef;      // [G * B] scaled-rotation coefficients
-  const u8* form;        // [G * B] 0: tangent form, 1: cotangent form
-  const int* op_gate;    // [n_ops] gate index of every op of this pass (-1: no coefficient)
+  const void* cfp;       // [B][n_ops] this pass's op coefficients per sample (backward: already negated)
+  const u8* fmp;         // [B][n_ops] 0: tangent form, 1: cotangent form
   const void* scale;     // [B] this pass's scale (forward) or inverse scale (backward)
   double* zpart;         // forward <Z> partials [(B * tps) x (K + 1)] or nullptr
   double* gpart;         // backward gradient partials
   const double* grad_out;   // backward: dL/d<Z> (B x n)
-  const u8* L;           // physical bit of every tile bit
-  const u8* nonlocal;    // physical bits outside the tile, ascending
   i64 tps;               // tiles per sample
   i64 gpart_offset;      // first gradient slot of this pass
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch
+  u8 L[16];              // physical bit of every tile bit
+  u8 nonlocal[40];       // physical bits outside the tile, ascending
 };
 
 __device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -197,57 +196,72 @@ __device__ __forceinline__ void scal(T* re, T* im, T s) {
 template <typename T> struct Acc { typedef float t; };
 template <> struct Acc<double> { typedef double t; };
 
+// Gradient inner products over the thread's N amplitude pairs. Four partial sums (by pair index mod 4)
+// keep the FMA dependency chains short; they are added in a fixed order.
+template <typename A>
+__device__ __forceinline__ A sum4(const A* g) { return (g[0] + g[1]) + (g[2] + g[3]); }
+
 template <int N, int S, typename T>
 __device__ __forceinline__ typename Acc<T>::t g_ry(const T* pr, const T* pi, const T* lr, const T* li) {
   typedef typename Acc<T>::t A;
-  A g = 0;
+  A g[4] = {0, 0, 0, 0};
+  int n = 0;
 #pragma unroll
   for (int i = 0; i < N; i++)
     if (!(i & S)) {
       const int j = i | S;   // Re(l1* p0) - Re(l0* p1)
-      g = fm((A)lr[j], (A)pr[i], g);
-      g = fm((A)li[j], (A)pi[i], g);
-      g = fm(-(A)lr[i], (A)pr[j], g);
-      g = fm(-(A)li[i], (A)pi[j], g);
+      A& h = g[n++ & 3];
+      h = fm((A)lr[j], (A)pr[i], h);
+      h = fm((A)li[j], (A)pi[i], h);
+      h = fm(-(A)lr[i], (A)pr[j], h);
+      h = fm(-(A)li[i], (A)pi[j], h);
     }
-  return g;
+  return sum4(g);
 }
 
 template <int N, int S, typename T>
 __device__ __forceinline__ typename Acc<T>::t g_rx(const T* pr, const T* pi, const T* lr, const T* li) {
   typedef typename Acc<T>::t A;
-  A g = 0;
+  A g[4] = {0, 0, 0, 0};
+  int n = 0;
 #pragma unroll
   for (int i = 0; i < N; i++)
     if (!(i & S)) {
       const int j = i | S;   // Im(l0* p1) + Im(l1* p0)
-      g = fm((A)lr[i], (A)pi[j], g);
-      g = fm(-(A)li[i], (A)pr[j], g);
-      g = fm((A)lr[j], (A)pi[i], g);
-      g = fm(-(A)li[j], (A)pr[i], g);
+      A& h = g[n++ & 3];
+      h = fm((A)lr[i], (A)pi[j], h);
+      h = fm(-(A)li[i], (A)pr[j], h);
+      h = fm((A)lr[j], (A)pi[i], h);
+      h = fm(-(A)li[j], (A)pr[i], h);
     }
-  return g;
+  return sum4(g);
 }
 
 template <int N, int S, typename T>
 __device__ __forceinline__ typename Acc<T>::t g_rz(const T* pr, const T* pi, const T* lr, const T* li) {
   typedef typename Acc<T>::t A;
-  A g0 = 0, g1 = 0;
+  A g[4] = {0, 0, 0, 0};   // [0], [1]: amplitudes with the bit clear; [2], [3]: set
+  int n0 = 0, n1 = 0;
 #pragma unroll
   for (int i = 0; i < N; i++) {
-    if (i & S) { g1 = fm((A)lr[i], (A)pi[i], g1); g1 = fm(-(A)li[i], (A)pr[i], g1); }
-    else       { g0 = fm((A)lr[i], (A)pi[i], g0); g0 = fm(-(A)li[i], (A)pr[i], g0); }
+    A& h = (i & S) ? g[2 + (n1++ & 1)] : g[n0++ & 1];
+    h = fm((A)lr[i], (A)pi[i], h);
+    h = fm(-(A)li[i], (A)pr[i], h);
   }
-  return g0 - g1;
+  return (g[0] + g[1]) - (g[2] + g[3]);
 }
 
 template <int N, typename T>
 __device__ __forceinline__ typename Acc<T>::t g_im(const T* pr, const T* pi, const T* lr, const T* li) {
   typedef typename Acc<T>::t A;
-  A g = 0;
+  A g[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int i = 0; i < N; i++) { g = fm((A)lr[i], (A)pi[i], g); g = fm(-(A)li[i], (A)pr[i], g); }
-  return g;
+  for (int i = 0; i < N; i++) {
+    A& h = g[i & 3];
+    h = fm((A)lr[i], (A)pi[i], h);
+    h = fm(-(A)li[i], (A)pr[i], h);
+  }
+  return sum4(g);
 }
 
 // Sum over the NTHR threads of a tile group. Groups are aligned blocks of NTHR lanes; when several
@@ -303,9 +317,9 @@ struct Ctx {
   const Args* a;
   void* tile;            // forward: the tile; backward: psi
   void* tile2;           // backward: lambda
-  const T* cf;
-  const u8* fm;
-  const double* gq;      // backward, lambda init: g of every tile bit, [K] = fixed-bit part
+  T* cf;                 // op coefficients of this tile's sample, [NOPS] = pass scale (shared memory)
+  u8* fm;                // op forms (shared memory)
+  double* gq;            // backward, lambda init: g of every tile bit, [K] = fixed-bit part
   i64 base;              // element offset of the tile (bits outside the tile) in the batched state
   i64 b, t;              // sample, tile within the sample
   u32 tid;
@@ -359,10 +373,11 @@ __device__ __forceinline__ void tile_coords(const Args& a, i64 tile, i64& b, i64
 }
 
 // ---------------------------------------------------------------- forward pass
-// Shared-memory bytes of one tile group (forward): tile (also the <Z> reduction area), coefficients, forms.
+// Shared-memory bytes of one tile group (forward): tile (also the <Z> reduction area), coefficients and
+// the pass scale (NOPS + 1 values), forms.
 template <typename T, int K, int NOPS>
 struct FwdGroupSmem {
-  static constexpr int NO = NOPS > 0 ? NOPS : 1;
+  static constexpr int NO = NOPS + 1;
   static constexpr int TILE = (2 * (int)sizeof(T)) << K;
   static constexpr int BYTES = (TILE + NO * (int)sizeof(T) + NO + 15) & ~15;
 };
@@ -374,26 +389,34 @@ template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void fwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
   typedef FwdGroupSmem<T, K, Spec::NOPS> SM;
   T* cf = reinterpret_cast<T*>(smem + SM::TILE);
-  u8* fmv = reinterpret_cast<u8*>(cf + SM::NO);
   Ctx<T> c;
   c.a = &a;
   c.tile = smem;
   c.tile2 = nullptr;
   c.cf = cf;
-  c.fm = fmv;
+  c.fm = reinterpret_cast<u8*>(cf + SM::NO);
   c.gq = nullptr;
   c.tid = tid;
   c.valid = valid;
   tile_coords(a, tile, c.b, c.t, c.base);
-  for (int i = tid; i < Spec::NOPS; i += NTHR) {
-    const int g = a.op_gate[i];
-    if (g >= 0) {
-      cf[i] = reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + c.b];
-      fmv[i] = a.form[(i64)g * a.B + c.b];
-    }
+  Spec::template fwd_phases<T>(c);   // the first phase issues its loads, then calls stage_fwd and syncs
+}
+
+// Per-tile constants into shared memory: op coefficients and forms of sample c.b, the pass scale in
+// slot NOPS. Called after the first phase has issued its global loads so the latencies overlap; the
+// caller synchronises before the first op.
+template <typename T, int NTHR, class Spec>
+__device__ __forceinline__ void stage_fwd(Ctx<T>& c) {
+  const Args& a = *c.a;
+  T* cf = c.cf;
+  u8* fm = c.fm;
+  const T* src = reinterpret_cast<const T*>(a.cfp) + c.b * Spec::NOPS;
+  const u8* fsrc = a.fmp + c.b * Spec::NOPS;
+  for (int i = c.tid; i < Spec::NOPS; i += NTHR) {
+    cf[i] = src[i];
+    fm[i] = fsrc[i];
   }
-  __syncthreads();
-  Spec::template fwd_phases<T>(c);
+  if (c.tid == (u32)(NTHR - 1)) cf[Spec::NOPS] = reinterpret_cast<const T*>(a.scale)[c.b];
 }
 
 template <typename T, int K, int R, int NTHR, class Spec>
@@ -410,7 +433,7 @@ struct BwdGroupSmem {
   typedef typename Acc<T>::t A;
   static constexpr int NW = (NTHR + 31) / 32;
   static constexpr int NG = NGS > 0 ? NGS : 1;
-  static constexpr int NO = NOPS > 0 ? NOPS : 1;
+  static constexpr int NO = NOPS + 1;
   static constexpr int TILE = (2 * (int)sizeof(T)) << K;
   static constexpr int RED = 2 * TILE;
   static constexpr int GQ = (RED + NW * NG * (int)sizeof(A) + 15) & ~15;
@@ -419,33 +442,23 @@ struct BwdGroupSmem {
   static constexpr int BYTES = (FM + NO + 15) & ~15;
 };
 
-template <typename T, int K, int R, int NTHR, class Spec>
-__device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
-  typedef typename Acc<T>::t A;
-  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS> SM;
-  A* red = reinterpret_cast<A*>(smem + SM::RED);          // [NW][NG]
-  double* gq = reinterpret_cast<double*>(smem + SM::GQ);  // [K + 1]
-  T* cf = reinterpret_cast<T*>(smem + SM::CF);
-  u8* fmv = smem + SM::FM;
-  Ctx<T> c;
-  c.a = &a;
-  c.tile = smem;
-  c.tile2 = smem + SM::TILE;
-  c.cf = cf;
-  c.fm = fmv;
-  c.gq = gq;
-  c.tid = tid;
-  c.valid = valid;
-  tile_coords(a, tile, c.b, c.t, c.base);
-  for (int i = tid; i < Spec::NOPS; i += NTHR) {
-    const int g = a.op_gate[i];
-    if (g >= 0) {
-      cf[i] = -reinterpret_cast<const T*>(a.coef)[(i64)g * a.B + c.b];   // inverse: negated coefficient
-      fmv[i] = a.form[(i64)g * a.B + c.b];
-    }
+// Backward per-tile constants: negated op coefficients, forms, the inverse pass scale (slot NOPS) and,
+// when lambda is formed on load, g of every tile bit ([K]: the fixed-bit part of the tile).
+template <typename T, int K, int NTHR, class Spec>
+__device__ __forceinline__ void stage_bwd(Ctx<T>& c) {
+  const Args& a = *c.a;
+  T* cf = c.cf;
+  u8* fm = c.fm;
+  const T* src = reinterpret_cast<const T*>(a.cfp) + c.b * Spec::NOPS;
+  const u8* fsrc = a.fmp + c.b * Spec::NOPS;
+  for (int i = c.tid; i < Spec::NOPS; i += NTHR) {
+    cf[i] = src[i];
+    fm[i] = fsrc[i];
   }
+  if (c.tid == (u32)(NTHR - 1)) cf[Spec::NOPS] = reinterpret_cast<const T*>(a.scale)[c.b];
   if (a.lam_in == nullptr) {
-    for (int j = tid; j <= K; j += NTHR) {
+    double* gq = c.gq;
+    for (int j = c.tid; j <= K; j += NTHR) {
       if (j < K) {
         gq[j] = a.grad_out[c.b * a.n + (a.n - 1 - a.L[j])];
       } else {
@@ -458,7 +471,23 @@ __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u3
       }
     }
   }
-  __syncthreads();
+}
+
+template <typename T, int K, int R, int NTHR, class Spec>
+__device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
+  typedef typename Acc<T>::t A;
+  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS> SM;
+  A* red = reinterpret_cast<A*>(smem + SM::RED);          // [NW][NG]
+  Ctx<T> c;
+  c.a = &a;
+  c.tile = smem;
+  c.tile2 = smem + SM::TILE;
+  c.cf = reinterpret_cast<T*>(smem + SM::CF);
+  c.fm = smem + SM::FM;
+  c.gq = reinterpret_cast<double*>(smem + SM::GQ);        // [K + 1]
+  c.tid = tid;
+  c.valid = valid;
+  tile_coords(a, tile, c.b, c.t, c.base);
   Spec::template bwd_phases<T>(c, red);
   __syncthreads();
   constexpr int NW = SM::NW, NG = SM::NG;

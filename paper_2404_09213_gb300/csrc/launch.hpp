@@ -26,6 +26,12 @@ struct CoefArgs {
   int n_inputs, B, P;
   void* coef;                   // [G * B]
   uint8_t* form;                // [G * B]
+  void* cfp_f;                  // packed forward op coefficients: pass p, sample b, op i at
+                                //   exec_begin[p] * B + b * (ops of p) + i (0 for ops without one)
+  uint8_t* fmp_f;               // packed forward forms, same index
+  void* cfp_b;                  // packed backward op coefficients (negated: the inverse rotation), indexed
+                                //   by exec_begin_b like cfp_f
+  uint8_t* fmp_b;
   void* scale_f;                // [P * B]
   void* scale_b;                // [P * B]
   double* gm;                   // [G * B] squared backward scale at each rotation

@@ -82,8 +82,8 @@ struct qsim_multi_s {
           *d_exbb = nullptr, *d_pass_circ = nullptr, *d_ninp = nullptr;
   int64_t *d_circ_param_off = nullptr, *d_circ_col_off = nullptr, *d_zq_off = nullptr;
   uint8_t* d_bits = nullptr;
-  int32_t* d_op_gate = nullptr;
-  std::vector<int64_t> off_bits, off_opf, off_opb;   // per global pass
+  std::vector<int64_t> off_bits;                     // per global pass
+  std::vector<int32_t> h_exbf, h_exbb;               // first op of every global pass in the packed coefficients
   int n_occ = 0;
   int32_t *d_occ_gate = nullptr, *d_p_ptr = nullptr, *d_p_occ = nullptr, *d_i_ptr = nullptr, *d_i_occ = nullptr,
           *d_col_stride = nullptr, *d_col_index = nullptr;
@@ -93,6 +93,8 @@ struct qsim_multi_s {
   int B = -1;
   void *coef = nullptr, *scale_f = nullptr, *scale_b = nullptr, *W = nullptr, *Lam = nullptr;
   uint8_t* form = nullptr;
+  void *cfp_f = nullptr, *cfp_b = nullptr;           // packed per-pass op coefficients (backward: negated)
+  uint8_t *fmp_f = nullptr, *fmp_b = nullptr;
   double *gm = nullptr, *zpart = nullptr, *gpart = nullptr, *G = nullptr;
   int64_t *d_occ_base = nullptr, *d_occ_tps = nullptr;
   ZCirc* d_zcirc = nullptr;
@@ -124,12 +126,12 @@ struct qsim_multi_s {
   int P(int c) const { return (int)sch[c].passes.size(); }
 
   void free_ws() {
-    void* ps[] = {coef, scale_f, scale_b, W, Lam, form, gm, zpart, gpart, G, d_occ_base, d_occ_tps, d_zcirc,
+    void* ps[] = {coef, cfp_f, cfp_b, fmp_f, fmp_b, scale_f, scale_b, W, Lam, form, gm, zpart, gpart, G, d_occ_base, d_occ_tps, d_zcirc,
                   d_items_f, d_items_b, d_counters, d_heads, d_status, d_args_f, d_args_b};
     for (void* p : ps)
       if (p) cudaFree(p);
-    coef = scale_f = scale_b = W = Lam = nullptr;
-    form = nullptr;
+    coef = cfp_f = cfp_b = scale_f = scale_b = W = Lam = nullptr;
+    form = fmp_f = fmp_b = nullptr;
     gm = zpart = gpart = G = nullptr;
     d_occ_base = d_occ_tps = nullptr;
     d_zcirc = nullptr;
@@ -150,7 +152,7 @@ struct qsim_multi_s {
   void free_all() {
     free_ws();
     void* ps[] = {d_gtype, d_gparam, d_exf, d_exbf, d_exb, d_exbb, d_pass_circ, d_ninp, d_circ_param_off,
-                  d_circ_col_off, d_zq_off, d_bits, d_op_gate, d_occ_gate, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ,
+                  d_circ_col_off, d_zq_off, d_bits, d_occ_gate, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ,
                   d_col_stride, d_col_index, d_col_circ_off};
     for (void* p : ps)
       if (p) cudaFree(p);
@@ -162,7 +164,7 @@ struct qsim_multi_s {
 
   int upload() {
     if (uploaded) return QSIM_OK;
-    std::vector<int32_t> gtype, gparam, exf, exbf, exb, exbb, pass_circ, ninp, op_gate, p_ptr, p_occ, i_ptr, i_occ,
+    std::vector<int32_t> gtype, gparam, exf, exbf, exb, exbb, pass_circ, ninp, p_ptr, p_occ, i_ptr, i_occ,
         col_stride, col_index, occ_gate;
     std::vector<int64_t> cpo, cco, zqo, col_circ_off;
     std::vector<uint8_t> bits;
@@ -189,17 +191,6 @@ struct qsim_multi_s {
         for (int j = 0; j < pp.dev.k; j++) bits.push_back(pp.dev.L[j]);
         for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.nonlocal[j]);
         bits.push_back(0);
-        off_opf.push_back((int64_t)op_gate.size());
-        for (int i = 0; i < pp.dev.n_ops; i++) {
-          const DevOp& op = s.ops[pp.dev.op0 + i];
-          op_gate.push_back(op.rot ? (int32_t)(goff[c] + op.gate) : -1);
-        }
-        off_opb.push_back((int64_t)op_gate.size());
-        for (int i = 0; i < pp.devb.n_ops; i++) {
-          const DevOp& op = s.ops[pp.devb.op0 + i];
-          op_gate.push_back(op.rot ? (int32_t)(goff[c] + op.gate) : -1);
-        }
-        op_gate.push_back(-1);
       }
       for (size_t j = 0; j < s.grad_gate.size(); j++) {
         const int g = s.grad_gate[j];
@@ -219,6 +210,8 @@ struct qsim_multi_s {
     }
     exbf.push_back((int32_t)exf.size());
     exbb.push_back((int32_t)exb.size());
+    h_exbf = exbf;
+    h_exbb = exbb;
     for (int c = 0; c <= C; c++) zqo.push_back(zq_off[c]);
     p_ptr.push_back(0);
     for (auto& l : p_list) {
@@ -237,7 +230,7 @@ struct qsim_multi_s {
     QSIM_UP(d_gtype, gtype) QSIM_UP(d_gparam, gparam) QSIM_UP(d_exf, exf) QSIM_UP(d_exbf, exbf)
     QSIM_UP(d_exb, exb) QSIM_UP(d_exbb, exbb) QSIM_UP(d_pass_circ, pass_circ) QSIM_UP(d_ninp, ninp)
     QSIM_UP(d_circ_param_off, cpo) QSIM_UP(d_circ_col_off, cco) QSIM_UP(d_zq_off, zqo) QSIM_UP(d_bits, bits)
-    QSIM_UP(d_op_gate, op_gate) QSIM_UP(d_occ_gate, occ_gate) QSIM_UP(d_p_ptr, p_ptr) QSIM_UP(d_p_occ, p_occ)
+    QSIM_UP(d_occ_gate, occ_gate) QSIM_UP(d_p_ptr, p_ptr) QSIM_UP(d_p_occ, p_occ)
     QSIM_UP(d_i_ptr, i_ptr) QSIM_UP(d_i_occ, i_occ) QSIM_UP(d_col_stride, col_stride)
     QSIM_UP(d_col_index, col_index) QSIM_UP(d_col_circ_off, col_circ_off)
 #undef QSIM_UP
@@ -309,6 +302,8 @@ struct qsim_multi_s {
       void** p;
       int64_t bytes;
     } al[] = {{&coef, G_tot * B_ * sc}, {reinterpret_cast<void**>(&form), G_tot * B_},
+              {&cfp_f, (int64_t)h_exbf.back() * B_ * sc}, {reinterpret_cast<void**>(&fmp_f), (int64_t)h_exbf.back() * B_},
+              {&cfp_b, (int64_t)h_exbb.back() * B_ * sc}, {reinterpret_cast<void**>(&fmp_b), (int64_t)h_exbb.back() * B_},
               {&scale_f, P_tot * B_ * sc}, {&scale_b, P_tot * B_ * sc},
               {reinterpret_cast<void**>(&gm), G_tot * B_ * 8}, {reinterpret_cast<void**>(&zpart), zp_off[C] * 8},
               {reinterpret_cast<void**>(&gpart), gp_off[C] * 8}, {reinterpret_cast<void**>(&G), (int64_t)n_occ * B_ * 8},
@@ -344,12 +339,11 @@ struct qsim_multi_s {
     const DevPass& d = bwd ? sch[c].passes[p].devb : sch[c].passes[p].dev;
     const int64_t gp = poff[c] + p;
     const int64_t amp0 = amp_off[c] * B;
-    a.coef = coef;
-    a.form = form;
-    a.op_gate = d_op_gate + (bwd ? off_opb[gp] : off_opf[gp]);
+    const int64_t e0 = (int64_t)(bwd ? h_exbb[gp] : h_exbf[gp]) * B;
+    a.cfp = static_cast<const char*>(bwd ? cfp_b : cfp_f) + e0 * sc;
+    a.fmp = (bwd ? fmp_b : fmp_f) + e0;
     a.scale = reinterpret_cast<const char*>(bwd ? scale_b : scale_f) + (size_t)gp * B * sc;
-    a.L = d_bits + off_bits[gp];
-    a.nonlocal = d_bits + off_bits[gp] + d.k;
+    set_bits(a, d);
     a.tps = d.tiles_per_sample;
     a.gpart_offset = d.gpart_offset;
     a.n_nonlocal = d.n_nonlocal;
@@ -389,6 +383,8 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
   if (opts) o = *opts;
   if (o.mode != QSIM_FUSED) return mfail(QSIM_ERR_ARG, "multi-circuit plans use the fused mode");
   if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return mfail(QSIM_ERR_ARG, "bad dtype");
+  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR || o.reserved != 0)
+    return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5] and reserved == 0");
   if (o.k == 0 || o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   auto* m = new qsim_multi_s();
   m->opts = o;
@@ -413,8 +409,9 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
     }
     Schedule s;
     if (!rc) {
+      const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
       const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
-      rc = build_schedule(gv, n_qubits[c], o, fwd_R_for(16, o.dtype), Rb, s, err);
+      rc = build_schedule(gv, n_qubits[c], o, Rf, Rb, s, err);
     }
     if (rc) {
       delete m;
@@ -472,6 +469,10 @@ static cudaError_t multi_enqueue_fwd(qsim_multi_t m, const void* d_params, const
   ca.P = (int)m->P_tot;
   ca.coef = m->coef;
   ca.form = m->form;
+  ca.cfp_f = m->cfp_f;
+  ca.fmp_f = m->fmp_f;
+  ca.cfp_b = m->cfp_b;
+  ca.fmp_b = m->fmp_b;
   ca.scale_f = m->scale_f;
   ca.scale_b = m->scale_b;
   ca.gm = m->gm;

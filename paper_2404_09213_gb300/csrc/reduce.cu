@@ -30,10 +30,14 @@ __global__ void coef_kernel(CoefArgs a) {
   }
   T* coef = reinterpret_cast<T*>(a.coef);
   const int e0 = a.exec_begin[p], e1 = a.exec_begin[p + 1];
+  T* cfp = reinterpret_cast<T*>(a.cfp_f) + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
+  uint8_t* fmp = a.fmp_f + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
   double fs = 1.0;
   for (int e = e0; e < e1; e++) {
     const int g = a.exec_gates[e];
     const int ty = a.gate_type[g];
+    T v = 0;
+    uint8_t f = 0;
     if (ty <= QSIM_RZ) {
       const int pr = a.gate_param[g];
       const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
@@ -41,27 +45,36 @@ __global__ void coef_kernel(CoefArgs a) {
       sincos(0.5 * th, &s, &c);
       const int64_t gi = (int64_t)g * a.B + b;
       if (fabs(s) <= fabs(c)) {
-        coef[gi] = (T)(s / c);
-        a.form[gi] = 0;
+        v = (T)(s / c);
         fs *= c;
       } else {
-        coef[gi] = (T)(c / s);
-        a.form[gi] = 1;
+        v = (T)(c / s);
+        f = 1;
         fs *= s;
       }
+      coef[gi] = v;
+      a.form[gi] = f;
     } else if (ty == QSIM_H) {
       fs *= 0.70710678118654752440;
     }
+    cfp[e] = v;
+    fmp[e] = f;
   }
   reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)fs;
   // backward: ops undone in reverse order of the backward op list; gm = (product of inverse scales so far)^2
   double bs = 1.0;
   const int b0 = a.exec_begin_b[p], b1 = a.exec_begin_b[p + 1];
+  T* cfpb = reinterpret_cast<T*>(a.cfp_b) + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
+  uint8_t* fmpb = a.fmp_b + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
   for (int e = b1 - 1; e >= b0; e--) {
     const int g = a.exec_gates_b[e];
     const int ty = a.gate_type[g];
+    cfpb[e] = 0;
+    fmpb[e] = 0;
     if (ty <= QSIM_RZ) {
       const int64_t gi = (int64_t)g * a.B + b;
+      cfpb[e] = -coef[gi];   // the inverse rotation
+      fmpb[e] = a.form[gi];
       a.gm[gi] = bs * bs;
       const int pr = a.gate_param[g];
       const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
