@@ -79,6 +79,12 @@ def max_over_ranks(x, world, device):
     return float(t.item())
 
 
+def replica_value(world, samples_per_rank, steps, ms_max):
+    """Whole-job samples/s of `world` replicas, each processing `samples_per_rank` samples per step,
+    timed by the slowest rank (ms_max over `steps` steps)."""
+    return world * samples_per_rank * steps / (ms_max / 1e3)
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -215,7 +221,11 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     wl = W.config(3, batch=args.batch)
-    plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=args.k, contiguous_bits=args.contiguous_bits)
+    k, autotune = args.k, None
+    if args.mode == "fused" and k == 0:   # tile size from the library's autotuner (untimed setup)
+        k, ms = q.autotune(wl.gates, wl.n, wl.batch, reps=2, contiguous_bits=args.contiguous_bits)
+        autotune = {"k_candidates": [10, 11, 12], "ms_per_fwd_bwd": ms, "chosen_k": k}
+    plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits)
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
     x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
@@ -254,7 +264,7 @@ def run_ours(args, world, rank, local):
     fwd_ms, bwd_ms, nf, nb = plan.read_profile()
     plan.set_profiling(0)
     ms_max = max_over_ranks(ms, world, dev)
-    value = world * B * args.steps / (ms_max / 1e3)
+    value = replica_value(world, B, args.steps, ms_max)
 
     # roofline of the dominant kernel (fused backward pass kernel in fused mode)
     peak, peak_kind = load_peaks()
@@ -308,14 +318,15 @@ def run_ours(args, world, rank, local):
         sec = max_over_ranks(t1 - t0, world, dev)
         h2d = hp.numel() * 4 + hx.numel() * 4 + hg.numel() * 8
         d2h = hz.numel() * 8 + hdp.numel() * 8 + hdi.numel() * 8
-        e2e = {"value": world * B * args.steps / sec, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e = {"value": replica_value(world, B, args.steps, sec * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 state, fp64 reductions)",
            "data": "synthetic (seeded splitmix64 angles and loss weights)",
            "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": B, "gates": len(wl.gates),
-                      "params": wl.n_params, "mode": args.mode, "k": desc["k"], "contiguous_bits": desc["c"],
+                      "params": wl.n_params, "mode": args.mode, "k": desc["k"], "autotune": autotune,
+                      "contiguous_bits": desc["c"],
                       "l2": "inputs larger than L2: 512 MiB state per step (L2 129 MB), no flush needed",
                       "parallelism": f"replicas x{world}"},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
@@ -336,7 +347,9 @@ def run_other(args, world, rank, local):
     if args.workload == "c4":
         wls = W.multi_circuit_config()
         B = 4
-        mp = q.MultiPlan([(w.gates, w.n) for w in wls], graph=True)
+        circuits = [(w.gates, w.n) for w in wls]
+        ks = q.multi_autotune(circuits, B, reps=2)   # per qubit count (untimed setup)
+        mp = q.MultiPlan(circuits, graph=True, ks=ks)
         p = torch.tensor(np.concatenate([w.params for w in wls]), dtype=torch.float32, device=dev)
         x = torch.tensor(np.concatenate([w.inputs.ravel() for w in wls]), dtype=torch.float32, device=dev)
         g = torch.tensor(np.concatenate([w.grad_out.ravel() for w in wls]), dtype=torch.float64, device=dev)
@@ -353,13 +366,14 @@ def run_other(args, world, rank, local):
         # algorithmic bytes of every pass (complex64): forward 16 B/amp (8 for the |0> start),
         # backward 32 B/amp (24 for the first, 16 for the last)
         tot = 0
-        for w in wls:
-            P = q.Plan(w.gates, w.n).info()["n_passes"]
+        for w, kc in zip(wls, ks):
+            P = q.Plan(w.gates, w.n, k=kc).info()["n_passes"]
             amps = B * (1 << w.n)
             tot += amps * (8 + 16 * (P - 1))
             tot += amps * (8 if P == 1 else 24 + 16 + 32 * (P - 2))
         name = "C4: 256 circuits, 8..22 qubits (log-uniform), depth 4..16, HEA (RY,RZ + CZ ladder), batch 4, c64, fwd+bwd"
-        extra = {"circuits": len(wls), "batch_per_circuit": B, "queue": mp.info(), "graph": True}
+        extra = {"circuits": len(wls), "batch_per_circuit": B, "graph": True,
+                 "k_by_qubits": {str(w.n): kc for w, kc in sorted(zip(wls, ks), key=lambda t: t[0].n)}}
     elif args.workload == "c5":
         wl = W.config(5)
         B = 1
@@ -396,6 +410,8 @@ def run_other(args, world, rank, local):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    if args.workload == "c4":
+        extra["queue"] = mp.info()
     clk = ClockSampler(local)
     time.sleep(0.3)
     launches0 = q.kernel_launches()

@@ -79,7 +79,9 @@ typedef struct {
                                 3 for complex128); more bits mean fewer shared-memory round trips per pass */
   int32_t fwd_reg_bits;      /* amplitudes per thread in forward phases = 2^bits (0 = default: 5 for complex64,
                                 4 for complex128); fewer bits mean fewer registers and more resident warps */
-  int32_t reserved;          /* must be 0 */
+  int32_t weight_remap;      /* 1: every trainable angle enters as theta' = pi * tanh(theta) (quantum weight
+                                remapping, Sec. "Additional Optimizations"), dparams are dL/dtheta through
+                                that map; inputs are used as given. 0: angles as given */
   int32_t graph;             /* multi-circuit plans: capture each direction's launch sequence in a CUDA graph and
                                 replay it while the caller's buffers are unchanged (0 = plain launches) */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
@@ -204,7 +206,9 @@ int qsim_expval_z_noalloc(const void* d_states, int32_t batch, int32_t n_qubits,
 typedef struct qsim_multi_s* qsim_multi_t;
 
 int qsim_multi_plan(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
-                    int32_t n_circuits, const qsim_plan_opts* opts, qsim_multi_t* out);
+                    int32_t n_circuits, const qsim_plan_opts* opts, const int32_t* h_k, qsim_multi_t* out);
+/*   h_k: NULL (every circuit uses opts->k), or one k per circuit (host, n_circuits entries, each in
+ *   [1, 12] for complex64 / [1, 11] for complex128), e.g. from qsim_multi_autotune. */
 
 /* Element offsets of every circuit's block for batch size `batch`; each array (n_circuits + 1
  * entries, the last = total) may be NULL. */
@@ -230,6 +234,26 @@ int qsim_multi_set_test_hooks(qsim_multi_t plan, int64_t withhold_item, int64_t 
 void qsim_multi_destroy(qsim_multi_t plan);
 
 /* Free the plan and its device workspace (synchronizes the plan's last stream). NULL is a no-op. */
+/* Tile-size autotuner (the fused pass's k). Plans the circuit with *opts for each candidate k in
+ * {max_k - 2, max_k - 1, max_k} (max_k = 12 complex64, 11 complex128), runs one untimed forward
+ * (+ backward when with_backward != 0; this also compiles the kernels) and then `reps` timed calls
+ * on zero-filled scratch buffers of `batch` samples that it allocates and frees itself (run time
+ * does not depend on the values), and writes the fastest k to opts->k. n_qubits <= max_k: opts->k =
+ * n_qubits (one pass), nothing is run. h_ms: NULL or 3 floats, mean ms per call of each candidate
+ * (-1 when not run). Synchronises `stream`. Errors: those of qsim_plan / qsim_forward /
+ * qsim_backward, QSIM_ERR_OOM for scratch. In the paper the maximum group width is a fixed
+ * argument of the greedy splitter (Sec. "Circuit Splitting", typically 3 to 6 qubits); here the
+ * width is measured per circuit and batch. */
+int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, int32_t batch,
+                  int32_t with_backward, int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream);
+
+/* Per-circuit k for qsim_multi_plan: qsim_autotune on the first circuit of every distinct qubit
+ * count (same batch, opts as the base), the result copied to every circuit of that count.
+ * h_k: n_circuits int32 (host, written). */
+int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
+                        int32_t n_circuits, int32_t batch, int32_t with_backward, int32_t reps,
+                        const qsim_plan_opts* opts, int32_t* h_k, void* stream);
+
 void qsim_plan_destroy(qsim_plan_t plan);
 
 /* Message of the last failed call on this thread ("" if none). */

@@ -18,6 +18,7 @@ It computes, plainly and slowly, what the accelerated path computes:
                 mentions both; the reading that the shift rule is exact, not a finite difference,
                 is recorded in the design notes).
 * ``bitsim``    a pure-Python per-basis-index simulator used only to pin the other two on tiny inputs.
+* ``remapping`` quantum weight remapping angle = pi * tanh(weight) and its chain rule (Section III-C).
 
 Every function here is pinned by tests in ``tests/test_oracle_pins.py`` against closed forms,
 library routines (scipy ``expm``) and brute force; none is "parity unpinned".
@@ -28,7 +29,9 @@ from .kron import simulate_kron
 from .strided import simulate_strided
 from .measure import expval_z, expval_zz
 from .grad import loss, grad_param_shift, grad_finite_diff, forward_z
+from .remapping import remap, remap_slope, forward_z_remapped, grad_remapped
 
 __all__ = ["gate_matrix_2x2", "expand_1q", "expand_controlled", "full_gate_matrix", "rx", "ry",
            "rz", "hadamard", "pauli_x", "gate_angle", "simulate_kron", "simulate_strided",
-           "expval_z", "expval_zz", "loss", "grad_param_shift", "grad_finite_diff", "forward_z"]
+           "expval_z", "expval_zz", "loss", "grad_param_shift", "grad_finite_diff", "forward_z",
+           "remap", "remap_slope", "forward_z_remapped", "grad_remapped"]

@@ -51,12 +51,13 @@ class Plan:
 
     ``dtype`` "c64" (complex64 state, float32 angles) or "c128"; ``mode`` "fused" or "per_gate";
     ``k`` qubits per fused pass (default 12 for c64, 11 for c128); ``checkpoint_passes`` > 0 stores
-    the forward state every that many passes for the backward to restart from.
+    the forward state every that many passes for the backward to restart from; ``weight_remap``
+    feeds every trainable weight w in as the angle pi * tanh(w) (gradients are dL/dw).
     """
 
     def __init__(self, gates, n_qubits, *, dtype="c64", mode="fused", k=0, contiguous_bits=0,
                  checkpoint_passes=0, mem_budget_bytes=0, sample_block=0, bwd_reg_bits=0,
-                 fwd_reg_bits=0):
+                 fwd_reg_bits=0, weight_remap=False):
         L = _lib.lib()
         self.gates = list(gates)
         self.n = int(n_qubits)
@@ -73,6 +74,7 @@ class Plan:
         opts.sample_block = sample_block
         opts.bwd_reg_bits = bwd_reg_bits
         opts.fwd_reg_bits = fwd_reg_bits
+        opts.weight_remap = 1 if weight_remap else 0
         h = ctypes.c_void_p()
         arr = gate_structs(self.gates)
         _lib.check(L.qsim_plan(arr, len(self.gates), self.n, ctypes.byref(opts), ctypes.byref(h)))
@@ -204,7 +206,7 @@ class MultiPlan:
     in circuit order; :meth:`offsets` gives the element offsets of every block for a batch size.
     """
 
-    def __init__(self, circuits, *, dtype="c64", k=0, graph=False):
+    def __init__(self, circuits, *, dtype="c64", k=0, graph=False, ks=None, weight_remap=False):
         L = _lib.lib()
         self.circuits = [(list(g), int(n)) for g, n in circuits]
         self.dtype = dtype
@@ -219,8 +221,10 @@ class MultiPlan:
         opts.k = k
         opts.dtype = self._code
         opts.graph = 1 if graph else 0
+        opts.weight_remap = 1 if weight_remap else 0
         h = ctypes.c_void_p()
-        _lib.check(L.qsim_multi_plan(lists, ng, nq, C, ctypes.byref(opts), ctypes.byref(h)))
+        kv = None if ks is None else (ctypes.c_int32 * C)(*[int(x) for x in ks])
+        _lib.check(L.qsim_multi_plan(lists, ng, nq, C, ctypes.byref(opts), kv, ctypes.byref(h)))
         self._h = h
         self._keep = arrs
         self._saved = None
@@ -276,6 +280,39 @@ class MultiPlan:
 
     def set_test_hooks(self, withhold_item=-1, timeout_ns=0):
         _lib.check(_lib.lib().qsim_multi_set_test_hooks(self._h, withhold_item, timeout_ns))
+
+
+def _opts(dtype, **kw):
+    opts = _lib.QsimPlanOpts()
+    _lib.lib().qsim_default_opts(ctypes.byref(opts))
+    opts.dtype = _DT[dtype][0]
+    for k, v in kw.items():
+        setattr(opts, k, v)
+    return opts
+
+
+def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64", stream=None, **opts):
+    """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate])."""
+    o = _opts(dtype, **opts)
+    ms = (ctypes.c_float * 3)()
+    arr = gate_structs(gates)
+    _lib.check(_lib.lib().qsim_autotune(arr, len(gates), int(n_qubits), int(batch), int(bool(with_backward)),
+                                        int(reps), ctypes.byref(o), ms, _stream(stream)))
+    return int(o.k), [float(x) for x in ms]
+
+
+def multi_autotune(circuits, batch, *, with_backward=True, reps=2, dtype="c64", stream=None):
+    """Per-circuit k for :class:`MultiPlan` (``qsim_multi_autotune``); ``circuits``: [(gates, n)]."""
+    C = len(circuits)
+    arrs = [gate_structs(g) for g, _ in circuits]
+    lists = (ctypes.POINTER(_lib.QsimGate) * C)(*[ctypes.cast(a, ctypes.POINTER(_lib.QsimGate)) for a in arrs])
+    ng = (ctypes.c_int32 * C)(*[len(g) for g, _ in circuits])
+    nq = (ctypes.c_int32 * C)(*[int(n) for _, n in circuits])
+    ks = (ctypes.c_int32 * C)()
+    o = _opts(dtype)
+    _lib.check(_lib.lib().qsim_multi_autotune(lists, ng, nq, C, int(batch), int(bool(with_backward)), int(reps),
+                                              ctypes.byref(o), ks, _stream(stream)))
+    return [int(x) for x in ks]
 
 
 def kernel_launches():

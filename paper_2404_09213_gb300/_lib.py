@@ -28,7 +28,7 @@ class QsimPlanOpts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("dtype", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("contiguous_bits", ctypes.c_int32), ("checkpoint_passes", ctypes.c_int32),
                 ("sample_block", ctypes.c_int32), ("bwd_reg_bits", ctypes.c_int32),
-                ("fwd_reg_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("fwd_reg_bits", ctypes.c_int32), ("weight_remap", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64)]
 
 
@@ -76,7 +76,14 @@ SIGNATURES = {
                                              ctypes.c_void_p, ctypes.c_void_p]),
     "qsim_multi_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.POINTER(QsimGate)), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
-                                       ctypes.POINTER(ctypes.c_void_p)]),
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_void_p)]),
+    "qsim_autotune": (ctypes.c_int, [ctypes.POINTER(QsimGate), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
+                                     ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
+    "qsim_multi_autotune": (ctypes.c_int, [ctypes.POINTER(ctypes.POINTER(QsimGate)), ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.c_void_p]),
     "qsim_multi_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int64)] * 4),
     "qsim_multi_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),

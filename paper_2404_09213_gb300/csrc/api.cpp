@@ -386,9 +386,9 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   }
   p->opts = o;
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
-      o.sample_block < 0 || o.reserved != 0) {
+      o.sample_block < 0 || (o.weight_remap != 0 && o.weight_remap != 1)) {
     delete p;
-    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, reserved == 0");
+    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0 or 1");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
@@ -503,6 +503,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   ca.n_inputs = s.n_inputs;
   ca.B = batch;
   ca.P = p->P();
+  ca.weight_remap = p->opts.weight_remap;
   ca.coef = p->coef;
   ca.form = p->form;
   ca.cfp_f = p->cfp_f;
@@ -625,6 +626,9 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
   ga.i_occ = p->d_i_occ;
   ga.dparams = d_dparams;
   ga.dinputs = d_dinputs;
+  ga.params = p->params;
+  ga.weight_remap = p->opts.weight_remap;
+  ga.dtype = s.dtype;
   e = launch_grad_reduce(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction");
   if (p->calls_left(1)) p->n_bwd_calls++;

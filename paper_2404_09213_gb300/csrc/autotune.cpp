@@ -1,0 +1,156 @@
+// Tile-size autotuner: times the fused path of a circuit for each candidate k on scratch buffers and
+// keeps the fastest. Built on the public entry points only (qsim_plan / qsim_forward / qsim_backward).
+//
+// Candidates are the largest tiles that still fit the register/shared-memory budget of one CTA
+// (max_k - 2 .. max_k). A larger k means fewer passes (fewer HBM round trips); a smaller one means
+// smaller CTAs with cheaper barriers and more of them resident per SM. Which wins depends on the
+// circuit and the batch, so it is measured. Circuits with n <= max_k run in one pass at k = n.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+#include "jit.hpp"
+
+namespace qsim {
+void set_last_error(const std::string& s);
+}
+
+namespace {
+
+struct Scratch {
+  std::vector<void*> bufs;
+  ~Scratch() {
+    for (void* p : bufs) cudaFree(p);
+  }
+  void* get(size_t bytes, cudaStream_t st, cudaError_t& e) {
+    if (e != cudaSuccess || bytes == 0) return nullptr;
+    void* p = nullptr;
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return nullptr;
+    bufs.push_back(p);
+    e = cudaMemsetAsync(p, 0, bytes, st);
+    return p;
+  }
+};
+
+int fail(int code, const std::string& m) {
+  qsim::set_last_error(m);
+  return code;
+}
+
+// Mean milliseconds of one forward (+ backward) call of the circuit planned with `o`; < 0 on error.
+int time_candidate(const qsim_gate* g, int32_t ng, int32_t n, int32_t batch, int32_t with_bwd, int32_t reps,
+                   const qsim_plan_opts& o, cudaStream_t st, float& ms) {
+  qsim_plan_t p = nullptr;
+  int rc = qsim_plan(g, ng, n, &o, &p);
+  if (rc) return rc;
+  qsim_plan_info inf;
+  qsim_plan_info_get(p, &inf);
+  const size_t sc = o.dtype == QSIM_C128 ? 8 : 4;
+  Scratch s;
+  cudaError_t e = cudaSuccess;
+  void* params = s.get(std::max<size_t>(1, (size_t)inf.n_params) * sc, st, e);
+  void* inputs = s.get(std::max<size_t>(1, (size_t)batch * inf.n_inputs) * sc, st, e);
+  void* states = s.get((size_t)batch * (2 * sc) << n, st, e);
+  double* z = static_cast<double*>(s.get((size_t)batch * n * 8, st, e));
+  double* gout = static_cast<double*>(s.get((size_t)batch * n * 8, st, e));
+  double* dp = static_cast<double*>(s.get(std::max<size_t>(1, (size_t)inf.n_params) * 8, st, e));
+  double* di = static_cast<double*>(s.get(std::max<size_t>(1, (size_t)batch * inf.n_inputs) * 8, st, e));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    qsim_plan_destroy(p);
+    return fail(QSIM_ERR_OOM, std::string("autotune scratch: ") + cudaGetErrorString(e));
+  }
+  auto step = [&]() {
+    int r = qsim_forward(p, params, inf.n_inputs ? inputs : nullptr, batch, nullptr, states, z, st);
+    if (!r && with_bwd) r = qsim_backward(p, gout, dp, inf.n_inputs ? di : nullptr, st);
+    return r;
+  };
+  rc = step();   // untimed: compiles the pass kernels and sizes the workspace
+  if (!rc) {
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < reps && !rc; i++) rc = step();
+    cudaEventRecord(e1, st);
+    e = cudaEventSynchronize(e1);
+    if (!rc && e != cudaSuccess) rc = fail(QSIM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+    if (!rc) rc = qsim_sync_status(p);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms = t / (float)reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  qsim_plan_destroy(p);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, int32_t batch, int32_t with_backward,
+                  int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream) {
+  if (!opts || batch < 1 || reps < 1) return fail(QSIM_ERR_ARG, "autotune: opts must be set, batch >= 1, reps >= 1");
+  if (opts->mode != QSIM_FUSED) return fail(QSIM_ERR_ARG, "autotune: fused mode only");
+  if (opts->dtype != QSIM_C64 && opts->dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "autotune: bad dtype");
+  const int kmax = qsim::max_k_for(opts->dtype);
+  if (h_ms)
+    for (int i = 0; i < 3; i++) h_ms[i] = -1.f;
+  if (n_qubits <= kmax) {   // one pass holds the whole state
+    opts->k = n_qubits;
+    return QSIM_OK;
+  }
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int best = -1;
+  float best_ms = 0.f;
+  for (int i = 0; i < 3; i++) {
+    qsim_plan_opts o = *opts;
+    o.k = kmax - 2 + i;
+    float ms = 0.f;
+    const int rc = time_candidate(h_gates, n_gates, n_qubits, batch, with_backward, reps, o, st, ms);
+    if (rc) return rc;
+    if (h_ms) h_ms[i] = ms;
+    if (best < 0 || ms < best_ms) {
+      best = o.k;
+      best_ms = ms;
+    }
+  }
+  opts->k = best;
+  return QSIM_OK;
+}
+
+int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
+                        int32_t n_circuits, int32_t batch, int32_t with_backward, int32_t reps,
+                        const qsim_plan_opts* opts, int32_t* h_k, void* stream) {
+  if (!h_gate_lists || !h_n_gates || !h_n_qubits || !h_k || n_circuits < 1)
+    return fail(QSIM_ERR_ARG, "multi autotune: NULL argument or no circuits");
+  qsim_plan_opts base;
+  qsim_default_opts(&base);
+  if (opts) base = *opts;
+  // one representative (the first circuit) per qubit count
+  std::map<int, int> rep_of;
+  for (int c = 0; c < n_circuits; c++)
+    if (!rep_of.count(h_n_qubits[c])) rep_of[h_n_qubits[c]] = c;
+  std::map<int, int> k_of;
+  for (auto& kv : rep_of) {
+    qsim_plan_opts o = base;
+    const int c = kv.second;
+    const int rc = qsim_autotune(h_gate_lists[c], h_n_gates[c], h_n_qubits[c], batch, with_backward, reps, &o,
+                                 nullptr, stream);
+    if (rc) return rc;
+    k_of[kv.first] = o.k;
+  }
+  for (int c = 0; c < n_circuits; c++) h_k[c] = k_of[h_n_qubits[c]];
+  return QSIM_OK;
+}
+
+}  // extern "C"

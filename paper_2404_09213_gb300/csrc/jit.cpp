@@ -196,6 +196,18 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 }  // namespace
 
 // ------------------------------------------------------------------ generation
+// Backward gradient partials: one per thread and slot in shared memory, reduced once at the end of
+// the tile (no shuffles between ops), unless that area would exceed 32 KiB per CTA (deep passes,
+// or many small tile groups in one CTA of a multi-circuit queue kernel), where every op is reduced
+// over its warp right away. cta: threads of the queue kernel's CTA (0: one tile per CTA).
+static bool defer_gradients(const DevPass& d, int dtype, int cta) {
+  const size_t sc = dtype == QSIM_C128 ? 8 : 4;
+  const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
+  const size_t nthr = (size_t)1 << (d.k - d.R);
+  const size_t groups = cta > 0 ? std::max<size_t>(1, (size_t)cta / nthr) : 1;
+  return ng * nthr * sc * groups <= 32 * 1024;
+}
+
 static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0) {
   const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
   const int P = d.n_phases;
@@ -203,6 +215,8 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   o << "  static constexpr int CTA = " << (cta > 0 ? cta : NTHR) << ";\n";
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
+  const bool defer = bwd && defer_gradients(d, s.dtype, cta);
+  o << "  static constexpr bool DEFER = " << (defer ? "true" : "false") << ";\n";
   for (int i = 0; i <= P; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
   auto dep_of = [&](const DevPhase& ph, int i) {
     uint32_t e = 0;
@@ -365,7 +379,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       if (!bwd) {
         o << "      " << inst("re", "im") << "\n";
       } else {
-        if (op.rot)
+        if (op.rot && defer)
+          o << "      red[" << op.gslot * NTHR << " + tid] = " << g.str() << ";\n";
+        else if (op.rot)
           o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ", A, CTA>(g); if (lane == 0u) red[warp * "
             << (d.n_gslots > 0 ? d.n_gslots : 1) << " + " << op.gslot << "] = g; }\n";
         o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
@@ -427,14 +443,15 @@ int bwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 3 : 4; retu
 int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
 
 // Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
-size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd) {
+size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
   const size_t no = (size_t)d.n_ops + 1;   // op coefficients + the pass scale
   if (!bwd) return (tile + no * sc + no + 15) & ~(size_t)15;
-  const int nthr = 1 << (d.k - d.R);
-  const size_t nw = (nthr + 31) / 32, ng = d.n_gslots > 0 ? d.n_gslots : 1;
+  const size_t nthr = (size_t)1 << (d.k - d.R);
+  const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const size_t red = 2 * tile;
-  const size_t gq = (red + nw * ng * sc + 15) & ~(size_t)15;
+  const size_t parts = defer_gradients(d, dtype, cta) ? ng * nthr : (nthr + 31) / 32 * ng;
+  const size_t gq = (red + parts * sc + 15) & ~(size_t)15;
   const size_t cf = gq + (d.k + 2) * 8;
   const size_t fm = cf + no * sc;
   return (fm + no + 15) & ~(size_t)15;
@@ -619,7 +636,7 @@ static std::string multi_unit(const Schedule& s, const DevPass& d, bool bwd, int
       << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
   else
     u << "  constexpr int GB = qj::BwdGroupSmem<" << T << ", " << K << ", " << R << ", NTHR, S_" << name << "::NOPS, S_"
-      << name << "::NGS>::BYTES;\n"
+      << name << "::NGS, S_" << name << "::DEFER>::BYTES;\n"
       << "  qj::bwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
       << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
   u << "}\n";
@@ -700,7 +717,7 @@ int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int c
         jm.kind[c][2 * p + dir] = kind_id[dir][name];
         const int nthr = 1 << (d.k - d.R);
         const size_t groups = (size_t)cta / nthr;
-        max_smem[dir] = std::max(max_smem[dir], groups * jit_smem_bytes(d, s.dtype, dir == 1));
+        max_smem[dir] = std::max(max_smem[dir], groups * jit_smem_bytes(d, s.dtype, dir == 1, cta));
       }
     }
   }

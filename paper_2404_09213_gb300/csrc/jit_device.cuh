@@ -428,15 +428,16 @@ __device__ __forceinline__ void fwd_pass(const Args& a) {
 // ---------------------------------------------------------------- backward pass
 // Shared-memory bytes of one tile group (backward): psi, lambda, gradient warp partials, g per tile
 // bit, coefficients and forms.
-template <typename T, int K, int R, int NTHR, int NOPS, int NGS>
+template <typename T, int K, int R, int NTHR, int NOPS, int NGS, bool DEFER>
 struct BwdGroupSmem {
   typedef typename Acc<T>::t A;
   static constexpr int NW = (NTHR + 31) / 32;
   static constexpr int NG = NGS > 0 ? NGS : 1;
   static constexpr int NO = NOPS + 1;
   static constexpr int TILE = (2 * (int)sizeof(T)) << K;
+  // gradient partials: every thread's [NG][NTHR] (DEFER) or every warp's [NW][NG]
   static constexpr int RED = 2 * TILE;
-  static constexpr int GQ = (RED + NW * NG * (int)sizeof(A) + 15) & ~15;
+  static constexpr int GQ = (RED + (DEFER ? NG * NTHR : NW * NG) * (int)sizeof(A) + 15) & ~15;
   static constexpr int CF = GQ + (K + 2) * 8;
   static constexpr int FM = CF + NO * (int)sizeof(T);
   static constexpr int BYTES = (FM + NO + 15) & ~15;
@@ -476,8 +477,8 @@ __device__ __forceinline__ void stage_bwd(Ctx<T>& c) {
 template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
   typedef typename Acc<T>::t A;
-  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS> SM;
-  A* red = reinterpret_cast<A*>(smem + SM::RED);          // [NW][NG]
+  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS, Spec::DEFER> SM;
+  A* red = reinterpret_cast<A*>(smem + SM::RED);
   Ctx<T> c;
   c.a = &a;
   c.tile = smem;
@@ -490,12 +491,32 @@ __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u3
   tile_coords(a, tile, c.b, c.t, c.base);
   Spec::template bwd_phases<T>(c, red);
   __syncthreads();
-  constexpr int NW = SM::NW, NG = SM::NG;
-  for (int sl = tid; sl < Spec::NGS; sl += NTHR) {
-    double acc = 0.0;
+  // DEFER: every op stored one partial per thread; sum each gradient slot over the group's threads
+  // in a fixed order (a warp per slot: strided lane sums, then a butterfly). Otherwise every op was
+  // reduced over its warp already and the warp totals are added here.
+  if constexpr (!Spec::DEFER) {
+    constexpr int NW = SM::NW, NG = SM::NG;
+    for (int sl = tid; sl < Spec::NGS; sl += NTHR) {
+      double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < NW; w++) acc += (double)red[w * NG + sl];
-    if (valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = acc;
+      for (int w = 0; w < NW; w++) acc += (double)red[w * NG + sl];
+      if (valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = acc;
+    }
+  } else if constexpr (NTHR >= 32) {
+    const u32 lane = tid & 31u, w = tid >> 5;
+    for (int sl = (int)w; sl < Spec::NGS; sl += NTHR / 32) {
+      A v = 0;
+#pragma unroll
+      for (int j = 0; j < NTHR / 32; j++) v += red[sl * NTHR + (int)lane + 32 * j];
+      v = warp_sum<32, A, 32>(v);
+      if (lane == 0u && valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = (double)v;
+    }
+  } else {
+    for (int sl = (int)tid; sl < Spec::NGS; sl += NTHR) {
+      A v = 0;
+      for (int u = 0; u < NTHR; u++) v += red[sl * NTHR + u];
+      if (valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = (double)v;
+    }
   }
 }
 

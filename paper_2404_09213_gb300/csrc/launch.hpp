@@ -24,6 +24,7 @@ struct CoefArgs {
   const void* params;
   const void* inputs;
   int n_inputs, B, P;
+  int weight_remap;             // 1: trainable angles enter as pi * tanh(param)
   void* coef;                   // [G * B]
   uint8_t* form;                // [G * B]
   void* cfp_f;                  // packed forward op coefficients: pass p, sample b, op i at
@@ -62,6 +63,8 @@ struct GradReduceArgs {
   const int32_t* i_ptr; const int32_t* i_occ;     // CSR: input column -> occurrences
   double* dparams;              // may be null
   double* dinputs;              // may be null
+  const void* params;           // weight_remap: the raw params (float32 / float64 by dtype) for the chain rule
+  int weight_remap, dtype;
 };
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st);
 
@@ -96,6 +99,8 @@ struct GradMultiArgs {
   const int32_t* col_index;     // per global column: column within its circuit
   double* dparams;
   double* dinputs;
+  const void* params;           // weight_remap: the raw concatenated params for the chain rule
+  int weight_remap, dtype;
 };
 cudaError_t launch_grad_reduce_multi(const GradMultiArgs& a, cudaStream_t st);
 

@@ -72,6 +72,7 @@ struct qsim_multi_s {
   std::vector<Schedule> sch;
   qsim_plan_opts opts{};
   int C = 0, el = 8, sc = 4, dtype = QSIM_C64;
+  const void* params = nullptr;   // of the last forward (weight remapping needs them in the backward)
   // global numbering
   std::vector<int64_t> goff, poff, param_off, col_off, amp_off, zq_off;
   int64_t G_tot = 0, P_tot = 0, n_params = 0, n_cols = 0;
@@ -113,6 +114,7 @@ struct qsim_multi_s {
   cudaStream_t last = nullptr;
   // CUDA graphs of the two launch sequences (keyed by the pointers they were captured with)
   cudaGraphExec_t gx_f = nullptr, gx_b = nullptr;
+  long long graph_kernels_f = 0, graph_kernels_b = 0;   // kernel nodes of each captured graph
   std::vector<const void*> key_f, key_b;
   std::vector<JitArgs> host_args_f, host_args_b;   // last uploaded argument blocks
   cudaStream_t cap = nullptr;   // plan-owned stream the graphs are captured on (the caller's may be the legacy stream)
@@ -373,7 +375,7 @@ struct qsim_multi_s {
 extern "C" {
 
 int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const int32_t* n_qubits, int32_t n_circ,
-                    const qsim_plan_opts* opts, qsim_multi_t* out) {
+                    const qsim_plan_opts* opts, const int32_t* h_k, qsim_multi_t* out) {
   qsim::set_last_error("");
   if (!out) return mfail(QSIM_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -383,8 +385,9 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
   if (opts) o = *opts;
   if (o.mode != QSIM_FUSED) return mfail(QSIM_ERR_ARG, "multi-circuit plans use the fused mode");
   if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return mfail(QSIM_ERR_ARG, "bad dtype");
-  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR || o.reserved != 0)
-    return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5] and reserved == 0");
+  if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
+      (o.weight_remap != 0 && o.weight_remap != 1))
+    return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5] and weight_remap 0 or 1");
   if (o.k == 0 || o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   auto* m = new qsim_multi_s();
   m->opts = o;
@@ -411,7 +414,15 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
     if (!rc) {
       const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
       const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
-      rc = build_schedule(gv, n_qubits[c], o, Rf, Rb, s, err);
+      qsim_plan_opts oc = o;
+      if (h_k) {
+        if (h_k[c] < 1 || h_k[c] > max_k_for(o.dtype)) {
+          delete m;
+          return mfail(QSIM_ERR_ARG, "circuit " + std::to_string(c) + ": per-circuit k outside [1, max k]");
+        }
+        oc.k = h_k[c];
+      }
+      rc = build_schedule(gv, n_qubits[c], oc, Rf, Rb, s, err);
     }
     if (rc) {
       delete m;
@@ -467,6 +478,7 @@ static cudaError_t multi_enqueue_fwd(qsim_multi_t m, const void* d_params, const
   ca.n_inputs = 0;
   ca.B = m->B;
   ca.P = (int)m->P_tot;
+  ca.weight_remap = m->opts.weight_remap;
   ca.coef = m->coef;
   ca.form = m->form;
   ca.cfp_f = m->cfp_f;
@@ -536,9 +548,12 @@ int qsim_multi_forward(qsim_multi_t m, const void* d_params, const void* d_input
       e = m->capture_stream();
       if (e == cudaSuccess) e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
+        const long long c0 = g_kernel_launches.load();
         cudaError_t e2 = multi_enqueue_fwd(m, d_params, d_inputs, d_states, d_z, m->cap);
         e = cudaStreamEndCapture(m->cap, &g);
         if (e == cudaSuccess) e = e2;
+        m->graph_kernels_f = g_kernel_launches.load() - c0;   // captured, not run: counted per replay
+        g_kernel_launches -= m->graph_kernels_f;
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gx_f, g, 0);
       if (g) cudaGraphDestroy(g);
@@ -546,11 +561,13 @@ int qsim_multi_forward(qsim_multi_t m, const void* d_params, const void* d_input
       m->key_f = key;
     }
     e = cudaGraphLaunch(m->gx_f, st);
+    if (e == cudaSuccess) g_kernel_launches += m->graph_kernels_f;
   } else {
     e = multi_enqueue_fwd(m, d_params, d_inputs, d_states, d_z, st);
   }
   if (e != cudaSuccess) return mcuda(e, "multi-circuit forward");
   m->states = d_states;
+  m->params = d_params;
   m->has_fwd = true;
   return QSIM_OK;
 }
@@ -586,6 +603,9 @@ static cudaError_t multi_enqueue_bwd(qsim_multi_t m, double* d_dparams, double* 
   ga.col_index = m->d_col_index;
   ga.dparams = d_dparams;
   ga.dinputs = d_dinputs;
+  ga.params = m->params;
+  ga.weight_remap = m->opts.weight_remap;
+  ga.dtype = m->dtype;
   return launch_grad_reduce_multi(ga, st);
 }
 
@@ -620,9 +640,12 @@ int qsim_multi_backward(qsim_multi_t m, const double* d_grad_out, double* d_dpar
       e = m->capture_stream();
       if (e == cudaSuccess) e = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
+        const long long c0 = g_kernel_launches.load();
         cudaError_t e2 = multi_enqueue_bwd(m, d_dparams, d_dinputs, m->cap);
         e = cudaStreamEndCapture(m->cap, &g);
         if (e == cudaSuccess) e = e2;
+        m->graph_kernels_b = g_kernel_launches.load() - c0;   // captured, not run: counted per replay
+        g_kernel_launches -= m->graph_kernels_b;
       }
       if (e == cudaSuccess) e = cudaGraphInstantiate(&m->gx_b, g, 0);
       if (g) cudaGraphDestroy(g);
@@ -630,6 +653,7 @@ int qsim_multi_backward(qsim_multi_t m, const double* d_grad_out, double* d_dpar
       m->key_b = key;
     }
     e = cudaGraphLaunch(m->gx_b, st);
+    if (e == cudaSuccess) g_kernel_launches += m->graph_kernels_b;
   } else {
     e = multi_enqueue_bwd(m, d_dparams, d_dinputs, st);
   }

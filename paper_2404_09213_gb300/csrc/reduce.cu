@@ -14,6 +14,21 @@ std::atomic<long long> g_kernel_launches{0};
 // with fixed partial matrices and two angle-dependent scalars. Here the scalars are formed once per
 // forward for every (gate, sample) and stored as one coefficient per rotation (tan or cot of theta/2,
 // whichever is at most 1 in magnitude) plus the factored-out cos / sin, accumulated per pass.
+constexpr double kPi = 3.14159265358979323846;
+
+// Angle of a trainable parameter: as given, or remapped into (-pi, pi) by pi * tanh (quantum weight
+// remapping, Sec. "Additional Optimizations"); d(angle)/d(param) is remap_slope.
+template <typename T>
+__device__ __forceinline__ double weight(T p, int remap) {
+  return remap ? kPi * tanh((double)p) : (double)p;
+}
+__device__ __forceinline__ double remap_slope(const void* params, int64_t i, int dtype) {
+  const double p = dtype == QSIM_C128 ? reinterpret_cast<const double*>(params)[i]
+                                      : (double)reinterpret_cast<const float*>(params)[i];
+  const double t = tanh(p);
+  return kPi * (1.0 - t * t);
+}
+
 template <typename T>
 __global__ void coef_kernel(CoefArgs a) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,7 +55,8 @@ __global__ void coef_kernel(CoefArgs a) {
     uint8_t f = 0;
     if (ty <= QSIM_RZ) {
       const int pr = a.gate_param[g];
-      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
+      const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
+                                : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
       double s, c;
       sincos(0.5 * th, &s, &c);
       const int64_t gi = (int64_t)g * a.B + b;
@@ -77,7 +93,8 @@ __global__ void coef_kernel(CoefArgs a) {
       fmpb[e] = a.form[gi];
       a.gm[gi] = bs * bs;
       const int pr = a.gate_param[g];
-      const double th = pr >= 0 ? (double)params[pr] : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
+      const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
+                                : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
       double s, c;
       sincos(0.5 * th, &s, &c);
       bs *= (a.form[gi] == 0) ? c : -s;
@@ -167,7 +184,7 @@ __global__ void grad_scatter_kernel(GradReduceArgs a) {
       const double* row = a.G + (int64_t)a.p_occ[o] * a.B;
       for (int b = 0; b < a.B; b++) acc += row[b];
     }
-    a.dparams[id] = acc;
+    a.dparams[id] = a.weight_remap ? acc * remap_slope(a.params, id, a.dtype) : acc;
   } else if (id < np + ni) {
     const int64_t r = id - np;
     const int b = (int)(r / a.n_inputs), c = (int)(r - (r / a.n_inputs) * a.n_inputs);
@@ -253,7 +270,7 @@ __global__ void grad_scatter_multi_kernel(GradMultiArgs a) {
       const double* row = a.G + (int64_t)a.p_occ[o] * a.B;
       for (int b = 0; b < a.B; b++) acc += row[b];
     }
-    a.dparams[id] = acc;
+    a.dparams[id] = a.weight_remap ? acc * remap_slope(a.params, id, a.dtype) : acc;
   } else if (id < np + ni) {
     const int64_t r = id - np;
     const int64_t gc = r / a.B;

@@ -364,3 +364,46 @@ def test_planted_mistakes_are_caught(monkeypatch, mistake):
         orig = g.expand_controlled
         monkeypatch.setattr(g, "expand_controlled", lambda c, t, U, W_: orig(t, c, U, W_))
     assert not _pins_pass(), f"planted mistake {mistake} was not caught by any pin"
+
+
+# ---------------------------------------------------------------- quantum weight remapping (Sec. III-C)
+def test_remap_range_and_fixed_points():
+    w = np.linspace(-6, 6, 41)
+    a = oracle.remap(w)
+    assert np.all(np.abs(a) < math.pi) and np.all(np.diff(a) > 0)       # into (-pi, pi), monotone
+    np.testing.assert_allclose(oracle.remap(-w), -a, atol=0)              # odd
+    np.testing.assert_allclose(oracle.remap(np.arctanh([0.5, -0.25])), [math.pi / 2, -math.pi / 4], atol=1e-15)
+
+
+@pytest.mark.parametrize("w", [-1.7, -0.4, 0.0, 0.3, 1.1, 2.6])
+def test_remap_single_rx_closed_form(w):
+    # RX(pi tanh w)|0>: <Z> = cos(pi tanh w), d<Z>/dw = -sin(pi tanh w) * pi (1 - tanh^2 w)
+    gates = [(W.RX, (0, -1), (-1, -1), 0)]
+    z = oracle.forward_z_remapped(gates, 1, [w], np.zeros((1, 0)))
+    np.testing.assert_allclose(z[0, 0], math.cos(math.pi * math.tanh(w)), atol=1e-14)
+    dp, _ = oracle.grad_remapped(gates, 1, [w], np.zeros((1, 0)), np.ones((1, 1)))
+    t = math.tanh(w)
+    np.testing.assert_allclose(dp[0], -math.sin(math.pi * t) * math.pi * (1 - t * t), atol=1e-13)
+
+
+def test_remap_chain_rule_equals_finite_difference_on_raw_weights():
+    wl = W.config(1, n=3, batch=2, layers=1)
+    w = wl.params - math.pi          # spread over both signs of tanh
+    dp, di = oracle.grad_remapped(wl.gates, wl.n, w, wl.inputs, wl.grad_out)
+    h = 1e-5
+    for p in range(len(w)):
+        wp = w.copy(); wp[p] += h
+        wm = w.copy(); wm[p] -= h
+        lp = oracle.loss(oracle.forward_z_remapped(wl.gates, wl.n, wp, wl.inputs), wl.grad_out)
+        lm = oracle.loss(oracle.forward_z_remapped(wl.gates, wl.n, wm, wl.inputs), wl.grad_out)
+        assert abs(dp[p] - (lp - lm) / (2 * h)) < 1e-8
+    # inputs are not remapped: their gradient is the plain one
+    _, di_plain = oracle.grad_param_shift(wl.gates, wl.n, oracle.remap(w), wl.inputs, wl.grad_out)
+    np.testing.assert_allclose(di, di_plain, atol=0)
+
+
+def test_planted_remap_slope_mistake_is_caught(monkeypatch):
+    from oracle import remapping as R
+    monkeypatch.setattr(R, "remap_slope", lambda w: np.pi * (1.0 - np.tanh(np.asarray(w, dtype=np.float64))))
+    with pytest.raises(AssertionError):
+        test_remap_single_rx_closed_form(1.1)
