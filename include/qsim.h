@@ -238,7 +238,8 @@ void qsim_multi_destroy(qsim_multi_t plan);
  * {max_k - 2, max_k - 1, max_k} (max_k = 12 complex64, 11 complex128), runs one untimed forward
  * (+ backward when with_backward != 0; this also compiles the kernels) and then `reps` timed calls
  * on zero-filled scratch buffers of `batch` samples that it allocates and frees itself (run time
- * does not depend on the values), and writes the fastest k to opts->k. n_qubits <= max_k: opts->k =
+ * does not depend on the values), and writes to opts->k the largest candidate whose time is within
+ * 2 % of the fastest. n_qubits <= max_k: opts->k =
  * n_qubits (one pass), nothing is run. h_ms: NULL or 3 floats, mean ms per call of each candidate
  * (-1 when not run). Synchronises `stream`. Errors: those of qsim_plan / qsim_forward /
  * qsim_backward, QSIM_ERR_OOM for scratch. In the paper the maximum group width is a fixed

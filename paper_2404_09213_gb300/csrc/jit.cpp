@@ -295,12 +295,16 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         o << "      if (a.lam_in == nullptr) {\n        double dt = c.gq[" << K << "];\n";
         for (int jb = 0; jb < Ph.n_tbits; jb++)
           o << "        dt += ((tid >> " << jb << ") & 1u) ? -c.gq[" << (int)Ph.tbit[jb] << "] : c.gq[" << (int)Ph.tbit[jb] << "];\n";
-        for (int r = 0; r < R; r++) o << "        const double g" << r << " = c.gq[" << (int)Ph.rbit[r] << "];\n";
-        for (int i = 0; i < N; i++) {
-          o << "        { const double dd = dt";
-          for (int r = 0; r < R; r++) o << (((i >> r) & 1) ? " - g" : " + g") << r;
-          o << "; lr[" << i << "] = (T)(dd * (double)pr[" << i << "]); lq[" << i << "] = (T)(dd * (double)pq[" << i << "]); }\n";
-        }
+        // d(i) = dt + sum_r (bit r of i ? -g_r : g_r): the all-plus value in double, then a butterfly in T
+        // (subtract 2 g_r for every set register bit), then lambda = d * psi in T
+        o << "        T dd[" << N << "];\n        dd[0] = (T)(dt";
+        for (int r = 0; r < R; r++) o << " + c.gq[" << (int)Ph.rbit[r] << "]";
+        o << ");\n";
+        for (int r = 0; r < R; r++)
+          o << "        { const T m = (T)(2.0 * c.gq[" << (int)Ph.rbit[r] << "]); for (int i = 0; i < " << (1 << r)
+            << "; i++) dd[i + " << (1 << r) << "] = dd[i] - m; }\n";
+        for (int i = 0; i < N; i++)
+          o << "        lr[" << i << "] = dd[" << i << "] * pr[" << i << "]; lq[" << i << "] = dd[" << i << "] * pq[" << i << "];\n";
         o << "      }\n";
       }
     } else {

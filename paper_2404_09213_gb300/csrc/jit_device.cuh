@@ -349,18 +349,31 @@ __device__ __forceinline__ void z_reduce_regs(void* smem, typename Acc<T>::t zt,
 #pragma unroll
   for (int r = 0; r < R; r++) red[tid * NZ + 1 + r] = zs[r];
   __syncthreads();
-  for (int j = tid; j <= K; j += NTHR) {
-    double acc = 0.0;
-    if (j == K) {
-      for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ];
-    } else if (Spec::zmap(j) >= 0) {
-      const int r = Spec::zmap(j);
-      for (int u = 0; u < NTHR; u++) acc += (double)red[u * NZ + 1 + r];
-    } else {
-      const int bit = -1 - Spec::zmap(j);
-      for (int u = 0; u < NTHR; u++) acc += ((u >> bit) & 1) ? -(double)red[u * NZ] : (double)red[u * NZ];
+  // row j of the tile's partials: K = total probability, register bit r = sum of zs[r], thread bit =
+  // zt with the sign of that bit of the thread. In the state's precision inside the tile (a warp per
+  // row: strided lane sums, then a butterfly); rows are FP64 from here on (z_final sums the tiles).
+  auto term = [&](int j, int u) -> A {
+    if (j == K) return red[u * NZ];
+    const int zm = Spec::zmap(j);
+    if (zm >= 0) return red[u * NZ + 1 + zm];
+    const A x = red[u * NZ];
+    return ((u >> (-1 - zm)) & 1) ? -x : x;
+  };
+  if constexpr (NTHR >= 32) {
+    const u32 lane = tid & 31u, w = tid >> 5;
+    for (int j = (int)w; j <= K; j += NTHR / 32) {
+      A v = 0;
+#pragma unroll
+      for (int i = 0; i < NTHR / 32; i++) v += term(j, (int)lane + 32 * i);
+      v = warp_sum<32, A, 32>(v);
+      if (lane == 0u && valid) zrow[j] = (double)v;
     }
-    if (valid) zrow[j] = acc;
+  } else {
+    for (int j = (int)tid; j <= K; j += NTHR) {
+      A v = 0;
+      for (int u = 0; u < NTHR; u++) v += term(j, u);
+      if (valid) zrow[j] = (double)v;
+    }
   }
 }
 

@@ -25,7 +25,9 @@ def test_autotune_times_three_candidates(q):
     k, ms = q.autotune(wl.gates, wl.n, 4, reps=1)
     assert k in (10, 11, 12)
     assert all(m > 0 for m in ms)
-    assert ms[k - 10] == min(ms)
+    # the largest k within 2 % of the fastest candidate
+    assert ms[k - 10] <= 1.02 * min(ms)
+    assert all(m > 1.02 * min(ms) for m in ms[k - 10 + 1:])
 
 
 def test_autotune_single_pass_when_the_state_fits(q):
