@@ -47,6 +47,9 @@ def parse():
                          "c4: 256 circuits (8..22 qubits) x 4 in one persistent launch, fwd+bwd; "
                          "c5: 30 qubits x 1, fwd + checkpointed bwd")
     ap.add_argument("--contiguous-bits", type=int, default=0)
+    ap.add_argument("--checkpoint-passes", type=int, default=1,
+                    help="store the state every this many forward passes (1: every pass, so backward passes "
+                         "read stored states instead of writing uncomputed ones; 0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default="")
@@ -164,23 +167,23 @@ def oracle_rate(wl, gate_budget_s=12.0, max_gates=None):
 
 
 # ------------------------------------------------------------------ our arm
-def algorithmic_bytes(plan_desc, B, n, direction):
-    """Bytes each fused pass must move (complex64): forward 16 B/amp (8 B for the |0> start), backward
-    32 B/amp (24 for the first pass, which forms lambda, 16 for the last, which stores nothing)."""
+def algorithmic_bytes(plan_desc, B, n, direction, checkpoint_passes=0):
+    """Bytes each fused pass must move (complex64, 8 B per amplitude and state read or written).
+
+    Forward: read + write (the first pass starts from |0> and only writes). Backward pass q: reads psi
+    and lambda (the last pass, which runs first, forms lambda from psi), writes lambda (not pass 0) and
+    psi unless q == 0 or the pass before it restarts from a stored checkpoint (q a multiple of the
+    checkpoint spacing)."""
     P = len(plan_desc["passes"])
     amps = B * (1 << n)
     if direction == "fwd":
         return [amps * (8 if q == 0 else 16) for q in range(P)]
+    m = checkpoint_passes
     out = []
     for q in range(P):
-        if P == 1:
-            out.append(amps * 8)
-        elif q == P - 1:
-            out.append(amps * 24)
-        elif q == 0:
-            out.append(amps * 16)
-        else:
-            out.append(amps * 32)
+        rd = 8 + (8 if q < P - 1 else 0)
+        wr = (8 if q > 0 else 0) + (8 if q > 0 and not (m > 0 and q % m == 0) else 0)
+        out.append(amps * (rd + wr))
     return out
 
 
@@ -223,9 +226,12 @@ def run_ours(args, world, rank, local):
     wl = W.config(3, batch=args.batch)
     k, autotune = args.k, None
     if args.mode == "fused" and k == 0:   # tile size from the library's autotuner (untimed setup)
-        k, ms = q.autotune(wl.gates, wl.n, wl.batch, reps=2, contiguous_bits=args.contiguous_bits)
+        k, ms = q.autotune(wl.gates, wl.n, wl.batch, reps=2, contiguous_bits=args.contiguous_bits,
+                           checkpoint_passes=args.checkpoint_passes)
         autotune = {"k_candidates": [10, 11, 12], "ms_per_fwd_bwd": ms, "chosen_k": k}
-    plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits)
+    ckpt = args.checkpoint_passes if args.mode == "fused" else 0
+    plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits,
+                  checkpoint_passes=ckpt)
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
     x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
@@ -269,7 +275,7 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel (fused backward pass kernel in fused mode)
     peak, peak_kind = load_peaks()
     fb = algorithmic_bytes(desc, B, wl.n, "fwd")
-    bb = algorithmic_bytes(desc, B, wl.n, "bwd")
+    bb = algorithmic_bytes(desc, B, wl.n, "bwd", ckpt)
     kern = "bwd_pass_kernel" if args.mode == "fused" else "pg_bwd_kernel"
     if fwd_ms.sum() > bwd_ms.sum():
         kern = "fwd_pass_kernel" if args.mode == "fused" else "pg_gate_kernel"
@@ -326,6 +332,8 @@ def run_ours(args, world, rank, local):
            "data": "synthetic (seeded splitmix64 angles and loss weights)",
            "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": B, "gates": len(wl.gates),
                       "params": wl.n_params, "mode": args.mode, "k": desc["k"], "autotune": autotune,
+                      "checkpoint_passes": ckpt, "checkpoints": plan.info()["n_checkpoints"],
+                      "workspace_bytes": plan.info()["workspace_bytes"],
                       "contiguous_bits": desc["c"],
                       "l2": "inputs larger than L2: 512 MiB state per step (L2 129 MB), no flush needed",
                       "parallelism": f"replicas x{world}"},
@@ -387,8 +395,8 @@ def run_other(args, world, rank, local):
             plan.backward(g, stream=stream)
         samples = B
         P = plan.info()["n_passes"]
-        amps = 1 << wl.n
-        tot = amps * (8 + 16 * (P - 1)) + amps * (24 + 16 + 32 * (P - 2))
+        desc = plan.describe()
+        tot = sum(algorithmic_bytes(desc, B, wl.n, "fwd")) + sum(algorithmic_bytes(desc, B, wl.n, "bwd", 8))
         name = "C5: 30 qubits, batch 1, c64, RX encoding + 8 x (RY,RZ + CNOT ring), fwd + checkpointed bwd"
         extra = {"passes": P, "checkpoint_passes": 8}
     else:

@@ -592,7 +592,8 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
         const bool seg_last = (q == p->seg_begin[seg + 1] - 1);
         const void* pin = seg_last ? ((seg == p->n_segments - 1) ? p->states : p->ckpt[seg]) : p->W;
         const void* lin = (q == P_ - 1) ? nullptr : p->Lam;
-        void* pout = q == 0 ? nullptr : p->W;
+        // the previous pass restarts from its checkpoint when this pass begins a segment: psi not stored
+        void* pout = (q == 0 || q == p->seg_begin[seg]) ? nullptr : p->W;
         void* lout = q == 0 ? nullptr : p->Lam;
         JitArgs ja = p->jit_args(q, true, sbk + (size_t)q * B * p->sc);
         ja.in = pin;

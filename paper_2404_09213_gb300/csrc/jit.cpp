@@ -410,15 +410,17 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         o << "        qj::z_reduce_regs<T, " << K << ", " << R << ", " << NTHR
           << ", S_SELF>(c.tile, zt, zs, a.zpart + (c.b * a.tps + c.t) * " << K + 1 << ", tid, c.valid);\n      }\n";
       } else {
+        // psi is not stored when the previous pass restarts from a checkpoint (a.out == nullptr)
         o << "      if (a.out != nullptr && c.valid) {\n"
-          << "        qj::scal<" << N << ">(pr, pq, sc); qj::scal<" << N << ">(lr, lq, sc);\n"
-          << "        T* po = reinterpret_cast<T*>(a.out);\n        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
-        for (int i = 0; i < N; i += 2) {
+          << "        qj::scal<" << N << ">(pr, pq, sc);\n        T* po = reinterpret_cast<T*>(a.out);\n";
+        for (int i = 0; i < N; i += 2)
           o << "        qj::stg_pair(po + 2 * " << goff("gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
             << "], pq[" << i + 1 << "]);\n";
+        o << "      }\n      if (a.lam_out != nullptr && c.valid) {\n"
+          << "        qj::scal<" << N << ">(lr, lq, sc);\n        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
+        for (int i = 0; i < N; i += 2)
           o << "        qj::stg_pair(lo + 2 * " << goff("gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
             << "], lq[" << i + 1 << "]);\n";
-        }
         o << "      }\n";
       }
     } else {
