@@ -84,6 +84,10 @@ typedef struct {
                                 that map; inputs are used as given. 0: angles as given */
   int32_t graph;             /* multi-circuit plans: capture each direction's launch sequence in a CUDA graph and
                                 replay it while the caller's buffers are unchanged (0 = plain launches) */
+  int32_t max_regs;          /* >0: registers per thread of the pass kernels capped so that at least
+                                65536 / (threads per tile * max_regs) CTAs fit on an SM (more resident warps,
+                                possibly a few spills); 0: the compiler's choice */
+  int32_t reserved;          /* must be 0 */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
 } qsim_plan_opts;
 

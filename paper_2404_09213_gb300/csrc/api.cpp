@@ -386,9 +386,11 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   }
   p->opts = o;
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
-      o.sample_block < 0 || (o.weight_remap != 0 && o.weight_remap != 1)) {
+      o.sample_block < 0 || (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs < 0 ||
+      (o.max_regs > 0 && o.max_regs < 32) || o.reserved != 0) {
     delete p;
-    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0 or 1");
+    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0 or 1, "
+                              "max_regs 0 or >= 32, reserved 0");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);

@@ -244,7 +244,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   auto goff = [&](const char* var, int i) {
     std::string e = var;
     for (int r = 1; r < R; r++)
-      if ((i >> r) & 1) e += std::string(" | ") + var + "u" + std::to_string(r);
+      if ((i >> r) & 1) e += std::string(" ^ gbu") + std::to_string(r);
     return "(" + e + ")";
   };
   if (!bwd) {
@@ -265,6 +265,29 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     const DevLayout& Li = s.layouts[d.lay0 + lin];
     const DevLayout& Lo = s.layouts[d.lay0 + lout];
     o << "    { // phase " << ph << (first ? " (loads from global)" : "") << (last ? " (stores to global)" : "") << "\n";
+    // CNOTs that open the phase (forward order) with the control on a thread bit and the target on a
+    // register bit >= 1 are conditional register swaps; they become an XOR of the thread's base
+    // address instead: at the load in the forward, at the store in the backward (applied last there).
+    std::vector<const DevOp*> fold;
+    for (int oi = Ph.op_begin; oi < Ph.op_end; oi++) {
+      const DevOp& op = s.ops[oi];
+      if (op.kind != K_CNOT_RT || op.a < 1) break;
+      fold.push_back(&op);
+    }
+    auto fold_smem = [&](const DevLayout& Lx) {
+      std::string t;
+      for (const DevOp* op : fold)
+        t += " ^ (((tb >> " + std::to_string(op->b) + ") & 1u) ? " +
+             std::to_string(lay_eval(Lx, K, dep_of(Ph, 1 << op->a))) + "u : 0u)";
+      return t;
+    };
+    auto fold_glob = [&](const char* base) {
+      std::string t = std::string("      qj::i64 ") + base + " = gb;\n";
+      for (const DevOp* op : fold)
+        t += std::string("      if ((tb >> ") + std::to_string(op->b) + ") & 1u) " + base + " ^= gbu" +
+             std::to_string(op->a) + ";\n";
+      return t;
+    };
     o << "      const qj::u32 tb = 0u";
     for (int jb = 0; jb < Ph.n_tbits; jb++) o << " | (((tid >> " << jb << ") & 1u) << " << (int)Ph.tbit[jb] << ")";
     o << ";\n      (void)tb;\n";
@@ -276,8 +299,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         for (int i = 0; i < N; i++) o << "        re[" << i << "] = T(0); im[" << i << "] = T(0);\n";
         o << "        if (tb == 0u && c.t == 0) re[0] = T(1);\n      } else {\n"
           << "        const T* in = reinterpret_cast<const T*>(a.in);\n";
+        o << fold_glob("gl");
         for (int i = 0; i < N; i += 2)
-          o << "        qj::ldg_pair(in + 2 * " << goff("gb", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
+          o << "        qj::ldg_pair(in + 2 * " << goff("gl", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
             << "], im[" << i + 1 << "]);\n";
         o << "      }\n";
         o << "      qj::stage_fwd<T, " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
@@ -308,7 +332,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         o << "      }\n";
       }
     } else {
-      o << "      const qj::u32 si = L" << lin << "(tb);\n";
+      o << "      const qj::u32 si = L" << lin << "(tb)" << (bwd ? std::string() : fold_smem(Li)) << ";\n";
       for (int i = 0; i < N; i += 2) {
         const uint32_t cc = lay_eval(Li, K, dep_of(Ph, i));
         if (!bwd) {
@@ -321,7 +345,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     }
     // ---- ops
     std::vector<int> order;
-    for (int oi = Ph.op_begin; oi < Ph.op_end; oi++) order.push_back(oi);
+    for (int oi = Ph.op_begin + (int)fold.size(); oi < Ph.op_end; oi++) order.push_back(oi);
     if (bwd) std::reverse(order.begin(), order.end());
     for (int oi : order) {
       const DevOp& op = s.ops[oi];
@@ -411,20 +435,22 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           << ", S_SELF>(c.tile, zt, zs, a.zpart + (c.b * a.tps + c.t) * " << K + 1 << ", tid, c.valid);\n      }\n";
       } else {
         // psi is not stored when the previous pass restarts from a checkpoint (a.out == nullptr)
+        o << fold_glob("gs");
         o << "      if (a.out != nullptr && c.valid) {\n"
           << "        qj::scal<" << N << ">(pr, pq, sc);\n        T* po = reinterpret_cast<T*>(a.out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(po + 2 * " << goff("gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
+          o << "        qj::stg_pair(po + 2 * " << goff("gs", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
             << "], pq[" << i + 1 << "]);\n";
         o << "      }\n      if (a.lam_out != nullptr && c.valid) {\n"
           << "        qj::scal<" << N << ">(lr, lq, sc);\n        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(lo + 2 * " << goff("gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
+          o << "        qj::stg_pair(lo + 2 * " << goff("gs", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
             << "], lq[" << i + 1 << "]);\n";
         o << "      }\n";
       }
     } else {
-      o << "      __syncthreads();\n      const qj::u32 so = L" << lout << "(tb);\n";
+      o << "      __syncthreads();\n      const qj::u32 so = L" << lout << "(tb)" << (bwd ? fold_smem(Lo) : std::string())
+        << ";\n";
       for (int i = 0; i < N; i += 2) {
         const uint32_t cc = lay_eval(Lo, K, dep_of(Ph, i));
         if (!bwd) {
@@ -475,14 +501,19 @@ static void jit_units(const Schedule& s, std::vector<std::string>& fnames, std::
       const bool bwd = dir == 1;
       const int K = d.k, R = d.R, NTHR = 1 << (K - R);
       std::string body = gen_spec_body(s, d, bwd);
-      std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" + body;
+      // register cap: at least this many CTAs per SM (65536 registers each)
+      const int minb = s.max_regs > 0 ? std::max(1, 65536 / (NTHR * s.max_regs)) : 0;
+      std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" +
+                        std::to_string(minb) + "|" + body;
       std::string name = std::string(bwd ? "qb_" : "qf_") + hex64(fnv1a(key));
       if (!units.count(name)) {
         std::ostringstream u;
         std::string b2 = body;
         for (size_t p; (p = b2.find("S_SELF")) != std::string::npos;) b2.replace(p, 6, "S_" + name);
         u << "struct S_" << name << " {\n" << b2 << "};\n";
-        u << "extern \"C\" __global__ void __launch_bounds__(" << NTHR << ") " << name
+        u << "extern \"C\" __global__ void __launch_bounds__(" << NTHR;
+        if (minb > 0) u << ", " << minb;
+        u << ") " << name
           << "(const qj::Args a) { qj::" << (bwd ? "bwd_pass" : "fwd_pass") << "<" << T << ", " << K << ", " << R
           << ", " << NTHR << ", S_" << name << ">(a); }\n";
         units[name] = u.str();
