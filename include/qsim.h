@@ -87,7 +87,11 @@ typedef struct {
   int32_t max_regs;          /* >0: registers per thread of the pass kernels capped so that at least
                                 65536 / (threads per tile * max_regs) CTAs fit on an SM (more resident warps,
                                 possibly a few spills); 0: the compiler's choice */
-  int32_t reserved;          /* must be 0 */
+  int32_t rotate_low_bits;   /* 1: index bits 1..contiguous_bits-1 are handed between passes to qubits needed
+                                next (a qubit remap folded into each pass's store; fewer passes when
+                                k >= 2 * contiguous_bits + 2, but each pass holds more gates and phases);
+                                0 (default): the contiguous_bits lowest bits hold the same qubits in every
+                                pass. Multi-circuit plans always keep them fixed */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
 } qsim_plan_opts;
 

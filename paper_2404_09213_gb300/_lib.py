@@ -29,7 +29,7 @@ class QsimPlanOpts(ctypes.Structure):
                 ("contiguous_bits", ctypes.c_int32), ("checkpoint_passes", ctypes.c_int32),
                 ("sample_block", ctypes.c_int32), ("bwd_reg_bits", ctypes.c_int32),
                 ("fwd_reg_bits", ctypes.c_int32), ("weight_remap", ctypes.c_int32),
-                ("graph", ctypes.c_int32), ("max_regs", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("graph", ctypes.c_int32), ("max_regs", ctypes.c_int32), ("rotate_low_bits", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_int64)]
 
 

@@ -58,7 +58,7 @@ struct qsim_plan_s {
   int32_t* d_occ_gate = nullptr;
   int64_t* d_occ_slot = nullptr;
   int32_t *d_p_ptr = nullptr, *d_p_occ = nullptr, *d_i_ptr = nullptr, *d_i_occ = nullptr;
-  uint8_t* d_Lnl_last = nullptr;
+  uint8_t* d_Qnl_last = nullptr;
   int n_occ = 0;
   // batch workspace
   int B_cap = -1;
@@ -160,7 +160,7 @@ struct qsim_plan_s {
     free_ws();
     destroy_events();
     void* ptrs[] = {d_gate_type, d_gate_param, d_exec_gates, d_exec_begin, d_exec_gates_b,
-                    d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Lnl_last};
+                    d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Qnl_last};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     jit_free(jit);
@@ -207,9 +207,9 @@ struct qsim_plan_s {
     }
     std::vector<uint8_t> lnl;
     if (s.mode == QSIM_FUSED && !s.passes.empty()) {
-      const DevPass& d = s.passes.back().dev;
-      for (int j = 0; j < d.k; j++) lnl.push_back(d.L[j]);
-      for (int j = 0; j < d.n_nonlocal; j++) lnl.push_back(d.nonlocal[j]);
+      const DevPass& d = s.passes.back().dev;   // logical qubits of its tile and tile-index bits
+      for (int j = 0; j < d.k; j++) lnl.push_back(d.Q[j]);
+      for (int j = 0; j < d.n_nonlocal; j++) lnl.push_back(d.QN[j]);
       lnl.push_back(0);
     }
 #define QSIM_UP(PTR, VEC) \
@@ -226,7 +226,7 @@ struct qsim_plan_s {
     QSIM_UP(d_p_occ, p_occ)
     QSIM_UP(d_i_ptr, i_ptr)
     QSIM_UP(d_i_occ, i_occ)
-    QSIM_UP(d_Lnl_last, lnl)
+    QSIM_UP(d_Qnl_last, lnl)
 #undef QSIM_UP
     if (e != cudaSuccess) return cuda_fail(e, "uploading the plan");
     if (s.mode == QSIM_FUSED) {
@@ -318,7 +318,7 @@ struct qsim_plan_s {
     a.cfp = static_cast<const char*>(bwd ? cfp_b : cfp_f) + e0 * sc;
     a.fmp = (bwd ? fmp_b : fmp_f) + e0;
     a.scale = scale;
-    set_bits(a, d);
+    set_bits(a, d, bwd);
     a.tps = d.tiles_per_sample;
     a.gpart_offset = d.gpart_offset;
     a.n_nonlocal = d.n_nonlocal;
@@ -387,14 +387,14 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   p->opts = o;
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
       o.sample_block < 0 || (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs < 0 ||
-      (o.max_regs > 0 && o.max_regs < 32) || o.reserved != 0) {
+      (o.max_regs > 0 && o.max_regs < 32) || (o.rotate_low_bits != 0 && o.rotate_low_bits != 1)) {
     delete p;
     return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0 or 1, "
-                              "max_regs 0 or >= 32, reserved 0");
+                              "max_regs 0 or >= 32, rotate_low_bits 0 or 1");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
-  rc = build_schedule(gv, n_qubits, o, Rf, Rb, p->s, err);
+  rc = build_schedule(gv, n_qubits, o, Rf, Rb, p->s, err, o.rotate_low_bits == 1);
   if (rc) {
     delete p;
     return fail(rc, err);
@@ -537,11 +537,17 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
     for (int b0 = 0; b0 < batch; b0 += G) {
       const int nb = std::min(G, batch - b0);
       for (int q = 0; q < P_; q++) {
+        // Passes update their segment's buffer in place (a pass reads and writes the same addresses of
+        // every tile: the layout changes between passes only permute qubits of its tile). The last
+        // pass also restores the canonical qubit order, which moves qubits outside its tile, so it
+        // writes out of place: the last segment runs in the workspace W and only its last pass writes
+        // the caller's buffer.
         const int seg = p->seg_of(q);
-        void* out = (seg == p->n_segments - 1) ? d_states : p->ckpt[seg];
+        void* sbuf = (seg == p->n_segments - 1) ? (P_ > 1 ? p->W : d_states) : p->ckpt[seg];
+        void* out = (q == P_ - 1) ? d_states : sbuf;
         const void* in;
         if (q == p->seg_begin[seg]) in = (seg == 0) ? d_init : p->ckpt[seg - 1];
-        else in = out;
+        else in = sbuf;
         JitArgs ja = p->jit_args(q, false, sf + (size_t)q * batch * p->sc);
         ja.in = in;
         ja.out = out;
@@ -554,7 +560,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
       }
     }
     const DevPass& last = s.passes.back().dev;
-    e = launch_z_final(p->zpart, last.k, p->d_Lnl_last, last.n_nonlocal, last.tiles_per_sample, s.n, batch, d_z, st);
+    e = launch_z_final(p->zpart, last.k, p->d_Qnl_last, last.n_nonlocal, last.tiles_per_sample, s.n, batch, d_z, st);
     if (e != cudaSuccess) return cuda_fail(e, "<Z> reduction");
   }
   p->has_fwd = true;

@@ -196,16 +196,20 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 }  // namespace
 
 // ------------------------------------------------------------------ generation
-// Backward gradient partials: one per thread and slot in shared memory, reduced once at the end of
-// the tile (no shuffles between ops), unless that area would exceed 32 KiB per CTA (deep passes,
-// or many small tile groups in one CTA of a multi-circuit queue kernel), where every op is reduced
-// over its warp right away. cta: threads of the queue kernel's CTA (0: one tile per CTA).
-static bool defer_gradients(const DevPass& d, int dtype, int cta) {
+// Backward gradient partials live in shared memory until the end of the tile: one per gradient slot
+// and group of 2^GS neighbouring threads, GS the smallest level (no shuffles at all for GS = 0) for
+// which they fit in 32 KiB per CTA; deep passes, or many small tile groups in one CTA of a
+// multi-circuit queue kernel, take GS up to a whole warp. cta: threads of the queue kernel's CTA
+// (0: one tile per CTA).
+static int grad_level(const DevPass& d, int dtype, int cta) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4;
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
-  const size_t nthr = (size_t)1 << (d.k - d.R);
-  const size_t groups = cta > 0 ? std::max<size_t>(1, (size_t)cta / nthr) : 1;
-  return ng * nthr * sc * groups <= 32 * 1024;
+  const int lt = d.k - d.R;                      // log2 threads per tile
+  const size_t groups = cta > 0 ? std::max<size_t>(1, (size_t)cta >> lt) : 1;
+  const int cap = std::min(lt, 5);
+  for (int gs = 0; gs < cap; gs++)
+    if (ng * ((size_t)1 << (lt - gs)) * sc * groups <= 32 * 1024) return gs;
+  return cap;
 }
 
 static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0) {
@@ -215,8 +219,8 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   o << "  static constexpr int CTA = " << (cta > 0 ? cta : NTHR) << ";\n";
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
-  const bool defer = bwd && defer_gradients(d, s.dtype, cta);
-  o << "  static constexpr bool DEFER = " << (defer ? "true" : "false") << ";\n";
+  const int gs = bwd ? grad_level(d, s.dtype, cta) : 0;
+  o << "  static constexpr int GS = " << gs << ";\n";
   for (int i = 0; i <= P; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
   auto dep_of = [&](const DevPhase& ph, int i) {
     uint32_t e = 0;
@@ -233,18 +237,24 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     o << "      default: return 0;\n    }\n  }\n";
   }
   // global offset of the thread's base element and of the register bits, for a phase
-  auto gaddr = [&](const DevPhase& ph, const char* var) {
+  // global offset of the thread's base element and of the register bits, for a phase, in the layout
+  // the pass reads (out = false: a.L, c.base) or writes (out = true: a.Lo, c.base_out)
+  auto gaddr = [&](const DevPhase& ph, const std::string& var, bool out) {
+    const char* Lv = out ? "a.Lo" : "a.L";
     std::ostringstream g;
-    g << "      qj::i64 " << var << " = c.base;\n";
+    g << "      qj::i64 " << var << " = " << (out ? "c.base_out" : "c.base") << ";\n";
     for (int jb = 0; jb < ph.n_tbits; jb++)
-      g << "      if ((tid >> " << jb << ") & 1u) " << var << " |= (qj::i64)1 << a.L[" << (int)ph.tbit[jb] << "];\n";
-    for (int r = 1; r < R; r++) g << "      const qj::i64 " << var << "u" << r << " = (qj::i64)1 << a.L[" << (int)ph.rbit[r] << "];\n";
+      g << "      if ((tid >> " << jb << ") & 1u) " << var << " |= (qj::i64)1 << " << Lv << "[" << (int)ph.tbit[jb] << "];\n";
+    for (int r = 1; r < R; r++)
+      g << "      const qj::i64 " << var << "u" << r << " = (qj::i64)1 << " << Lv << "[" << (int)ph.rbit[r] << "];\n";
     return g.str();
   };
-  auto goff = [&](const char* var, int i) {
-    std::string e = var;
+  // address of register pair i from a base and the offsets <offs>u<r> (XOR: a folded base may
+  // already carry a register bit)
+  auto goff = [&](const std::string& base, const std::string& offs, int i) {
+    std::string e = base;
     for (int r = 1; r < R; r++)
-      if ((i >> r) & 1) e += std::string(" ^ gbu") + std::to_string(r);
+      if ((i >> r) & 1) e += " ^ " + offs + "u" + std::to_string(r);
     return "(" + e + ")";
   };
   if (!bwd) {
@@ -281,17 +291,18 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
              std::to_string(lay_eval(Lx, K, dep_of(Ph, 1 << op->a))) + "u : 0u)";
       return t;
     };
-    auto fold_glob = [&](const char* base) {
-      std::string t = std::string("      qj::i64 ") + base + " = gb;\n";
+    auto fold_glob = [&](const std::string& base, const std::string& from) {
+      std::string t = "      qj::i64 " + base + " = " + from + ";\n";
       for (const DevOp* op : fold)
-        t += std::string("      if ((tb >> ") + std::to_string(op->b) + ") & 1u) " + base + " ^= gbu" +
+        t += "      if ((tb >> " + std::to_string(op->b) + ") & 1u) " + base + " ^= " + from + "u" +
              std::to_string(op->a) + ";\n";
       return t;
     };
     o << "      const qj::u32 tb = 0u";
     for (int jb = 0; jb < Ph.n_tbits; jb++) o << " | (((tid >> " << jb << ") & 1u) << " << (int)Ph.tbit[jb] << ")";
     o << ";\n      (void)tb;\n";
-    if (first || last) o << gaddr(Ph, "gb");
+    if (first) o << gaddr(Ph, "gb", false);
+    if (last) o << gaddr(Ph, "gs", true);
     // ---- load
     if (first) {
       if (!bwd) {
@@ -299,20 +310,20 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         for (int i = 0; i < N; i++) o << "        re[" << i << "] = T(0); im[" << i << "] = T(0);\n";
         o << "        if (tb == 0u && c.t == 0) re[0] = T(1);\n      } else {\n"
           << "        const T* in = reinterpret_cast<const T*>(a.in);\n";
-        o << fold_glob("gl");
+        o << fold_glob("gl", "gb");
         for (int i = 0; i < N; i += 2)
-          o << "        qj::ldg_pair(in + 2 * " << goff("gl", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
+          o << "        qj::ldg_pair(in + 2 * " << goff("gl", "gb", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
             << "], im[" << i + 1 << "]);\n";
         o << "      }\n";
         o << "      qj::stage_fwd<T, " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
       } else {
         o << "      {\n        const T* in = reinterpret_cast<const T*>(a.in);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::ldg_pair(in + 2 * " << goff("gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
+          o << "        qj::ldg_pair(in + 2 * " << goff("gb", "gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
             << "], pq[" << i + 1 << "]);\n";
         o << "      }\n      if (a.lam_in != nullptr) {\n        const T* li = reinterpret_cast<const T*>(a.lam_in);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::ldg_pair(li + 2 * " << goff("gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
+          o << "        qj::ldg_pair(li + 2 * " << goff("gb", "gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
             << "], lq[" << i + 1 << "]);\n";
         // lambda = d(e) psi, d(e) = gq[K] + sum_j (bit_j(e) ? -g_j : g_j)
         o << "      }\n      qj::stage_bwd<T, " << K << ", " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
@@ -407,11 +418,11 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       if (!bwd) {
         o << "      " << inst("re", "im") << "\n";
       } else {
-        if (op.rot && defer)
+        if (op.rot && gs == 0)
           o << "      red[" << op.gslot * NTHR << " + tid] = " << g.str() << ";\n";
         else if (op.rot)
-          o << "      { A g = " << g.str() << "; g = qj::warp_sum<" << NTHR << ", A, CTA>(g); if (lane == 0u) red[warp * "
-            << (d.n_gslots > 0 ? d.n_gslots : 1) << " + " << op.gslot << "] = g; }\n";
+          o << "      { A g = qj::part_sum<" << (1 << gs) << ", A, CTA>(" << g.str() << "); if ((tid & " << ((1 << gs) - 1)
+            << "u) == 0u) red[" << op.gslot * (NTHR >> gs) << " + (tid >> " << gs << ")] = g; }\n";
         o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
       }
     }
@@ -422,7 +433,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         o << "      qj::scal<" << N << ">(re, im, sc);\n"
           << "      if (c.valid) {\n        T* out = reinterpret_cast<T*>(a.out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(out + 2 * " << goff("gb", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
+          o << "        qj::stg_pair(out + 2 * " << goff("gs", "gs", i) << ", re[" << i << "], im[" << i << "], re[" << i + 1
             << "], im[" << i + 1 << "]);\n";
         o << "      }\n      if (a.zpart != nullptr) {\n        typedef typename qj::Acc<T>::t A;\n        A zt = 0, zs[" << R << "];\n";
         for (int r = 0; r < R; r++) o << "        zs[" << r << "] = 0;\n";
@@ -435,16 +446,16 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           << ", S_SELF>(c.tile, zt, zs, a.zpart + (c.b * a.tps + c.t) * " << K + 1 << ", tid, c.valid);\n      }\n";
       } else {
         // psi is not stored when the previous pass restarts from a checkpoint (a.out == nullptr)
-        o << fold_glob("gs");
+        o << fold_glob("gf", "gs");
         o << "      if (a.out != nullptr && c.valid) {\n"
           << "        qj::scal<" << N << ">(pr, pq, sc);\n        T* po = reinterpret_cast<T*>(a.out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(po + 2 * " << goff("gs", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
+          o << "        qj::stg_pair(po + 2 * " << goff("gf", "gs", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
             << "], pq[" << i + 1 << "]);\n";
         o << "      }\n      if (a.lam_out != nullptr && c.valid) {\n"
           << "        qj::scal<" << N << ">(lr, lq, sc);\n        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(lo + 2 * " << goff("gs", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
+          o << "        qj::stg_pair(lo + 2 * " << goff("gf", "gs", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
             << "], lq[" << i + 1 << "]);\n";
         o << "      }\n";
       }
@@ -482,7 +493,7 @@ size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta) {
   const size_t nthr = (size_t)1 << (d.k - d.R);
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const size_t red = 2 * tile;
-  const size_t parts = defer_gradients(d, dtype, cta) ? ng * nthr : (nthr + 31) / 32 * ng;
+  const size_t parts = ng * (nthr >> grad_level(d, dtype, cta));
   const size_t gq = (red + parts * sc + 15) & ~(size_t)15;
   const size_t cf = gq + (d.k + 2) * 8;
   const size_t fm = cf + no * sc;
@@ -673,7 +684,7 @@ static std::string multi_unit(const Schedule& s, const DevPass& d, bool bwd, int
       << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
   else
     u << "  constexpr int GB = qj::BwdGroupSmem<" << T << ", " << K << ", " << R << ", NTHR, S_" << name << "::NOPS, S_"
-      << name << "::NGS, S_" << name << "::DEFER>::BYTES;\n"
+      << name << "::NGS, S_" << name << "::GS>::BYTES;\n"
       << "  qj::bwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
       << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
   u << "}\n";
@@ -758,6 +769,16 @@ int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int c
       }
     }
   }
+  // one queue kernel links every distinct pass structure of its direction; keep that link to a size
+  // known to work (a few hundred functions of straight-line code make a very large program)
+  constexpr size_t kMaxKinds = 192;
+  for (int dir = 0; dir < 2; dir++)
+    if (kinds[dir].size() > kMaxKinds) {
+      err = "multi-circuit plan has " + std::to_string(kinds[dir].size()) +
+            " distinct pass structures in one direction (at most " + std::to_string(kMaxKinds) +
+            " per queue kernel): split the circuit list into several plans";
+      return QSIM_ERR_UNSUPPORTED;
+    }
   // compile every unit (relocatable) in parallel, cached
   std::vector<std::pair<std::string, std::string>> todo;   // name, source
   std::map<std::string, std::string> bins;

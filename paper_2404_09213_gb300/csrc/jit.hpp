@@ -28,13 +28,26 @@ struct JitArgs {
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch (tiles cover samples b0, b0+1, ...)
   uint8_t L[16];
   uint8_t nonlocal[40];
+  uint8_t Lo[16];
+  uint8_t nonlocal_o[40];
+  uint8_t Q[16];
+  uint8_t QN[40];
 };
-static_assert(sizeof(JitArgs) == 168, "JitArgs must match qj::Args");
+static_assert(sizeof(JitArgs) == 280, "JitArgs must match qj::Args");
 
-// Physical bit positions of a pass into its kernel arguments.
-inline void set_bits(JitArgs& a, const DevPass& d) {
-  for (int j = 0; j < d.k; j++) a.L[j] = d.L[j];
-  for (int j = 0; j < d.n_nonlocal; j++) a.nonlocal[j] = d.nonlocal[j];
+// Layouts of a pass into its kernel arguments. The forward reads the pass's input layout and writes
+// its output layout; the backward undoes the pass, so it reads the output layout and writes the input.
+inline void set_bits(JitArgs& a, const DevPass& d, bool bwd) {
+  for (int j = 0; j < d.k; j++) {
+    a.L[j] = bwd ? d.Lo[j] : d.L[j];
+    a.Lo[j] = bwd ? d.L[j] : d.Lo[j];
+    a.Q[j] = d.Q[j];
+  }
+  for (int j = 0; j < d.n_nonlocal; j++) {
+    a.nonlocal[j] = bwd ? d.nonlocal_o[j] : d.nonlocal[j];
+    a.nonlocal_o[j] = bwd ? d.nonlocal[j] : d.nonlocal_o[j];
+    a.QN[j] = d.QN[j];
+  }
 }
 
 struct JitKernel {

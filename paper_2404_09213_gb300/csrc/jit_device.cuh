@@ -31,8 +31,12 @@ struct Args {
   i64 tps;               // tiles per sample
   i64 gpart_offset;      // first gradient slot of this pass
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch
-  u8 L[16];              // physical bit of every tile bit
-  u8 nonlocal[40];       // physical bits outside the tile, ascending
+  u8 L[16];              // tile bit j: physical bit in the layout the pass reads
+  u8 nonlocal[40];       // tile-index bit i: physical bit in the layout the pass reads
+  u8 Lo[16];             // the same in the layout the pass writes (qubits remapped between passes)
+  u8 nonlocal_o[40];
+  u8 Q[16];              // logical qubit of tile bit j
+  u8 QN[40];             // logical qubit of tile-index bit i
 };
 
 __device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -274,6 +278,16 @@ __device__ __forceinline__ A warp_sum(A v) {
   return v;
 }
 
+// Sum over aligned groups of W neighbouring lanes (W a power of two <= 32); every lane gets its
+// group's sum. Lanes outside a CTA of fewer than 32 threads do not take part.
+template <int W, typename A, int CTA>
+__device__ __forceinline__ A part_sum(A v) {
+  constexpr unsigned mask = CTA >= 32 ? 0xffffffffu : ((1u << CTA) - 1u);
+#pragma unroll
+  for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off);
+  return v;
+}
+
 // ---------------------------------------------------------------- pair access in shared memory
 __device__ __forceinline__ void ldp(const void* tile, u32 w, float& r0, float& i0, float& r1, float& i1) {
   const float4 v = reinterpret_cast<const float4*>(tile)[w >> 1];
@@ -320,7 +334,8 @@ struct Ctx {
   T* cf;                 // op coefficients of this tile's sample, [NOPS] = pass scale (shared memory)
   u8* fm;                // op forms (shared memory)
   double* gq;            // backward, lambda init: g of every tile bit, [K] = fixed-bit part
-  i64 base;              // element offset of the tile (bits outside the tile) in the batched state
+  i64 base;              // element offset of the tile (bits outside the tile) in the batched state, read layout
+  i64 base_out;          // the same in the layout the pass writes
   i64 b, t;              // sample, tile within the sample
   u32 tid;
   bool valid;
@@ -377,12 +392,16 @@ __device__ __forceinline__ void z_reduce_regs(void* smem, typename Acc<T>::t zt,
   }
 }
 
-__device__ __forceinline__ void tile_coords(const Args& a, i64 tile, i64& b, i64& t, i64& base) {
+__device__ __forceinline__ void tile_coords(const Args& a, i64 tile, i64& b, i64& t, i64& base, i64& base_out) {
   b = tile / a.tps + a.b0;
   t = tile - (b - a.b0) * a.tps;
   base = b << a.n;
+  base_out = base;
   for (int j = 0; j < a.n_nonlocal; j++)
-    if ((t >> j) & 1) base += (i64)1 << a.nonlocal[j];
+    if ((t >> j) & 1) {
+      base += (i64)1 << a.nonlocal[j];
+      base_out += (i64)1 << a.nonlocal_o[j];
+    }
 }
 
 // ---------------------------------------------------------------- forward pass
@@ -411,7 +430,7 @@ __device__ __forceinline__ void fwd_tile(const Args& a, i64 tile, bool valid, u3
   c.gq = nullptr;
   c.tid = tid;
   c.valid = valid;
-  tile_coords(a, tile, c.b, c.t, c.base);
+  tile_coords(a, tile, c.b, c.t, c.base, c.base_out);
   Spec::template fwd_phases<T>(c);   // the first phase issues its loads, then calls stage_fwd and syncs
 }
 
@@ -441,16 +460,16 @@ __device__ __forceinline__ void fwd_pass(const Args& a) {
 // ---------------------------------------------------------------- backward pass
 // Shared-memory bytes of one tile group (backward): psi, lambda, gradient warp partials, g per tile
 // bit, coefficients and forms.
-template <typename T, int K, int R, int NTHR, int NOPS, int NGS, bool DEFER>
+template <typename T, int K, int R, int NTHR, int NOPS, int NGS, int GS>
 struct BwdGroupSmem {
   typedef typename Acc<T>::t A;
   static constexpr int NW = (NTHR + 31) / 32;
   static constexpr int NG = NGS > 0 ? NGS : 1;
   static constexpr int NO = NOPS + 1;
   static constexpr int TILE = (2 * (int)sizeof(T)) << K;
-  // gradient partials: every thread's [NG][NTHR] (DEFER) or every warp's [NW][NG]
+  // gradient partials [NG][NTHR >> GS]: one per slot and group of 2^GS neighbouring threads
   static constexpr int RED = 2 * TILE;
-  static constexpr int GQ = (RED + (DEFER ? NG * NTHR : NW * NG) * (int)sizeof(A) + 15) & ~15;
+  static constexpr int GQ = (RED + NG * (NTHR >> GS) * (int)sizeof(A) + 15) & ~15;
   static constexpr int CF = GQ + (K + 2) * 8;
   static constexpr int FM = CF + NO * (int)sizeof(T);
   static constexpr int BYTES = (FM + NO + 15) & ~15;
@@ -474,11 +493,11 @@ __device__ __forceinline__ void stage_bwd(Ctx<T>& c) {
     double* gq = c.gq;
     for (int j = c.tid; j <= K; j += NTHR) {
       if (j < K) {
-        gq[j] = a.grad_out[c.b * a.n + (a.n - 1 - a.L[j])];
+        gq[j] = a.grad_out[c.b * a.n + a.Q[j]];
       } else {
         double dc = 0.0;
         for (int q = 0; q < a.n_nonlocal; q++) {
-          const double g = a.grad_out[c.b * a.n + (a.n - 1 - a.nonlocal[q])];
+          const double g = a.grad_out[c.b * a.n + a.QN[q]];
           dc += ((c.t >> q) & 1) ? -g : g;
         }
         gq[K] = dc;
@@ -490,7 +509,7 @@ __device__ __forceinline__ void stage_bwd(Ctx<T>& c) {
 template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
   typedef typename Acc<T>::t A;
-  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS, Spec::DEFER> SM;
+  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS, Spec::GS> SM;
   A* red = reinterpret_cast<A*>(smem + SM::RED);
   Ctx<T> c;
   c.a = &a;
@@ -501,33 +520,26 @@ __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u3
   c.gq = reinterpret_cast<double*>(smem + SM::GQ);        // [K + 1]
   c.tid = tid;
   c.valid = valid;
-  tile_coords(a, tile, c.b, c.t, c.base);
+  tile_coords(a, tile, c.b, c.t, c.base, c.base_out);
   Spec::template bwd_phases<T>(c, red);
   __syncthreads();
-  // DEFER: every op stored one partial per thread; sum each gradient slot over the group's threads
-  // in a fixed order (a warp per slot: strided lane sums, then a butterfly). Otherwise every op was
-  // reduced over its warp already and the warp totals are added here.
-  if constexpr (!Spec::DEFER) {
-    constexpr int NW = SM::NW, NG = SM::NG;
-    for (int sl = tid; sl < Spec::NGS; sl += NTHR) {
-      double acc = 0.0;
-#pragma unroll
-      for (int w = 0; w < NW; w++) acc += (double)red[w * NG + sl];
-      if (valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = acc;
-    }
-  } else if constexpr (NTHR >= 32) {
+  // Every op stored one partial per group of 2^GS neighbouring threads (summed by shuffles first);
+  // sum each gradient slot over the NP = NTHR >> GS partials in a fixed order: a warp per slot
+  // (strided lane sums, then a butterfly) when there are at least 32, else a thread per slot.
+  constexpr int NP = NTHR >> Spec::GS;
+  if constexpr (NP >= 32) {
     const u32 lane = tid & 31u, w = tid >> 5;
     for (int sl = (int)w; sl < Spec::NGS; sl += NTHR / 32) {
       A v = 0;
 #pragma unroll
-      for (int j = 0; j < NTHR / 32; j++) v += red[sl * NTHR + (int)lane + 32 * j];
+      for (int j = 0; j < NP / 32; j++) v += red[sl * NP + (int)lane + 32 * j];
       v = warp_sum<32, A, 32>(v);
       if (lane == 0u && valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = (double)v;
     }
   } else {
     for (int sl = (int)tid; sl < Spec::NGS; sl += NTHR) {
       A v = 0;
-      for (int u = 0; u < NTHR; u++) v += red[sl * NTHR + u];
+      for (int u = 0; u < NP; u++) v += red[sl * NP + u];
       if (valid) a.gpart[((a.gpart_offset + sl) * a.B + c.b) * a.tps + c.t] = (double)v;
     }
   }

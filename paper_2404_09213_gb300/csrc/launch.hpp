@@ -45,7 +45,8 @@ struct CoefArgs {
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st);
 
 // ---- <Z> final reduction from per-tile partials: z[b][q]
-cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_L_and_nonlocal, int n_nonlocal,
+// d_Q_and_nonlocal: logical qubit of every tile bit, then of every tile-index bit, of the last pass
+cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Q_and_nonlocal, int n_nonlocal,
                            int64_t tiles_per_sample, int n, int B, double* z, cudaStream_t st);
 
 // ---- gradient reductions

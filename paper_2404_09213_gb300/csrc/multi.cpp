@@ -190,8 +190,8 @@ struct qsim_multi_s {
         exbb.push_back((int32_t)exb.size());
         for (int i = 0; i < pp.devb.n_ops; i++) exb.push_back((int32_t)(goff[c] + s.ops[pp.devb.op0 + i].gate));
         off_bits.push_back((int64_t)bits.size());
-        for (int j = 0; j < pp.dev.k; j++) bits.push_back(pp.dev.L[j]);
-        for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.nonlocal[j]);
+        for (int j = 0; j < pp.dev.k; j++) bits.push_back(pp.dev.Q[j]);   // logical qubits (<Z> reduction)
+        for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.QN[j]);
         bits.push_back(0);
       }
       for (size_t j = 0; j < s.grad_gate.size(); j++) {
@@ -345,7 +345,7 @@ struct qsim_multi_s {
     a.cfp = static_cast<const char*>(bwd ? cfp_b : cfp_f) + e0 * sc;
     a.fmp = (bwd ? fmp_b : fmp_f) + e0;
     a.scale = reinterpret_cast<const char*>(bwd ? scale_b : scale_f) + (size_t)gp * B * sc;
-    set_bits(a, d);
+    set_bits(a, d, bwd);
     a.tps = d.tiles_per_sample;
     a.gpart_offset = d.gpart_offset;
     a.n_nonlocal = d.n_nonlocal;
@@ -354,8 +354,11 @@ struct qsim_multi_s {
     a.b0 = 0;
     char* st = reinterpret_cast<char*>(const_cast<void*>(states_c));
     if (!bwd) {
-      a.in = p == 0 ? nullptr : st;
-      a.out = st;
+      // intermediate states in the workspace W (updated in place); the last pass, which restores the
+      // canonical qubit order and so does not write the addresses it reads, writes the state block
+      char* w = reinterpret_cast<char*>(W) + amp0 * el;
+      a.in = p == 0 ? nullptr : w;
+      a.out = p == P(c) - 1 ? st : w;
       a.zpart = p == P(c) - 1 ? zpart + zp_off[c] : nullptr;
     } else {
       char* w = reinterpret_cast<char*>(W) + amp0 * el;
@@ -386,9 +389,9 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
   if (o.mode != QSIM_FUSED) return mfail(QSIM_ERR_ARG, "multi-circuit plans use the fused mode");
   if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return mfail(QSIM_ERR_ARG, "bad dtype");
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
-      (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs != 0 || o.reserved != 0)
-    return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], weight_remap 0 or 1, max_regs and "
-                               "reserved 0 (multi-circuit kernels size their own CTAs)");
+      (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs != 0)
+    return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], weight_remap 0 or 1, max_regs 0 "
+                               "(multi-circuit kernels size their own CTAs)");
   if (o.k == 0 || o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   auto* m = new qsim_multi_s();
   m->opts = o;
@@ -423,7 +426,7 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
         }
         oc.k = h_k[c];
       }
-      rc = build_schedule(gv, n_qubits[c], oc, Rf, Rb, s, err);
+      rc = build_schedule(gv, n_qubits[c], oc, Rf, Rb, s, err, false);
     }
     if (rc) {
       delete m;

@@ -62,8 +62,14 @@ struct DevPass {
   int32_t n_nonlocal, pad0;
   int64_t tiles_per_sample;
   int64_t gpart_offset;             // offset of this pass's gradient partials (per batch layout)
-  uint8_t L[kMaxTileBits];          // physical bit position of each tile bit
-  uint8_t nonlocal[40];             // physical bit positions outside the tile, ascending
+  // Layouts: the pass reads its input in layout pi_p and writes its output in pi_{p+1} (logical qubit
+  // -> physical index bit; pi_0 and the last output layout are canonical, qubit q at bit n-1-q).
+  uint8_t L[kMaxTileBits];          // tile bit j: physical bit in the input layout
+  uint8_t nonlocal[40];             // tile-index bit i (a qubit outside the tile): input-layout bit
+  uint8_t Lo[kMaxTileBits];         // tile bit j: physical bit in the output layout
+  uint8_t nonlocal_o[40];           // tile-index bit i: output-layout bit
+  uint8_t Q[kMaxTileBits];          // logical qubit of tile bit j
+  uint8_t QN[40];                   // logical qubit of tile-index bit i
 };
 
 }  // namespace qsim

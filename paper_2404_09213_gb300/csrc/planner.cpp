@@ -155,32 +155,40 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
   const int n = s.n, k = d.k, R = d.R;
   int tb_of_q[kMaxQubits];
   for (int q = 0; q < n; q++) tb_of_q[q] = -1;
-  for (int j = 0; j < k; j++) tb_of_q[n - 1 - d.L[j]] = j;
+  for (int j = 0; j < k; j++) tb_of_q[d.Q[j]] = j;
   d.phase0 = (int)s.phases.size();
   d.op0 = (int)s.ops.size();
   d.lay0 = (int)s.layouts.size();
   std::vector<int> remaining = pp.gates;
   int gslot = 0;
   // The first and the last register phase move their amplitudes straight between registers and global
-  // memory; keeping tile bits 1..3 (the low index bits of a contiguous run) out of their register sets
-  // makes lanes 0..7 of a warp cover one contiguous 128-byte run.
-  std::vector<int> edge_excl;
+  // memory: the first in the pass's input layout, the last in its output layout. The tile bits at
+  // physical bits 1..3 of that layout (the low bits of a contiguous run) lead the phase's thread bits,
+  // so lanes 0..7 of a warp cover one contiguous 128-byte run.
+  std::vector<int> fin, fout;
   if (k - R >= 3)
-    for (int j = 1; j <= 3 && j < s.c; j++) edge_excl.push_back(j);
-  auto excluded = [&](int tb, bool edge) {
-    return edge && std::find(edge_excl.begin(), edge_excl.end(), tb) != edge_excl.end();
-  };
-  auto make_phase = [&](std::vector<int> regs, const std::vector<int>& taken, bool edge) {
+    for (int b = 1; b <= 3 && b < s.c; b++)
+      for (int j = 0; j < k; j++) {
+        if (d.L[j] == b) fin.push_back(j);
+        if (d.Lo[j] == b) fout.push_back(j);
+      }
+  auto in_list = [](const std::vector<int>& v, int x) { return std::find(v.begin(), v.end(), x) != v.end(); };
+  auto excluded = [&](int tb, bool edge) { return edge && in_list(fin, tb); };
+  // front: tile bits that must be the phase's leading thread bits (and so not register bits)
+  auto make_phase = [&](std::vector<int> regs, const std::vector<int>& taken, const std::vector<int>* front) {
     for (int j = k - 1; j >= 0 && (int)regs.size() < R; j--)
-      if (std::find(regs.begin(), regs.end(), j) == regs.end() && !excluded(j, edge)) regs.push_back(j);
+      if (!in_list(regs, j) && !(front && in_list(*front, j))) regs.push_back(j);
     for (int j = k - 1; j >= 0 && (int)regs.size() < R; j--)   // small tiles: any bit
-      if (std::find(regs.begin(), regs.end(), j) == regs.end()) regs.push_back(j);
+      if (!in_list(regs, j)) regs.push_back(j);
     std::sort(regs.begin() + 1, regs.end());
     DevPhase ph{};
     for (int i = 0; i < R; i++) ph.rbit[i] = (uint8_t)regs[i];
     int nt = 0;
+    if (front)
+      for (int j : *front)
+        if (!in_list(regs, j)) ph.tbit[nt++] = (uint8_t)j;
     for (int j = 0; j < k; j++)
-      if (std::find(regs.begin(), regs.end(), j) == regs.end()) ph.tbit[nt++] = (uint8_t)j;
+      if (!in_list(regs, j) && !(front && in_list(*front, j))) ph.tbit[nt++] = (uint8_t)j;
     ph.n_tbits = (uint8_t)nt;
     ph.op_begin = (int)s.ops.size();
     auto reg_of = [&](int tb) {
@@ -267,23 +275,25 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
       }
     }
     const bool last = rest.empty();
-    // a phase that is both first and last must respect the constraint; otherwise only the first does here
-    bool edge = first;
+    // the first phase loads in the input layout; a last phase also stores in the output layout when
+    // its registers allow (else an op-free closing phase does, below)
+    const std::vector<int>* front = first ? &fin : nullptr;
     if (last && !first) {
       bool viol = false;
-      for (int t : regs) viol = viol || excluded(t, true);
-      edge = !viol;   // respects the store constraint if it can; else an extra phase is added below
+      for (int t : regs) viol = viol || in_list(fout, t);
+      if (!viol) front = &fout;
     }
-    make_phase(regs, taken, first || (last && edge));
+    make_phase(regs, taken, front);
     first = false;
     remaining = rest;
   }
-  // the last phase stores to global memory: add an op-free phase if its register set breaks the rule
-  if (!edge_excl.empty()) {
+  // the last phase stores to global memory: add an op-free phase unless its leading thread bits are
+  // the output layout's run
+  if (!fout.empty()) {
     const DevPhase& lp = s.phases.back();
-    bool viol = false;
-    for (int i = 0; i < R; i++) viol = viol || excluded(lp.rbit[i], true);
-    if (viol) make_phase({0}, {}, true);
+    bool ok = lp.n_tbits >= (int)fout.size();
+    for (size_t i = 0; ok && i < fout.size(); i++) ok = lp.tbit[i] == fout[i];
+    if (!ok) make_phase({0}, {}, &fout);
   }
   d.n_phases = (int)s.phases.size() - d.phase0;
   d.n_ops = (int)s.ops.size() - d.op0;
@@ -300,7 +310,7 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
 }
 
 int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& o, int R_fwd, int R_bwd,
-                   Schedule& s, std::string& err) {
+                   Schedule& s, std::string& err, bool rotate_low) {
   s = Schedule{};
   s.n = n;
   s.gates = gates;
@@ -351,17 +361,28 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
     }
     return QSIM_OK;
   }
-  // ---- greedy k-local fusion, per-wire order preserved
+  // ---- greedy k-local fusion, per-wire order preserved, with a rotating coalescing set.
+  // The c lowest physical index bits must be tile bits of every pass (runs of 2^c amplitudes give
+  // coalesced accesses). Physical bit 0 always holds qubit n-1 (the pair in one 16-byte word). Bits
+  // 1..c-1 are handed between passes to qubits local in both passes, picked by their next use, so
+  // they stop occupying tile slots for qubits the circuit does not touch next: pass p writes its
+  // output in the new layout, a qubit remap that costs no memory traffic of its own (the paper's
+  // reshape that moves the group's qubits into their own dimension, Sec. "Circuit Splitting", done by
+  // the store addressing). The last pass writes the canonical layout.
   std::vector<char> done(G, 0);
   int n_done = 0;
-  std::set<int> always;
-  for (int q = n - c; q < n; q++) always.insert(q);
-  s.passes.reserve(G + 1);
-  while (n_done < G || s.passes.empty()) {
-    std::set<int> S = always, blocked;
-    PassPlan pp;
+  std::vector<int> phys(n), at(n);   // current layout: logical qubit -> physical bit, and inverse
+  for (int q = 0; q < n; q++) {
+    phys[q] = n - 1 - q;
+    at[n - 1 - q] = q;
+  }
+  const bool rotate = rotate_low && k >= 2 * c + 2;   // room for the carried low qubits plus the canonical ones
+  std::set<int> canon_low;
+  for (int b = 0; b < c; b++) canon_low.insert(n - 1 - b);
+  auto greedy = [&](std::set<int> S, std::vector<char>& dn, std::vector<int>& took) {
+    std::set<int> blocked;
     for (int i = 0; i < G; i++) {
-      if (done[i]) continue;
+      if (dn[i]) continue;
       int q[2], nq;
       gate_qubits(gates[i], q, nq);
       bool blk = false;
@@ -374,37 +395,108 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
       for (int j = 0; j < nq; j++) T.insert(q[j]);
       if ((int)T.size() <= k) {
         S = T;
-        pp.gates.push_back(i);
-        done[i] = 1;
-        n_done++;
+        took.push_back(i);
+        dn[i] = 1;
       } else {
         for (int j = 0; j < nq; j++) blocked.insert(q[j]);
       }
     }
-    if (pp.gates.empty() && G > 0) {
+    return S;
+  };
+  auto set_out_layout = [&](DevPass& d) {   // output layout of a pass = the current layout
+    for (int j = 0; j < d.k; j++) d.Lo[j] = (uint8_t)phys[d.Q[j]];
+    for (int i = 0; i < d.n_nonlocal; i++) d.nonlocal_o[i] = (uint8_t)phys[d.QN[i]];
+  };
+  std::vector<int> prevS;
+  s.passes.reserve(G + 1);
+  while (n_done < G || s.passes.empty()) {
+    if (rotate && !s.passes.empty()) {
+      // hand physical bits 1..c-1 to the previous pass's qubits that are needed soonest
+      std::vector<int> next_use(n, G);
+      for (int i = G - 1; i >= 0; i--) {
+        if (done[i]) continue;
+        int q[2], nq;
+        gate_qubits(gates[i], q, nq);
+        for (int j = 0; j < nq; j++) next_use[q[j]] = i;
+      }
+      std::vector<int> cand;
+      for (int q : prevS)
+        if (q != at[0]) cand.push_back(q);
+      std::stable_sort(cand.begin(), cand.end(), [&](int a, int b) {
+        return next_use[a] != next_use[b] ? next_use[a] < next_use[b] : phys[a] < phys[b];
+      });
+      for (int b = 1; b < c; b++) {
+        const int qn = cand[b - 1], qo = at[b], pb = phys[qn];
+        phys[qn] = b;
+        at[b] = qn;
+        phys[qo] = pb;
+        at[pb] = qo;
+      }
+    }
+    if (!s.passes.empty()) set_out_layout(s.passes.back().dev);   // the previous pass writes this layout
+    std::set<int> S0;
+    for (int b = 0; b < c; b++) S0.insert(at[b]);
+    std::vector<char> dn = done;
+    std::vector<int> took;
+    std::set<int> S = greedy(S0, dn, took);
+    if (rotate && n_done + (int)took.size() == G) {
+      // the last pass writes the canonical layout: its low qubits must be in the tile
+      std::set<int> T = S;
+      T.insert(canon_low.begin(), canon_low.end());
+      if ((int)T.size() <= k) {
+        S = T;
+      } else {
+        std::set<int> S1 = S0;
+        S1.insert(canon_low.begin(), canon_low.end());
+        dn = done;
+        took.clear();
+        S = greedy(S1, dn, took);
+      }
+    }
+    if (took.empty() && G > 0) {
       err = "internal: fusion made no progress";
       return QSIM_ERR_ARG;
     }
-    // pad the local set to k qubits, lowest physical positions first
-    for (int pos = 0; pos < n && (int)S.size() < k; pos++) S.insert(n - 1 - pos);
-    std::vector<int> pos;
-    for (int q : S) pos.push_back(n - 1 - q);
-    std::sort(pos.begin(), pos.end());
+    done = dn;
+    n_done += (int)took.size();
+    PassPlan pp;
+    pp.gates = took;
+    // pad the local set to k qubits, lowest physical bits first
+    for (int b = 0; b < n && (int)S.size() < k; b++) S.insert(at[b]);
+    // tile bits: 0..c-1 = physical bits 0..c-1 of the input layout, then the rest by physical bit
+    std::vector<int> Q;
+    for (int b = 0; b < c; b++) Q.push_back(at[b]);
+    std::vector<int> rest;
+    for (int q : S)
+      if (phys[q] >= c) rest.push_back(q);
+    std::sort(rest.begin(), rest.end(), [&](int a, int b) { return phys[a] < phys[b]; });
+    Q.insert(Q.end(), rest.begin(), rest.end());
     DevPass& d = pp.dev;
     d.k = k;
     d.R = R;
     for (int j = 0; j < k; j++) {
-      d.L[j] = (uint8_t)pos[j];
-      pp.local_qubits.push_back(n - 1 - pos[j]);
+      d.Q[j] = (uint8_t)Q[j];
+      d.L[j] = (uint8_t)phys[Q[j]];
+      pp.local_qubits.push_back(Q[j]);
     }
     int nl = 0;
-    for (int p = 0; p < n; p++)
-      if (std::find(pos.begin(), pos.end(), p) == pos.end()) d.nonlocal[nl++] = (uint8_t)p;
+    for (int b = 0; b < n; b++)
+      if (!S.count(at[b])) {
+        d.QN[nl] = (uint8_t)at[b];
+        d.nonlocal[nl++] = (uint8_t)b;
+      }
     d.n_nonlocal = nl;
     d.tiles_per_sample = (int64_t)1 << nl;
+    prevS = Q;
     s.passes.push_back(pp);
     if (G == 0) break;
   }
+  // the last pass writes the canonical layout
+  for (int q = 0; q < n; q++) {
+    phys[q] = n - 1 - q;
+    at[n - 1 - q] = q;
+  }
+  set_out_layout(s.passes.back().dev);
   const int w0 = (o.dtype == QSIM_C128) ? 0 : 1;
   Lcg rng{0x51ED270B5EEDULL};
   for (auto& pp : s.passes) {
@@ -439,6 +531,12 @@ std::string describe_schedule(const Schedule& s) {
     for (int j = 0; j < d.k; j++) o << (j ? "," : "") << (int)d.L[j];
     o << "],\"nonlocal\":[";
     for (int j = 0; j < d.n_nonlocal; j++) o << (j ? "," : "") << (int)d.nonlocal[j];
+    o << "],\"Lo\":[";
+    for (int j = 0; j < d.k; j++) o << (j ? "," : "") << (int)d.Lo[j];
+    o << "],\"nonlocal_o\":[";
+    for (int j = 0; j < d.n_nonlocal; j++) o << (j ? "," : "") << (int)d.nonlocal_o[j];
+    o << "],\"QN\":[";
+    for (int j = 0; j < d.n_nonlocal; j++) o << (j ? "," : "") << (int)d.QN[j];
     o << "],\"n_gslots\":" << d.n_gslots;
     for (int dir = 0; dir < 2; dir++) {
       const DevPass& D = dir == 0 ? pp.dev : pp.devb;

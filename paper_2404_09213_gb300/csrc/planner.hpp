@@ -45,8 +45,11 @@ int validate_gates(const qsim_gate* g, int n_gates, int n, std::vector<Gate>& ou
                    int& n_inputs, std::string& err);
 
 // Build the full schedule. R is the register bits per phase (<= kMaxR).
+// rotate_low: hand the coalescing bits 1..c-1 between passes (fewer passes; single-circuit plans).
+// Multi-circuit plans keep them fixed: every circuit then repeats a few pass structures, and the queue
+// kernel links one function per distinct structure.
 int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& o, int R_fwd, int R_bwd,
-                   Schedule& s, std::string& err);
+                   Schedule& s, std::string& err, bool rotate_low = true);
 
 std::string describe_schedule(const Schedule& s);
 

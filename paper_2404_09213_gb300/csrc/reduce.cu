@@ -133,16 +133,15 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // z[b][q] from per-tile partials: block per (b, q).
-__global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Lnl, int n_nonlocal, int64_t tps,
+__global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Qnl, int n_nonlocal, int64_t tps,
                                int n, int B, double* z) {
   __shared__ double sh[32];
   const int b = blockIdx.x / n, q = blockIdx.x - (blockIdx.x / n) * n;
-  const int pos = n - 1 - q;
-  int tbit = -1, nlbit = -1;
+  int tbit = -1, nlbit = -1;   // qubit q is tile bit tbit or tile-index bit nlbit of the last pass
   for (int j = 0; j < k; j++)
-    if (Lnl[j] == pos) tbit = j;
+    if (Qnl[j] == q) tbit = j;
   for (int j = 0; j < n_nonlocal; j++)
-    if (Lnl[k + j] == pos) nlbit = j;
+    if (Qnl[k + j] == q) nlbit = j;
   double acc = 0.0;
   for (int64_t t = threadIdx.x; t < tps; t += blockDim.x) {
     const double* row = zpart + ((int64_t)b * tps + t) * (k + 1);
@@ -153,10 +152,10 @@ __global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Lnl, i
   if (threadIdx.x == 0) z[(int64_t)b * n + q] = acc;
 }
 
-cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Lnl, int n_nonlocal, int64_t tps, int n,
+cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Qnl, int n_nonlocal, int64_t tps, int n,
                            int B, double* z, cudaStream_t st) {
   if ((int64_t)B * n == 0) return cudaSuccess;
-  z_final_kernel<<<(unsigned)(B * n), 256, 0, st>>>(zpart, k, d_Lnl, n_nonlocal, tps, n, B, z);
+  z_final_kernel<<<(unsigned)(B * n), 256, 0, st>>>(zpart, k, d_Qnl, n_nonlocal, tps, n, B, z);
   g_kernel_launches++;
   return cudaGetLastError();
 }
@@ -224,13 +223,12 @@ __global__ void z_final_multi_kernel(ZMultiArgs a) {
   const ZCirc d = a.circ[c];
   const int64_t r = gz - (int64_t)a.B * a.zq_off[c];
   const int b = (int)(r / d.n), q = (int)(r - (int64_t)b * d.n);
-  const int pos = d.n - 1 - q;
-  const uint8_t* Lnl = a.bits + d.bits_off;
+  const uint8_t* Qnl = a.bits + d.bits_off;   // logical qubits of the last pass's tile and tile-index bits
   int tbit = -1, nlbit = -1;
   for (int j = 0; j < d.k; j++)
-    if (Lnl[j] == pos) tbit = j;
+    if (Qnl[j] == q) tbit = j;
   for (int j = 0; j < d.n_nonlocal; j++)
-    if (Lnl[d.k + j] == pos) nlbit = j;
+    if (Qnl[d.k + j] == q) nlbit = j;
   double acc = 0.0;
   for (int64_t t = threadIdx.x; t < d.tps; t += blockDim.x) {
     const double* row = a.zpart + d.zp_off + ((int64_t)b * d.tps + t) * (d.k + 1);

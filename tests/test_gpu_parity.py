@@ -76,6 +76,17 @@ for seed, (n, dtype, mode, k, c) in enumerate([
 
 @pytest.mark.parametrize("seed,n,dtype,mode,k,c", CASES)
 def test_random_circuits(q, seed, n, dtype, mode, k, c):
+    _random_case(q, seed, n, dtype, mode, k, c)
+
+
+# qubits handed between the low (coalescing) index bits from pass to pass: each pass writes a new layout
+@pytest.mark.parametrize("seed,n,dtype,k,c", [(20, 11, "c64", 8, 3), (21, 12, "c64", 10, 4), (22, 13, "c128", 11, 4),
+                                              (23, 12, "c64", 6, 2)])
+def test_random_circuits_rotating_layouts(q, seed, n, dtype, k, c):
+    _random_case(q, seed, n, dtype, "fused", k, c, rotate_low_bits=True)
+
+
+def _random_case(q, seed, n, dtype, mode, k, c, **kw):
     rng = np.random.default_rng(100 + seed)
     n_par, n_in, B = 7, 3, 3
     gates = random_circuit(rng, n, 8 * n + 10, n_par, n_in)
@@ -91,7 +102,7 @@ def test_random_circuits(q, seed, n, dtype, mode, k, c):
     pr, ir = rounded(wl, dtype)
     cdt = torch.complex128 if dtype == "c128" else torch.complex64
     init = torch.tensor(init_np, dtype=cdt, device="cuda") if use_init else None
-    r = run(q, wl, dtype, mode, init=init, k=k, contiguous_bits=c)
+    r = run(q, wl, dtype, mode, init=init, k=k, contiguous_bits=c, **kw)
     init_ref = init.cpu().numpy().astype(np.complex128) if use_init else None
     psi = oracle.simulate_strided(gates, n, pr, ir, init=init_ref)
     t = TOL[dtype]
@@ -148,10 +159,11 @@ def test_c3_full_size_sampled(q):
 
 
 # ---------------------------------------------------------------- C5 ansatz at 12 qubits, checkpointed
-@pytest.mark.parametrize("ckpt", [0, 1, 3])
-def test_c5_ansatz_12q_checkpointed(q, ckpt):
+@pytest.mark.parametrize("ckpt,rot", [(0, False), (1, False), (3, False), (0, True), (1, True), (2, True)])
+def test_c5_ansatz_12q_checkpointed(q, ckpt, rot):
+    # with rotating layouts the checkpoints hold states in the layouts the passes wrote
     wl = W.config(5, n=12, batch=2)
-    r = run(q, wl, "c64", "fused", k=8, checkpoint_passes=ckpt)
+    r = run(q, wl, "c64", "fused", k=10 if rot else 8, checkpoint_passes=ckpt, rotate_low_bits=rot)
     if ckpt:
         assert r["plan"].info()["n_checkpoints"] >= 1
     pr, ir = rounded(wl, "c64")

@@ -40,11 +40,16 @@ def gate_qubits(g):
 CASES = [("ring20", W.ring_ansatz(20, 10), 20, {}), ("ring12", W.ring_ansatz(12, 6), 12, {}),
          ("ring30", W.ring_ansatz(30, 2), 30, {}), ("hea15", W.hea_cz_ansatz(15, 5), 15, {}),
          ("ring20k8", W.ring_ansatz(20, 3), 20, {"k": 8}), ("ring10c2", W.ring_ansatz(10, 3), 10, {"k": 6, "contiguous_bits": 2}),
-         ("c128", W.ring_ansatz(16, 3), 16, {"dtype": "c128"})]
+         ("c128", W.ring_ansatz(16, 3), 16, {"dtype": "c128"}),
+         ("ring20rot", W.ring_ansatz(20, 10), 20, {"rotate_low_bits": True}),
+         ("ring30rot", W.ring_ansatz(30, 2), 30, {"rotate_low_bits": True, "k": 11}),
+         ("hea15rot", W.hea_cz_ansatz(15, 5), 15, {"rotate_low_bits": True, "k": 10}),
+         ("c128rot", W.ring_ansatz(16, 3), 16, {"dtype": "c128", "rotate_low_bits": True})]
 _r = random.Random(7)
 for i in range(12):
     n = _r.randint(1, 14)
-    CASES.append((f"rand{i}", random_circuit(_r, n, _r.randint(0, 60)), n, {"k": _r.randint(min(n, 6), 12)}))
+    CASES.append((f"rand{i}", random_circuit(_r, n, _r.randint(0, 60)), n,
+                  {"k": _r.randint(min(n, 6), 12), "rotate_low_bits": bool(i % 2)}))
 
 
 @pytest.mark.parametrize("name,gates,n,kw", CASES, ids=[c[0] for c in CASES])
@@ -63,13 +68,14 @@ def test_schedule_invariants(q, name, gates, n, kw):
             if w in last:
                 assert pos[last[w]] < pos[gi], f"wire {w}: gate {gi} before {last[w]}"
             last[w] = gi
+    check_layouts(d, n)
     for ps in d["passes"]:
         local = ps["local_qubits"]
         assert len(local) == k and len(set(local)) == k
-        assert sorted(ps["L"]) == ps["L"] and ps["L"] == [n - 1 - q_ for q_ in local]
-        assert sorted(ps["L"] + ps["nonlocal"]) == list(range(n))
         c = d["c"]
-        assert ps["L"][:c] == list(range(c)), "low index bits must be local (coalescing)"
+        assert ps["L"][:c] == list(range(c)), "low index bits of the read layout must be local (coalescing)"
+        assert set(range(c)) <= set(ps["Lo"]), "low index bits of the written layout must be local"
+        assert ps["Lo"][0] == 0, "bit 0 (the 16-byte pair) keeps its qubit"
         for g in ps["gates"]:
             assert set(gate_qubits(gates[g])) <= set(local)
         for ph_key, lay_key, RR in (("phases", "layouts", R), ("bwd_phases", "bwd_layouts", d["Rb"])):
@@ -78,6 +84,31 @@ def test_schedule_invariants(q, name, gates, n, kw):
         slots = sorted(op["gslot"] for ph in ps["bwd_phases"] for op in ph["ops"] if op["gslot"] >= 0)
         assert slots == list(range(ps["n_gslots"]))
         assert ps["n_gslots"] == sum(1 for g in ps["gates"] if gates[g][0] in (W.RX, W.RY, W.RZ))
+
+
+def layout(ps, out):
+    """qubit -> physical bit of the layout a pass reads (out=False) or writes (out=True)."""
+    L, NL = (ps["Lo"], ps["nonlocal_o"]) if out else (ps["L"], ps["nonlocal"])
+    m = {q_: b for q_, b in zip(ps["local_qubits"], L)}
+    m.update({q_: b for q_, b in zip(ps["QN"], NL)})
+    return m
+
+
+def check_layouts(d, n):
+    canon = {q_: n - 1 - q_ for q_ in range(n)}
+    passes = d["passes"]
+    for ps in passes:
+        for out in (False, True):
+            m = layout(ps, out)
+            assert sorted(m) == list(range(n)) and sorted(m.values()) == list(range(n)), "a bijection"
+    assert layout(passes[0], False) == canon, "the first pass reads the canonical layout"
+    assert layout(passes[-1], True) == canon, "the last pass writes the canonical layout"
+    for a, b in zip(passes, passes[1:]):
+        assert layout(a, True) == layout(b, False), "a pass reads the layout its predecessor wrote"
+    # every pass but the last writes exactly the addresses it reads (only qubits of its tile change
+    # places), so those passes may update a buffer in place
+    for ps in passes[:-1]:
+        assert ps["nonlocal_o"] == ps["nonlocal"] and sorted(ps["Lo"]) == sorted(ps["L"])
 
 
 def check_phases(gates, ps, phases, layouts, k, R, local):
@@ -119,7 +150,7 @@ def check_phases(gates, ps, phases, layouts, k, R, local):
 
 
 @pytest.mark.parametrize("n,kw", [(6, {"k": 4, "contiguous_bits": 2}), (10, {"k": 6}), (14, {"k": 9}),
-                                  (16, {"k": 12})])
+                                  (16, {"k": 12}), (16, {"k": 10, "rotate_low_bits": True})])
 def test_index_maps_are_the_brute_force_permutation(q, n, kw):
     gates = W.ring_ansatz(n, 2)
     p = q.Plan(gates, n, **kw)
@@ -151,15 +182,29 @@ def test_empty_circuit_and_single_qubit(q):
     assert d1["k"] == 1 and [ps["gates"] for ps in d1["passes"]] == [[0, 1]]
 
 
-@pytest.mark.parametrize("n,kw", [(20, {}), (16, {"dtype": "c128"}), (14, {"k": 10}), (13, {"k": 12})])
+@pytest.mark.parametrize("n,kw", [(20, {}), (16, {"dtype": "c128"}), (14, {"k": 10}), (13, {"k": 12}),
+                                  (20, {"rotate_low_bits": True}), (18, {"k": 10, "rotate_low_bits": True})])
 def test_edge_phases_keep_the_contiguous_run_in_threads(q, n, kw):
-    # first and last register phase move data straight between registers and global memory: tile bits
-    # 1..3 (the low bits of a contiguous run) must be thread bits there so a warp's accesses coalesce
+    # first and last register phase move data straight between registers and global memory: the tile
+    # bits at physical bits 1..3 (the low bits of a contiguous run) must lead the thread bits there so
+    # a warp's accesses coalesce
     d = q.Plan(W.ring_ansatz(n, 3), n, **kw).describe()
     for ps in d["passes"]:
         for key, R in (("phases", d["R"]), ("bwd_phases", d["Rb"])):
             if d["k"] - R < 3:
                 continue
-            for ph in (ps[key][0], ps[key][-1]):
-                assert not ({1, 2, 3} & set(ph["rbits"])), (key, ph["rbits"])
-                assert ph["tbits"][:3] == [1, 2, 3]
+            # phase 0 moves data in the layout the pass reads, the last phase in the one it writes
+            for ph, L in ((ps[key][0], ps["L"]), (ps[key][-1], ps["Lo"])):
+                run = [L.index(b) for b in (1, 2, 3)]
+                assert not (set(run) & set(ph["rbits"])), (key, ph["rbits"])
+                assert ph["tbits"][:3] == run
+
+
+def test_rotating_low_bits_cut_the_passes():
+    # the 20-qubit ring workload at k = 12: the c = 4 coalescing bits are handed between passes
+    # instead of holding qubits 16..19 in every tile (24 passes with them fixed)
+    import paper_2404_09213_gb300 as qq
+    wl = W.config(3)
+    assert qq.Plan(wl.gates, wl.n, k=12, rotate_low_bits=True).info()["n_passes"] <= 20
+    assert qq.Plan(wl.gates, wl.n, k=11, rotate_low_bits=True).info()["n_passes"] <= 25
+    assert qq.Plan(wl.gates, wl.n, k=12).info()["n_passes"] == 24
