@@ -3,17 +3,17 @@
  *
  * What it computes (arXiv 2404.09213, "Qandle"):
  *   - a batch of B states of n qubits, psi_b in C^(2^n), stored (B, 2^n) row-major with interleaved
- *     (re, im) — the batched shape (B, 2^W) of Section II-D;
- *   - qubit q is the q-th MOST significant index bit (MSb-0, Section II-A): bit (n-1-q) of x;
- *   - a gate list (Section II-B: embedding layers, trainable layers) applied in order, each gate one
+ *     (re, im) — the batched shape (B, 2^W) of Sec. "Concept of Shapes";
+ *   - qubit q is the q-th MOST significant index bit (MSb-0, Sec. "Symbols"): bit (n-1-q) of x;
+ *   - a gate list (Sec. "Hybrid Machine Learning": embedding layers, trainable layers) applied in order, each gate one
  *     of RX, RY, RZ (R_P(theta) = exp(-i theta P / 2); RX written as in Eq. 1), H, X, CNOT, CZ;
  *   - the measurement layer <Z_i>_b = sum_x |psi_b[x]|^2 (1 - 2 bit_i(x)) for every qubit i;
- *   - gradients of L = sum_{b,i} g_{b,i} <Z_i>_b by the adjoint method (Section II-B: backpropagation
+ *   - gradients of L = sum_{b,i} g_{b,i} <Z_i>_b by the adjoint method (Sec. "Hybrid Machine Learning": backpropagation
  *     through the simulator); shared parameters sum over the batch, inputs are per sample.
  *
  * Gates are never expanded to 2^n x 2^n matrices (the paper's Eq. 2 caching): the planner groups
  * consecutive gates touching at most k qubits into one pass over the state (the circuit splitting
- * of Section III-B), and each 2x2 is formed on the device from the angle.
+ * of Sec. "Circuit Splitting"), and each 2x2 is formed on the device from the angle.
  *
  * Conventions for every call below:
  *   - status: 0 = QSIM_OK, negative = error; the message is in qsim_last_error() (thread-local).
@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-/* Gate types (Section III-A names R_x; RY/RZ/H/X/CNOT/CZ follow the textbook definitions). */
+/* Gate types (Sec. "Gate Matrix Caching" names R_x; RY/RZ/H/X/CNOT/CZ follow the textbook definitions). */
 enum { QSIM_RX = 0, QSIM_RY = 1, QSIM_RZ = 2, QSIM_H = 3, QSIM_X = 4, QSIM_CNOT = 5, QSIM_CZ = 6 };
 
 /* One gate: {type, targets, controls, param index}.
@@ -198,7 +198,7 @@ int qsim_expval_z_noalloc(const void* d_states, int32_t batch, int32_t n_qubits,
 
 /* ------------------------------------------------------------------------------------------------
  * Several circuits of uneven size in one persistent launch per direction (the batched training of
- * many hybrid models; Section II-B's circuits, each planned as above).
+ * many hybrid models; Sec. "Hybrid Machine Learning"'s circuits, each planned as above).
  *
  * Every circuit gets its own k-local passes; a device work queue lists tile jobs in rounds (pass 0 of
  * every circuit, then pass 1, ...). One persistent kernel per direction claims jobs with an atomic

@@ -7,18 +7,18 @@ It computes, plainly and slowly, what the accelerated path computes:
 
 * ``gates``     2x2 gate matrices (RX via the paper's partial-matrix decomposition, Eq. 1) and their
                 Kronecker expansion to the full register (Eq. 2, reading: I_{2^w} (x) G (x) I_{2^(W-1-w)}
-                with 0-based w, MSb-0 as in Section II-A).
+                with 0-based w, MSb-0 as in Sec. "Symbols").
 * ``kron``      Oracle-K: every gate expanded to a dense 2^W x 2^W matrix by explicit Kronecker
-                products and applied by a dense matrix-vector product (Section III-A, Eq. 2).
+                products and applied by a dense matrix-vector product (Sec. "Gate Matrix Caching", Eq. 2).
 * ``strided``   Oracle-S: every gate applied by reshaping the state to (2^w, 2, 2^(W-1-w)) and
-                contracting the middle axis (the reshape method of Section II-D); used above 12 qubits.
-* ``measure``   <Z_i> = sum_x |psi_x|^2 (1 - 2 bit_i(x)) (measurement layer, Section II-B).
+                contracting the middle axis (the reshape method of Sec. "Concept of Shapes"); used above 12 qubits.
+* ``measure``   <Z_i> = sum_x |psi_x|^2 (1 - 2 bit_i(x)) (measurement layer, Sec. "Hybrid Machine Learning").
 * ``grad``      loss L = sum_{b,i} g_{b,i} <Z_i>_b, its gradient by the parameter-shift rule
-                (exact for exp(-i theta P / 2)) and by central finite differences (Section II-B
+                (exact for exp(-i theta P / 2)) and by central finite differences (Sec. "Hybrid Machine Learning"
                 mentions both; the reading that the shift rule is exact, not a finite difference,
                 is recorded in the design notes).
 * ``bitsim``    a pure-Python per-basis-index simulator used only to pin the other two on tiny inputs.
-* ``remapping`` quantum weight remapping angle = pi * tanh(weight) and its chain rule (Section III-C).
+* ``remapping`` quantum weight remapping angle = pi * tanh(weight) and its chain rule (Sec. "Additional Optimizations").
 
 Every function here is pinned by tests in ``tests/test_oracle_pins.py`` against closed forms,
 library routines (scipy ``expm``) and brute force; none is "parity unpinned".

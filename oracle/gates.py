@@ -1,6 +1,6 @@
-"""Gate matrices and their Kronecker expansion (Section III-A).
+"""Gate matrices and their Kronecker expansion (Sec. "Gate Matrix Caching").
 
-Conventions (Section II-A and II-D of the paper): qubit w is the w-th most significant bit of an
+Conventions (Secs. "Symbols" and "Concept of Shapes" of the paper): qubit w is the w-th most significant bit of an
 amplitude index, so on W qubits a single-qubit gate G on qubit w is I_{2^w} (x) G (x) I_{2^(W-1-w)}.
 The printed exponent in Eq. 2 (I_{2^(W-w)} after the gate) would give dimension 2^(W+1); the reading
 used here is the 0-based one that keeps the dimension at 2^W.

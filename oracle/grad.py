@@ -1,4 +1,4 @@
-"""Loss and reference gradients (Section II-B: parameter-shift rule and backpropagation).
+"""Loss and reference gradients (Sec. "Hybrid Machine Learning": parameter-shift rule and backpropagation).
 
 L = sum_{b,i} g_{b,i} <Z_i>_b. Trainable parameters are shared by the batch, so dL/dparams sums
 over samples; encoded inputs belong to one sample each, so dL/dinputs is per sample.

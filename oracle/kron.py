@@ -1,4 +1,4 @@
-"""Oracle-K: dense Kronecker-expanded simulation (Section III-A, Eq. 2).
+"""Oracle-K: dense Kronecker-expanded simulation (Sec. "Gate Matrix Caching", Eq. 2).
 
 Each gate is expanded to its full 2^W x 2^W matrix and applied to every state by a dense product,
 in circuit order. Gates whose angle is shared by the whole batch are applied to all samples at once

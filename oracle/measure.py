@@ -1,7 +1,7 @@
-"""Measurement layer (Section II-B): Pauli-Z expectation values of every qubit.
+"""Measurement layer (Sec. "Hybrid Machine Learning"): Pauli-Z expectation values of every qubit.
 
 <Z_i>_b = sum_x |psi_b[x]|^2 (1 - 2 bit_i(x)), where bit_i(x) is the i-th most significant of the n
-index bits (MSb-0, Section II-A), i.e. (x >> (n-1-i)) & 1.
+index bits (MSb-0, Sec. "Symbols"), i.e. (x >> (n-1-i)) & 1.
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-"""Quantum weight remapping (Section III-C, "Additional Optimizations") — test infrastructure only.
+"""Quantum weight remapping (Sec. "Additional Optimizations") — test infrastructure only.
 
 The paper maps every trainable weight into a bounded range such as [-pi, pi] with a smooth function,
 naming the hyperbolic tangent; the reading taken here is angle = pi * tanh(weight), applied to the

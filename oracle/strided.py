@@ -1,4 +1,4 @@
-"""Oracle-S: per-gate strided simulation by reshaping (Section II-D).
+"""Oracle-S: per-gate strided simulation by reshaping (Sec. "Concept of Shapes").
 
 The paper applies a single-qubit gate G on qubit w by viewing the state as (..., 2, ...) with the
 w-th axis separate and multiplying by G over that axis. Here the batched state (B, 2^W) is viewed as

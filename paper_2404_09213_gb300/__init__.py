@@ -5,7 +5,7 @@ The Python layer only marshals arguments: every step (angle -> 2x2 coefficients,
 of ``include/qsim.h``.
 
 * :class:`Plan`           — a planned circuit; ``forward`` / ``backward`` on CUDA tensors.
-* :class:`QSimFunction`   — ``torch.autograd.Function`` over a plan (Section IV-A: circuits as
+* :class:`QSimFunction`   — ``torch.autograd.Function`` over a plan (Sec. "API": circuits as
                             modules whose weights are ordinary parameters).
 * :class:`QSimLayer`      — ``torch.nn.Module`` holding the trainable angles.
 * :func:`expval_z`        — the standalone measurement layer.
@@ -349,7 +349,7 @@ class QSimFunction(torch.autograd.Function):
 
 
 class QSimLayer(torch.nn.Module):
-    """A circuit as a module: its rotation angles are an ``nn.Parameter`` (Section IV-A)."""
+    """A circuit as a module: its rotation angles are an ``nn.Parameter`` (Sec. "API")."""
 
     def __init__(self, gates, n_qubits, init_params=None, **plan_kw):
         super().__init__()

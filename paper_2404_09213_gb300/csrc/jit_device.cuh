@@ -3,7 +3,7 @@
 // and shared-memory layouts as compile-time constants); it includes no host or std headers.
 //
 // A CTA owns one tile: the 2^K amplitudes of one sample whose index bits outside the pass's local
-// set are fixed (the reshape to (rest, group) of the paper's Section III-B, with the group axis held
+// set are fixed (the reshape to (rest, group) of the paper's Sec. "Circuit Splitting", with the group axis held
 // in shared memory). Load: 16-byte cp.async copies of runs of 2^c contiguous amplitudes. Compute:
 // register phases of 2^R amplitudes per thread; rotations use the scaled one-FMA forms
 //   RY: [[1,-t],[t,1]] / [[u,-1],[1,u]],  RX: [[1,-it],[-it,1]] / [[u,-i],[-i,u]],

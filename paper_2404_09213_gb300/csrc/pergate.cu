@@ -1,6 +1,6 @@
 // Plain one-kernel-per-gate path: every gate is one full sweep over the batched state.
 //
-// This is the direct GPU counterpart of the paper's Section II-D single-qubit update (reshape the
+// This is the direct GPU counterpart of the paper's Sec. "Concept of Shapes" single-qubit update (reshape the
 // state so the target qubit is its own axis, multiply by the 2x2) with no fusion at all. It is kept
 // as the comparison baseline for the fused path and uses the same precision and reductions.
 #include <cuda_runtime.h>

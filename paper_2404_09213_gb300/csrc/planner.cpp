@@ -1,4 +1,4 @@
-// Host planner: validation, greedy k-local fusion (Section III-B circuit splitting, re-targeted to
+// Host planner: validation, greedy k-local fusion (Sec. "Circuit Splitting" circuit splitting, re-targeted to
 // tiles of 2^k amplitudes), register phases and conflict-free shared-memory layouts.
 #include "planner.hpp"
 

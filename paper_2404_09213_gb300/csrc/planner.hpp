@@ -1,6 +1,6 @@
 // Host planner: validation, k-local fusion into passes, register phases and smem layouts.
 //
-// Section III-B of the paper splits a circuit into groups of gates on at most a few qubits and
+// Sec. "Circuit Splitting" of the paper splits a circuit into groups of gates on at most a few qubits and
 // runs each group as one operation over the reshaped state. Here the group size is k (a tile of
 // 2^k amplitudes in shared memory), groups are chosen greedily in gate order while keeping the
 // per-wire order, and each group becomes one pass of a CUDA kernel.

@@ -10,7 +10,7 @@ namespace qsim {
 std::atomic<long long> g_kernel_launches{0};
 
 // ------------------------------------------------------------------ coefficients
-// Gate-matrix caching (Section III-A, Eq. 1) writes R_x(theta) = cos(theta/2) R_xa + (-i sin(theta/2)) R_xb
+// Gate-matrix caching (Sec. "Gate Matrix Caching", Eq. 1) writes R_x(theta) = cos(theta/2) R_xa + (-i sin(theta/2)) R_xb
 // with fixed partial matrices and two angle-dependent scalars. Here the scalars are formed once per
 // forward for every (gate, sample) and stored as one coefficient per rotation (tan or cot of theta/2,
 // whichever is at most 1 in magnitude) plus the factored-out cos / sin, accumulated per pass.

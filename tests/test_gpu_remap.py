@@ -1,4 +1,4 @@
-"""Quantum weight remapping (angle = pi * tanh(weight) for trainable weights, Sec. III-C) on the GPU
+"""Quantum weight remapping (angle = pi * tanh(weight) for trainable weights, Sec. "Additional Optimizations") on the GPU
 path against the FP64 oracle: states, <Z> and dL/dweights through the chain rule, single and
 multi-circuit plans, fused and per-gate modes."""
 import math

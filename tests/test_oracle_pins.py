@@ -94,7 +94,7 @@ def test_paper_worked_examples():
 
 
 def _check_reshape_example(n, group, shape):
-    """Section III-B: a sub-circuit on ``group`` is applied by viewing the state as
+    """Sec. "Circuit Splitting": a sub-circuit on ``group`` is applied by viewing the state as
     (prod d_rest, prod d_group) and multiplying over the last axis; the result must equal the
     Kronecker oracle's sequential application of the same gates."""
     rng = np.random.default_rng(5)
@@ -366,7 +366,7 @@ def test_planted_mistakes_are_caught(monkeypatch, mistake):
     assert not _pins_pass(), f"planted mistake {mistake} was not caught by any pin"
 
 
-# ---------------------------------------------------------------- quantum weight remapping (Sec. III-C)
+# ---------------------------------------------------------------- quantum weight remapping (Sec. "Additional Optimizations")
 def test_remap_range_and_fixed_points():
     w = np.linspace(-6, 6, 41)
     a = oracle.remap(w)

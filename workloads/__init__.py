@@ -12,9 +12,9 @@ Gate tuples mirror the C struct ``qsim_gate``: ``(type, targets, controls, param
 * ``<= -2`` input column ``-2 - param`` of the per-sample input matrix.
 
 Qubit ``q`` is the ``q``-th most significant bit of an amplitude index (MSb-0 ordering of the
-paper's Section II-A); that convention is the simulators' business, not this module's.
+paper's Sec. "Symbols"); that convention is the simulators' business, not this module's.
 
-The five standard workloads follow the paper's hybrid-model structure (Section II-B: an
+The five standard workloads follow the paper's hybrid-model structure (Sec. "Hybrid Machine Learning": an
 embedding layer, trainable rotation layers, a measurement layer):
 
 =====  ==========================================================================
