@@ -242,6 +242,27 @@ int qsim_multi_set_test_hooks(qsim_multi_t plan, int64_t withhold_item, int64_t 
 void qsim_multi_destroy(qsim_multi_t plan);
 
 /* Free the plan and its device workspace (synchronizes the plan's last stream). NULL is a no-op. */
+/* OpenQASM 2.0 import (the paper's simulator exchanges circuits through OpenQASM, Sec. "API").
+ * `text`: a NUL-terminated program using OPENQASM 2.x; include "qelib1.inc"; qreg / creg
+ * declarations (quantum registers are concatenated in declaration order into qubits 0..n-1);
+ * barrier and measure (ignored: results are <Z_i>); and the gates h, x, id, rx(a), ry(a), rz(a),
+ * cx (CX), cz on qubits reg[i] or whole registers (broadcast). Angles are expressions of decimal
+ * literals, pi, + - * / and parentheses. Every rotation gets its own parameter index, in program
+ * order, and its angle is written to h_params[index]; no gate is input-encoded.
+ * Outputs (host): *n_gates, *n_params, *n_qubits always; h_gates (cap_gates records) and h_params
+ * (cap_params doubles) when not NULL (NULL = query the counts only).
+ * Errors: QSIM_ERR_ARG with "line L: ..." for anything outside the subset, or arrays too small. */
+int qsim_parse_qasm(const char* text, qsim_gate* h_gates, int32_t cap_gates, int32_t* n_gates, double* h_params,
+                    int32_t cap_params, int32_t* n_params, int32_t* n_qubits);
+
+/* OpenQASM 2.0 export of a gate list with concrete angles: h_params[param] for trainable rotations,
+ * h_inputs[column] (one sample's input row) for input-encoded ones (either may be NULL when unused).
+ * Writes one register q[n_qubits] and one statement per gate (angles with 17 significant digits, so
+ * qsim_parse_qasm reads back the same doubles). *needed = bytes including the NUL; buf (cap bytes)
+ * may be NULL to query. Errors: QSIM_ERR_ARG / QSIM_ERR_QUBIT / QSIM_ERR_PARAM for malformed gates. */
+int qsim_export_qasm(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, const double* h_params,
+                     const double* h_inputs, char* buf, size_t cap, size_t* needed);
+
 /* Tile-size autotuner (the fused pass's k). Plans the circuit with *opts for each candidate k in
  * {max_k - 2, max_k - 1, max_k} (max_k = 12 complex64, 11 complex128), runs one untimed forward
  * (+ backward when with_backward != 0; this also compiles the kernels) and then `reps` timed calls

@@ -317,6 +317,34 @@ def multi_autotune(circuits, batch, *, with_backward=True, reps=2, dtype="c64", 
     return [int(x) for x in ks]
 
 
+def parse_qasm(text):
+    """OpenQASM 2.0 program -> (gates, params (P,) float64, n_qubits) (``qsim_parse_qasm``)."""
+    L = _lib.lib()
+    raw = text.encode() if isinstance(text, str) else bytes(text)
+    ng, npar, nq = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _lib.check(L.qsim_parse_qasm(raw, None, 0, ctypes.byref(ng), None, 0, ctypes.byref(npar), ctypes.byref(nq)))
+    garr = (_lib.QsimGate * max(ng.value, 1))()
+    parr = (ctypes.c_double * max(npar.value, 1))()
+    _lib.check(L.qsim_parse_qasm(raw, garr, ng.value, ctypes.byref(ng), parr, npar.value, ctypes.byref(npar),
+                                 ctypes.byref(nq)))
+    gates = [(g.type, (g.targets[0], g.targets[1]), (g.controls[0], g.controls[1]), g.param)
+             for g in garr[:ng.value]]
+    return gates, np.array(parr[:npar.value], dtype=np.float64), int(nq.value)
+
+
+def export_qasm(gates, n_qubits, params=None, inputs_row=None):
+    """Gate list with concrete angles -> OpenQASM 2.0 text (``qsim_export_qasm``)."""
+    L = _lib.lib()
+    arr = gate_structs(gates)
+    p = None if params is None else (ctypes.c_double * max(len(params), 1))(*[float(v) for v in params])
+    x = None if inputs_row is None else (ctypes.c_double * max(len(inputs_row), 1))(*[float(v) for v in inputs_row])
+    need = ctypes.c_size_t()
+    _lib.check(L.qsim_export_qasm(arr, len(gates), int(n_qubits), p, x, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _lib.check(L.qsim_export_qasm(arr, len(gates), int(n_qubits), p, x, buf, need.value, ctypes.byref(need)))
+    return buf.value.decode()
+
+
 def kernel_launches():
     """Kernels launched by the library in this process so far."""
     return int(_lib.lib().qsim_kernel_launches())

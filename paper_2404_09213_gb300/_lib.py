@@ -78,6 +78,12 @@ SIGNATURES = {
     "qsim_multi_plan": (ctypes.c_int, [ctypes.POINTER(ctypes.POINTER(QsimGate)), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_void_p)]),
+    "qsim_parse_qasm": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(QsimGate), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "qsim_export_qasm": (ctypes.c_int, [ctypes.POINTER(QsimGate), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                        ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "qsim_autotune": (ctypes.c_int, [ctypes.POINTER(QsimGate), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
                                      ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),
