@@ -81,7 +81,9 @@ typedef struct {
                                 4 for complex128); fewer bits mean fewer registers and more resident warps */
   int32_t weight_remap;      /* 1: every trainable angle enters as theta' = pi * tanh(theta) (quantum weight
                                 remapping, Sec. "Additional Optimizations"), dparams are dL/dtheta through
-                                that map; inputs are used as given. 0: angles as given */
+                                that map; inputs are used as given. 2: input angles are remapped as well
+                                (dinputs likewise; single-circuit plans, used by qsim_landscape).
+                                0: angles as given */
   int32_t graph;             /* multi-circuit plans: capture each direction's launch sequence in a CUDA graph and
                                 replay it while the caller's buffers are unchanged (0 = plain launches) */
   int32_t max_regs;          /* >0: registers per thread of the pass kernels capped so that at least
@@ -262,6 +264,24 @@ int qsim_parse_qasm(const char* text, qsim_gate* h_gates, int32_t cap_gates, int
  * may be NULL to query. Errors: QSIM_ERR_ARG / QSIM_ERR_QUBIT / QSIM_ERR_PARAM for malformed gates. */
 int qsim_export_qasm(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, const double* h_params,
                      const double* h_inputs, char* buf, size_t cap, size_t* needed);
+
+/* Gradient landscape (App. "Barren Plateaus": the absolute gradient of every parameter at different
+ * rotations of that parameter, the others constant, with and without weight remapping). For every
+ * trainable parameter k and value v: dL/dtheta_k at theta = base with theta_k = values[v], where
+ * L = sum_i weights[i] <Z_i>. One batched forward + adjoint backward over n_params * n_values
+ * parameter vectors: the circuit's trainable parameters become per-sample angles (input columns),
+ * so the batch dimension carries the vectors. The circuit must not have input-encoded gates.
+ *   opts: dtype, k, ... as for qsim_plan (fused mode); weight_remap 1 sweeps the raw weights w
+ *         (angle = pi * tanh(w)) and returns dL/dw.
+ *   d_base (n_params,), d_values (n_values,): float32 (complex64) / float64 (complex128), device.
+ *   d_weights (n_qubits,) float64, device.  d_grid (n_params, n_values) float64, device, written.
+ *   d_z: NULL, or (n_params * n_values, n_qubits) float64: <Z> of every evaluated vector, row k*V+v.
+ * Allocates stream-ordered scratch for n_params * n_values states and returns after the work is
+ * complete (it synchronises `stream`). Errors: those of qsim_plan / qsim_forward / qsim_backward,
+ * QSIM_ERR_PARAM (input-encoded gates, no parameters), QSIM_ERR_OOM. */
+int qsim_landscape(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, const qsim_plan_opts* opts,
+                   const void* d_base, const void* d_values, int32_t n_values, const double* d_weights,
+                   double* d_grid, double* d_z, void* stream);
 
 /* Tile-size autotuner (the fused pass's k). Plans the circuit with *opts for each candidate k in
  * {max_k - 2, max_k - 1, max_k} (max_k = 12 complex64, 11 complex128), runs one untimed forward

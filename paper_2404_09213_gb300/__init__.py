@@ -317,6 +317,27 @@ def multi_autotune(circuits, batch, *, with_backward=True, reps=2, dtype="c64", 
     return [int(x) for x in ks]
 
 
+def landscape(gates, n_qubits, base, values, weights, *, dtype="c64", weight_remap=False, k=0, z=False,
+              stream=None):
+    """Gradient landscape (``qsim_landscape``): grid[p, v] = dL/dtheta_p at base with theta_p = values[v].
+
+    ``base`` (P,), ``values`` (V,) CUDA tensors of the plan's real dtype; ``weights`` (n,) float64 CUDA
+    tensor (L = sum_i weights[i] <Z_i>). Returns the (P, V) float64 grid, and the (P*V, n) <Z> when
+    ``z`` is true."""
+    _, cdt, rdt = _DT[dtype]
+    base = base.to(rdt).contiguous()
+    values = values.to(rdt).contiguous()
+    weights = weights.to(torch.float64).contiguous()
+    P, V = int(base.numel()), int(values.numel())
+    grid = torch.empty((P, V), dtype=torch.float64, device=base.device)
+    zt = torch.empty((P * V, int(n_qubits)), dtype=torch.float64, device=base.device) if z else None
+    o = _opts(dtype, k=k, weight_remap=1 if weight_remap else 0)
+    arr = gate_structs(gates)
+    _lib.check(_lib.lib().qsim_landscape(arr, len(gates), int(n_qubits), ctypes.byref(o), _ptr(base), _ptr(values),
+                                         V, _ptr(weights), _ptr(grid), _ptr(zt), _stream(stream)))
+    return (grid, zt) if z else grid
+
+
 def parse_qasm(text):
     """OpenQASM 2.0 program -> (gates, params (P,) float64, n_qubits) (``qsim_parse_qasm``)."""
     L = _lib.lib()

@@ -84,6 +84,9 @@ SIGNATURES = {
     "qsim_export_qasm": (ctypes.c_int, [ctypes.POINTER(QsimGate), ctypes.c_int32, ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                         ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "qsim_landscape": (ctypes.c_int, [ctypes.POINTER(QsimGate), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(QsimPlanOpts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "qsim_autotune": (ctypes.c_int, [ctypes.POINTER(QsimGate), ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(QsimPlanOpts),
                                      ctypes.POINTER(ctypes.c_float), ctypes.c_void_p]),

@@ -386,10 +386,10 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   }
   p->opts = o;
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
-      o.sample_block < 0 || (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs < 0 ||
+      o.sample_block < 0 || o.weight_remap < 0 || o.weight_remap > 2 || o.max_regs < 0 ||
       (o.max_regs > 0 && o.max_regs < 32) || (o.rotate_low_bits != 0 && o.rotate_low_bits != 1)) {
     delete p;
-    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0 or 1, "
+    return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0..2, "
                               "max_regs 0 or >= 32, rotate_low_bits 0 or 1");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
@@ -636,6 +636,7 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
   ga.dparams = d_dparams;
   ga.dinputs = d_dinputs;
   ga.params = p->params;
+  ga.inputs = p->inputs;
   ga.weight_remap = p->opts.weight_remap;
   ga.dtype = s.dtype;
   e = launch_grad_reduce(ga, st);

@@ -24,7 +24,7 @@ struct CoefArgs {
   const void* params;
   const void* inputs;
   int n_inputs, B, P;
-  int weight_remap;             // 1: trainable angles enter as pi * tanh(param)
+  int weight_remap;             // 1: trainable angles enter as pi * tanh(param); 2: input angles as well
   void* coef;                   // [G * B]
   uint8_t* form;                // [G * B]
   void* cfp_f;                  // packed forward op coefficients: pass p, sample b, op i at
@@ -65,6 +65,7 @@ struct GradReduceArgs {
   double* dparams;              // may be null
   double* dinputs;              // may be null
   const void* params;           // weight_remap: the raw params (float32 / float64 by dtype) for the chain rule
+  const void* inputs;           // weight_remap == 2: the raw inputs (B x n_inputs) likewise
   int weight_remap, dtype;
 };
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st);
@@ -104,6 +105,13 @@ struct GradMultiArgs {
   int weight_remap, dtype;
 };
 cudaError_t launch_grad_reduce_multi(const GradMultiArgs& a, cudaStream_t st);
+
+// ---- gradient landscape (one batched evaluation of n_params x n_values parameter vectors)
+// rows[k * V + v][j] = (j == k ? values[v] : base[j]); gout[b][i] = weights[i] for every row b;
+// grid[k][v] = dinputs[(k * V + v) * P + k]
+cudaError_t launch_landscape_inputs(const void* base, const void* values, int P, int V, int dtype, void* rows,
+                                    const double* weights, int n, double* gout, cudaStream_t st);
+cudaError_t launch_landscape_gather(const double* dinputs, int P, int V, double* grid, cudaStream_t st);
 
 // ---- per-gate (plain) path
 struct PerGateArgs {

@@ -1,6 +1,7 @@
 // Angle -> coefficient formation, and the deterministic FP64 reductions (<Z>, gradients).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "launch.hpp"
@@ -56,7 +57,7 @@ __global__ void coef_kernel(CoefArgs a) {
     if (ty <= QSIM_RZ) {
       const int pr = a.gate_param[g];
       const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
-                                : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
+                                : weight(inputs[(int64_t)b * n_inputs + (-2 - pr)], a.weight_remap == 2);
       double s, c;
       sincos(0.5 * th, &s, &c);
       const int64_t gi = (int64_t)g * a.B + b;
@@ -94,7 +95,7 @@ __global__ void coef_kernel(CoefArgs a) {
       a.gm[gi] = bs * bs;
       const int pr = a.gate_param[g];
       const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
-                                : (double)inputs[(int64_t)b * n_inputs + (-2 - pr)];
+                                : weight(inputs[(int64_t)b * n_inputs + (-2 - pr)], a.weight_remap == 2);
       double s, c;
       sincos(0.5 * th, &s, &c);
       bs *= (a.form[gi] == 0) ? c : -s;
@@ -189,7 +190,7 @@ __global__ void grad_scatter_kernel(GradReduceArgs a) {
     const int b = (int)(r / a.n_inputs), c = (int)(r - (r / a.n_inputs) * a.n_inputs);
     double acc = 0.0;
     for (int o = a.i_ptr[c]; o < a.i_ptr[c + 1]; o++) acc += a.G[(int64_t)a.i_occ[o] * a.B + b];
-    a.dinputs[r] = acc;
+    a.dinputs[r] = a.weight_remap == 2 ? acc * remap_slope(a.inputs, r, a.dtype) : acc;
   }
 }
 
@@ -420,4 +421,49 @@ cudaError_t launch_expval_z(const void* states, int n, int B, int dtype, double*
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ gradient landscape
+template <typename T>
+__global__ void landscape_rows_kernel(const T* base, const T* values, int P, int V, T* rows, const double* w, int n,
+                                      double* gout) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t B = (int64_t)P * V;
+  if (id < B * P) {
+    const int64_t b = id / P;
+    const int j = (int)(id - b * P), k = (int)(b / V), v = (int)(b - (int64_t)k * V);
+    rows[id] = j == k ? values[v] : base[j];
+  }
+  if (id < B * n) gout[id] = w[id % n];
+}
+
+__global__ void landscape_gather_kernel(const double* dinputs, int P, int V, double* grid) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)P * V) return;
+  const int k = (int)(id / V);
+  grid[id] = dinputs[id * P + k];   // sample id = k * V + v varied parameter k
+}
+
+cudaError_t launch_landscape_inputs(const void* base, const void* values, int P, int V, int dtype, void* rows,
+                                    const double* weights, int n, double* gout, cudaStream_t st) {
+  const int64_t B = (int64_t)P * V, total = std::max<int64_t>(B * P, B * n);
+  if (total == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (dtype == QSIM_C128)
+    landscape_rows_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(base),
+        static_cast<const double*>(values), P, V, static_cast<double*>(rows), weights, n, gout);
+  else
+    landscape_rows_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(base),
+        static_cast<const float*>(values), P, V, static_cast<float*>(rows), weights, n, gout);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_landscape_gather(const double* dinputs, int P, int V, double* grid, cudaStream_t st) {
+  const int64_t total = (int64_t)P * V;
+  if (total == 0) return cudaSuccess;
+  landscape_gather_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dinputs, P, V, grid);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
 }  // namespace qsim
+

@@ -104,6 +104,37 @@ def hea_cz_ansatz(n: int, depth: int, encode: bool = True):
     return gates
 
 
+def sel_ansatz(n: int, layers: int, reupload: bool = False, encode: bool = True):
+    """Strongly Entangling Layers (the circuit family of the paper's App. "Barren Plateaus").
+
+    Layer l: Rot(phi, theta, omega) = RZ(omega) RY(theta) RZ(phi) on every qubit q (applied as RZ(phi),
+    then RY(theta), then RZ(omega); parameters 3(l n + q) + 0, 1, 2), then CNOT(q, (q + r) mod n) for
+    q = 0..n-1 with range r = (l mod (n - 1)) + 1. ``encode``: RX(x_q) angle encoding of n inputs
+    before the first layer; ``reupload``: before every layer (data re-uploading, the embedding
+    variant named in the paper's Sec. "Hybrid Machine Learning").
+    """
+    gates = []
+    for l in range(layers):
+        if encode and (l == 0 or reupload):
+            gates += [gate(RX, (q,), param=input_param(q)) for q in range(n)]
+        for q in range(n):
+            base = 3 * (l * n + q)
+            gates += [gate(RZ, (q,), param=base), gate(RY, (q,), param=base + 1), gate(RZ, (q,), param=base + 2)]
+        if n >= 2:
+            r = (l % (n - 1)) + 1
+            gates += [gate(CNOT, ((q + r) % n,), (q,)) for q in range(n)]
+    return gates
+
+
+def sel_workload(name: str, n: int, batch: int, layers: int, dtype: str, seed: int, reupload: bool = True,
+                 encode: bool = True) -> Workload:
+    gates = sel_ansatz(n, layers, reupload, encode)
+    rng = SplitMix64(seed)
+    inputs, params, grad_out = _draw(rng, batch, n if encode else 0, count_params(gates), n)
+    return Workload(name, n, batch, dtype, gates, params, inputs, grad_out, True,
+                    {"layers": layers, "seed": seed, "reupload": reupload})
+
+
 def count_params(gates) -> int:
     return 1 + max([g[3] for g in gates if g[3] >= 0], default=-1)
 
