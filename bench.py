@@ -42,10 +42,12 @@ def parse():
     ap.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
     ap.add_argument("--k", type=int, default=0)
     ap.add_argument("--batch", type=int, default=64, help="samples (64 = the workload; smaller for ncu captures)")
-    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c3", choices=["c2", "c3", "c4", "c5", "sel", "landscape"],
                     help="c3 (default): 20 qubits x 64, fwd+bwd; c2: 12 qubits x 1024 forward; "
                          "c4: 256 circuits (8..22 qubits) x 4 in one persistent launch, fwd+bwd; "
-                         "c5: 30 qubits x 1, fwd + checkpointed bwd")
+                         "c5: 30 qubits x 1, fwd + checkpointed bwd; sel: 20 qubits x 64, Strongly Entangling "
+                         "Layers with data re-uploading, fwd+bwd; landscape: every parameter of a 5-qubit SEL "
+                         "circuit swept over 256 values (qsim_landscape)")
     ap.add_argument("--contiguous-bits", type=int, default=0)
     ap.add_argument("--checkpoint-passes", type=int, default=1,
                     help="store the state every this many forward passes (1: every pass, so backward passes "
@@ -399,6 +401,45 @@ def run_other(args, world, rank, local):
         tot = sum(algorithmic_bytes(desc, B, wl.n, "fwd")) + sum(algorithmic_bytes(desc, B, wl.n, "bwd", 8))
         name = "C5: 30 qubits, batch 1, c64, RX encoding + 8 x (RY,RZ + CNOT ring), fwd + checkpointed bwd"
         extra = {"passes": P, "checkpoint_passes": 8}
+    elif args.workload == "sel":
+        wl = W.sel_workload("SEL", 20, 64, 5, "c64", seed=W.SEED_BASE + 6, reupload=True)
+        B = wl.batch
+        k, _ = q.autotune(wl.gates, wl.n, B, reps=2, checkpoint_passes=1)
+        plan = q.Plan(wl.gates, wl.n, k=k, checkpoint_passes=1)
+        p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
+        x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
+        g = torch.tensor(wl.grad_out, dtype=torch.float64, device=dev)
+        states = torch.empty((B, 1 << wl.n), dtype=torch.complex64, device=dev)
+        z = torch.empty((B, wl.n), dtype=torch.float64, device=dev)
+
+        def step():
+            plan.forward(p, x, states=states, z=z, stream=stream)
+            plan.backward(g, stream=stream)
+        samples = B
+        desc = plan.describe()
+        tot = sum(algorithmic_bytes(desc, B, wl.n, "fwd")) + sum(algorithmic_bytes(desc, B, wl.n, "bwd", 1))
+        name = ("SEL: 20 qubits, batch 64, c64, 5 Strongly Entangling Layers (Rot + range-r CNOTs) with data "
+                "re-uploading before every layer, fwd+bwd")
+        extra = {"passes": len(desc["passes"]), "k": k, "gates": len(wl.gates), "params": wl.n_params,
+                 "checkpoint_passes": 1}
+    elif args.workload == "landscape":
+        n, layers, V = 5, 5, 256
+        gates = W.sel_ansatz(n, layers, encode=False)
+        P = W.count_params(gates)
+        rng = W.SplitMix64(W.SEED_BASE + 7)
+        base = torch.tensor(rng.uniforms(P) * 2 * math.pi - math.pi, dtype=torch.float32, device=dev)
+        values = torch.linspace(-math.pi, math.pi, V, device=dev)
+        weights = torch.ones(n, dtype=torch.float64, device=dev)
+
+        def step():
+            q.landscape(gates, n, base, values, weights, weight_remap=True, stream=stream)
+        samples = P * V
+        B = P * V
+        tot = B * (1 << n) * (8 + 24)   # one pass each way (whole 5-qubit state in one tile)
+        name = (f"gradient landscape: {P} parameters of a 5-qubit, {layers}-layer SEL circuit, each swept over "
+                f"{V} values with the others fixed, weight remapping (one qsim_landscape call per step, plan "
+                "and kernel loading included)")
+        extra = {"params": P, "values": V, "gradient_vectors_per_step": P * V}
     else:
         wl = W.config(2)
         B = wl.batch
@@ -434,8 +475,9 @@ def run_other(args, world, rank, local):
     clocks = clk.stop()
     launches = q.kernel_launches() - launches0
     gbs = tot * args.steps / (ms / 1e3) / 1e9
-    metric = "fwd+adjoint-bwd samples/s" if args.workload != "c2" else "forward samples/s"
-    out = {"metric": metric, "value": samples * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+    metric = {"c2": "forward samples/s", "landscape": "gradient vectors/s"}.get(args.workload, "fwd+adjoint-bwd samples/s")
+    unit = "gradient vectors/s" if args.workload == "landscape" else UNIT
+    out = {"metric": metric, "value": samples * args.steps / (ms / 1e3), "unit": unit, "n_gpus": 1,
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 state, fp64 reductions)",
            "data": "synthetic (seeded splitmix64)", "config": dict(workload=name, **extra),
