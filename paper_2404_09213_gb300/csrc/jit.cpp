@@ -228,6 +228,14 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       if ((i >> r) & 1) e |= 1u << ph.rbit[r];
     return e;
   };
+  // shared-memory element of a phase's register pair i in layout Lx = (thread part) ^ (constant part);
+  // when the two parts cannot share a bit the XOR is an addition (the constant folds into the offset)
+  auto disjoint = [&](const DevLayout& Lx, const DevPhase& ph) {
+    uint32_t mt = 0, mr = 0;
+    for (int jb = 0; jb < ph.n_tbits; jb++) mt |= lay_eval(Lx, K, 1u << ph.tbit[jb]);
+    for (int r = 1; r < R; r++) mr |= lay_eval(Lx, K, 1u << ph.rbit[r]);
+    return (mt & mr) == 0;
+  };
   // <Z> bit map of the phase that stores to global memory (forward: the last phase)
   if (!bwd) {
     const DevPhase& lp = s.phases[d.phase0 + P - 1];
@@ -343,14 +351,16 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         o << "      }\n";
       }
     } else {
-      o << "      const qj::u32 si = L" << lin << "(tb)" << (bwd ? std::string() : fold_smem(Li)) << ";\n";
+      const std::string fl = bwd ? std::string() : fold_smem(Li);
+      const char* ad = fl.empty() && disjoint(Li, Ph) ? "true" : "false";
+      o << "      const qj::u32 si = L" << lin << "(tb)" << fl << ";\n";
       for (int i = 0; i < N; i += 2) {
         const uint32_t cc = lay_eval(Li, K, dep_of(Ph, i));
         if (!bwd) {
-          o << "      qj::ldp(c.tile, si ^ " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+          o << "      qj::ldpx<" << ad << ">(c.tile, si, " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
         } else {
-          o << "      qj::ldp(c.tile, si ^ " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
-          o << "      qj::ldp(c.tile2, si ^ " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+          o << "      qj::ldpx<" << ad << ">(c.tile, si, " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
+          o << "      qj::ldpx<" << ad << ">(c.tile2, si, " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
         }
       }
     }
@@ -460,15 +470,16 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         o << "      }\n";
       }
     } else {
-      o << "      __syncthreads();\n      const qj::u32 so = L" << lout << "(tb)" << (bwd ? fold_smem(Lo) : std::string())
-        << ";\n";
+      const std::string fs = bwd ? fold_smem(Lo) : std::string();
+      const char* ad = fs.empty() && disjoint(Lo, Ph) ? "true" : "false";
+      o << "      __syncthreads();\n      const qj::u32 so = L" << lout << "(tb)" << fs << ";\n";
       for (int i = 0; i < N; i += 2) {
         const uint32_t cc = lay_eval(Lo, K, dep_of(Ph, i));
         if (!bwd) {
-          o << "      qj::stp(c.tile, so ^ " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+          o << "      qj::stpx<" << ad << ">(c.tile, so, " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
         } else {
-          o << "      qj::stp(c.tile, so ^ " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
-          o << "      qj::stp(c.tile2, so ^ " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
+          o << "      qj::stpx<" << ad << ">(c.tile, so, " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
+          o << "      qj::stpx<" << ad << ">(c.tile2, so, " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
         }
       }
       o << "      __syncthreads();\n";

@@ -305,6 +305,29 @@ __device__ __forceinline__ void stp(void* tile, u32 w, double r0, double i0, dou
   reinterpret_cast<double2*>(tile)[w ^ 1u] = make_double2(r1, i1);
 }
 
+// Pair access at element s ^ c, s the thread's part and c a compile-time constant (both with bit 0
+// clear). ADD: s and c have no bit in common, so s ^ c == s + c and the constant becomes the
+// instruction's address offset.
+template <bool ADD, typename T>
+__device__ __forceinline__ void ldpx(const void* tile, u32 s, u32 c, T& r0, T& i0, T& r1, T& i1) {
+  if constexpr (sizeof(T) == 4) {
+    const u32 q = ADD ? (s >> 1) + (c >> 1) : ((s ^ c) >> 1);
+    const float4 v = reinterpret_cast<const float4*>(tile)[q];
+    r0 = v.x; i0 = v.y; r1 = v.z; i1 = v.w;
+  } else {
+    ldp(tile, ADD ? s + c : s ^ c, r0, i0, r1, i1);
+  }
+}
+template <bool ADD, typename T>
+__device__ __forceinline__ void stpx(void* tile, u32 s, u32 c, T r0, T i0, T r1, T i1) {
+  if constexpr (sizeof(T) == 4) {
+    const u32 q = ADD ? (s >> 1) + (c >> 1) : ((s ^ c) >> 1);
+    reinterpret_cast<float4*>(tile)[q] = make_float4(r0, i0, r1, i1);
+  } else {
+    stp(tile, ADD ? s + c : s ^ c, r0, i0, r1, i1);
+  }
+}
+
 // ---------------------------------------------------------------- direct global <-> register I/O
 // The first register phase loads its amplitudes straight from global memory and the last one stores
 // them straight back; the planner keeps tile bits 1..3 as thread bits there, so lanes 0..7 of a warp
