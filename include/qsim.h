@@ -134,18 +134,21 @@ int qsim_plan_kernel_source(qsim_plan_t plan, char* h_buf, size_t cap, size_t* n
 int qsim_plan_compile_kernels(qsim_plan_t plan);
 
 /* Physical amplitude indices (within one sample) of the 2^k elements of tile `tile` of pass
- * `pass`, in tile order (tile bit j <-> physical bit L_j): the gather/scatter map of that pass.
- * h_out must hold 2^k int64 values. Host only. */
+ * `pass`, in tile order, in the qubit layout that pass reads (tile bit j <-> physical bit L_j of
+ * that layout; pass 0 reads the canonical layout, and a pass writes the layout the next one reads):
+ * the gather map of that pass. h_out must hold 2^k int64 values. Host only. */
 int qsim_tile_index_map(qsim_plan_t plan, int32_t pass, int64_t tile, int64_t* h_out);
 
 /* Forward pass.
  *   d_params:  (n_params,) float32/float64 trainable angles (may be NULL if n_params == 0)
  *   d_inputs:  (batch, n_inputs) float32/float64 encoded inputs (NULL if n_inputs == 0)
  *   d_init:    (batch, 2^n) complex initial states, or NULL for |0...0> in every sample
- *   d_states:  (batch, 2^n) complex output: the final states (may equal d_init)
+ *   d_states:  (batch, 2^n) complex output: the final states, canonical qubit order (may equal d_init)
  *   d_z:       (batch, n) float64 output <Z_i>_b
- * The plan remembers d_params, d_inputs and d_states for the backward: they must stay unchanged
- * until qsim_backward has been enqueued. Workspace is (re)allocated on `stream` when batch grows. */
+ * Intermediate states live in the plan's workspace (and checkpoints); only the last pass writes
+ * d_states. The plan remembers d_params, d_inputs and d_states for the backward: they must stay
+ * unchanged until qsim_backward has been enqueued. Workspace is (re)allocated on `stream` when the
+ * batch size changes. */
 int qsim_forward(qsim_plan_t plan, const void* d_params, const void* d_inputs, int32_t batch,
                  const void* d_init, void* d_states, double* d_z, void* stream);
 
@@ -157,7 +160,9 @@ int qsim_forward(qsim_plan_t plan, const void* d_params, const void* d_inputs, i
 int qsim_backward(qsim_plan_t plan, const double* d_grad_out, double* d_dparams, double* d_dinputs,
                   void* stream);
 
-/* Synchronize `plan`'s last stream and return the device-side status (QSIM_OK or QSIM_ERR_TIMEOUT). */
+/* Synchronize `plan`'s last stream and return its status: QSIM_OK, or QSIM_ERR_CUDA when the stream
+ * reports a CUDA error (single-circuit kernels have no device-side waits; the bounded waits of the
+ * multi-circuit queue report QSIM_ERR_TIMEOUT through qsim_multi_sync_status). */
 int qsim_sync_status(qsim_plan_t plan);
 
 /* Standalone measurement layer: <Z_i>_b of arbitrary states (the same reduction the fused path
