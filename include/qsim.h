@@ -223,7 +223,9 @@ typedef struct qsim_multi_s* qsim_multi_t;
 int qsim_multi_plan(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
                     int32_t n_circuits, const qsim_plan_opts* opts, const int32_t* h_k, qsim_multi_t* out);
 /*   h_k: NULL (every circuit uses opts->k), or one k per circuit (host, n_circuits entries, each in
- *   [1, 12] for complex64 / [1, 11] for complex128), e.g. from qsim_multi_autotune. */
+ *   [1, 11] for complex64 / [1, 10] for complex128: one below the single-circuit maximum, so that the
+ *   queue kernels, which hold every pass structure, stay small enough for four CTAs per SM), e.g. from
+ *   qsim_multi_autotune. opts->k is clamped to the same maximum. */
 
 /* Element offsets of every circuit's block for batch size `batch`; each array (n_circuits + 1
  * entries, the last = total) may be NULL. */
@@ -241,6 +243,11 @@ int qsim_multi_sync_status(qsim_multi_t plan);
 /* Queue statistics: circuits, work items per direction, distinct specialised pass codes per direction. */
 int qsim_multi_info(qsim_multi_t plan, int32_t* n_circuits, int64_t* n_items_fwd, int64_t* n_items_bwd,
                     int32_t* n_kernels_fwd, int32_t* n_kernels_bwd);
+
+/* Resources of the two persistent queue kernels (index 0 forward, 1 backward), known after the
+ * first forward: resident CTAs per SM, registers per thread, dynamic shared memory per CTA. One
+ * queue kernel holds every pass structure of its direction, so these are the maxima over them. */
+int qsim_multi_kernel_info(qsim_multi_t plan, int32_t* h_ctas_per_sm, int32_t* h_regs, int64_t* h_smem);
 
 /* Test hook for the bounded waits: the completion of queue item `withhold_item` (-1 = none) is never
  * signalled, and waits give up after timeout_ns (<= 0: the default of 4 s). */
@@ -302,8 +309,9 @@ int qsim_landscape(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, 
 int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, int32_t batch,
                   int32_t with_backward, int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream);
 
-/* Per-circuit k for qsim_multi_plan: qsim_autotune on the first circuit of every distinct qubit
- * count (same batch, opts as the base), the result copied to every circuit of that count.
+/* Per-circuit k for qsim_multi_plan: the qsim_autotune measurement (candidates up to the
+ * multi-circuit maximum, max_k - 1) on the first circuit of every distinct qubit count (same batch,
+ * opts as the base), the result copied to every circuit of that count.
  * h_k: n_circuits int32 (host, written). */
 int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
                         int32_t n_circuits, int32_t batch, int32_t with_backward, int32_t reps,

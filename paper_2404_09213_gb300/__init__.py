@@ -247,6 +247,12 @@ class MultiPlan:
         _lib.check(_lib.lib().qsim_multi_offsets(self._h, batch, *ptrs))
         return dict(zip(("params", "inputs", "states", "z"), arrs))
 
+    def kernel_info(self):
+        """Queue kernels' resident CTAs per SM, registers per thread, shared memory (fwd, bwd)."""
+        c = (ctypes.c_int32 * 2)(); r = (ctypes.c_int32 * 2)(); m = (ctypes.c_int64 * 2)()
+        _lib.check(_lib.lib().qsim_multi_kernel_info(self._h, c, r, m))
+        return {"ctas_per_sm": list(c), "regs": list(r), "smem": list(m)}
+
     def info(self):
         vals = [ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()]
         _lib.check(_lib.lib().qsim_multi_info(self._h, *[ctypes.byref(v) for v in vals]))

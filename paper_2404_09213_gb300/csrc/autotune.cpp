@@ -93,16 +93,12 @@ int time_candidate(const qsim_gate* g, int32_t ng, int32_t n, int32_t batch, int
   return rc;
 }
 
-}  // namespace
-
-extern "C" {
-
-int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, int32_t batch, int32_t with_backward,
-                  int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream) {
+// Candidates kmax - 2 .. kmax; n_qubits <= kmax runs in one pass at k = n_qubits.
+int autotune_upto(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, int32_t batch, int32_t with_backward,
+                  int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream, int kmax) {
   if (!opts || batch < 1 || reps < 1) return fail(QSIM_ERR_ARG, "autotune: opts must be set, batch >= 1, reps >= 1");
   if (opts->mode != QSIM_FUSED) return fail(QSIM_ERR_ARG, "autotune: fused mode only");
   if (opts->dtype != QSIM_C64 && opts->dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "autotune: bad dtype");
-  const int kmax = qsim::max_k_for(opts->dtype);
   if (h_ms)
     for (int i = 0; i < 3; i++) h_ms[i] = -1.f;
   if (n_qubits <= kmax) {   // one pass holds the whole state
@@ -128,6 +124,17 @@ int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, i
   return QSIM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, int32_t batch, int32_t with_backward,
+                  int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream) {
+  if (!opts) return fail(QSIM_ERR_ARG, "autotune: opts must be set");
+  return autotune_upto(h_gates, n_gates, n_qubits, batch, with_backward, reps, opts, h_ms, stream,
+                       qsim::max_k_for(opts->dtype));
+}
+
 int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
                         int32_t n_circuits, int32_t batch, int32_t with_backward, int32_t reps,
                         const qsim_plan_opts* opts, int32_t* h_k, void* stream) {
@@ -144,8 +151,9 @@ int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n
   for (auto& kv : rep_of) {
     qsim_plan_opts o = base;
     const int c = kv.second;
-    const int rc = qsim_autotune(h_gate_lists[c], h_n_gates[c], h_n_qubits[c], batch, with_backward, reps, &o,
-                                 nullptr, stream);
+    // multi-circuit plans take tiles of at most max_k - 1 qubits (see multi.cpp)
+    const int rc = autotune_upto(h_gate_lists[c], h_n_gates[c], h_n_qubits[c], batch, with_backward, reps, &o,
+                                 nullptr, stream, qsim::max_k_for(o.dtype) - 1);
     if (rc) return rc;
     k_of[kv.first] = o.k;
   }

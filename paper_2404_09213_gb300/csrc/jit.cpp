@@ -206,9 +206,10 @@ static int grad_level(const DevPass& d, int dtype, int cta) {
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const int lt = d.k - d.R;                      // log2 threads per tile
   const size_t groups = cta > 0 ? std::max<size_t>(1, (size_t)cta >> lt) : 1;
+  const size_t budget = cta > 0 ? 16 * 1024 : 32 * 1024;   // queue kernels: keep CTAs small (see multi.cpp)
   const int cap = std::min(lt, 5);
   for (int gs = 0; gs < cap; gs++)
-    if (ng * ((size_t)1 << (lt - gs)) * sc * groups <= 32 * 1024) return gs;
+    if (ng * ((size_t)1 << (lt - gs)) * sc * groups <= budget) return gs;
   return cap;
 }
 
@@ -565,8 +566,11 @@ static int nvrtc_compile_unit(const std::string& src, std::string& cubin, std::s
     err = "nvrtcCreateProgram failed";
     return QSIM_ERR_UNSUPPORTED;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--fmad=true", "-rdc=true"};
-  const int rc = nv.compile(prog, rdc ? 5 : 4, opts);
+  // relocatable pass functions are linked into one queue kernel whose register count is the maximum
+  // over them: cap them so that four 128-thread CTAs fit on an SM
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "--fmad=true", "-rdc=true",
+                        "--maxrregcount=128"};
+  const int rc = nv.compile(prog, rdc ? 6 : 4, opts);
   size_t ls = 0;
   nv.log_size(prog, &ls);
   std::string log(ls, '\0');
@@ -749,7 +753,7 @@ int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int c
   }
   int maj = 0, min = 0;
   if (nv.h) nv.version(&maj, &min);
-  const std::string tag = "_rdc_sm103a_" + std::to_string(maj) + "." + std::to_string(min) + "_" +
+  const std::string tag = "_rdc_r128_sm103a_" + std::to_string(maj) + "." + std::to_string(min) + "_" +
                           hex64(fnv1a(kJitDeviceSource)).substr(0, 8);
   const std::string dir = cache_dir();
   std::map<std::string, std::string> units[2];   // name -> source (per direction)
@@ -891,6 +895,9 @@ int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int c
     cudaGetDevice(&devi);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devi);
     jk.max_blocks = (int64_t)per_sm * sms;   // persistent grid: every block resident at once
+    jk.per_sm = per_sm;
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k)) == cudaSuccess) jk.regs = fa.numRegs;
   }
   jm.n_kinds[0] = (int)kinds[0].size();
   jm.n_kinds[1] = (int)kinds[1].size();

@@ -55,6 +55,7 @@ struct JitKernel {
   size_t smem = 0;
   int nthr = 0;
   int64_t max_blocks = 0;   // resident blocks (persistent queue kernels only)
+  int per_sm = 0, regs = 0; // resident blocks per SM and registers per thread (queue kernels only)
 };
 
 struct JitPlan {

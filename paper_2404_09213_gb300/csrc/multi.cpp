@@ -24,7 +24,12 @@ namespace {
 thread_local std::string m_err;
 int mfail(int code, const std::string& msg);
 
-constexpr int kCtaF = 128, kCtaB = 256;
+// Queue kernel CTAs of 128 threads in both directions; with tiles of at most max_k - 1 qubits
+// (2^(k - R) <= 128 threads per tile) and at most 128 registers per thread (link option) four
+// CTAs fit on an SM. Every pass structure of a direction lives in one kernel, so its registers and
+// shared memory are the maxima over them: larger tiles would cost every circuit occupancy.
+constexpr int kCtaF = 128, kCtaB = 128;
+static int multi_max_k(int dtype) { return max_k_for(dtype) - 1; }
 
 struct QItem {   // mirrors qj::Item
   int32_t kind, arg;
@@ -392,7 +397,7 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
       (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs != 0)
     return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], weight_remap 0 or 1, max_regs 0 "
                                "(multi-circuit kernels size their own CTAs)");
-  if (o.k == 0 || o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
+  if (o.k == 0 || o.k > multi_max_k(o.dtype)) o.k = multi_max_k(o.dtype);
   auto* m = new qsim_multi_s();
   m->opts = o;
   m->C = n_circ;
@@ -420,9 +425,10 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
       const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
       qsim_plan_opts oc = o;
       if (h_k) {
-        if (h_k[c] < 1 || h_k[c] > max_k_for(o.dtype)) {
+        if (h_k[c] < 1 || h_k[c] > multi_max_k(o.dtype)) {
           delete m;
-          return mfail(QSIM_ERR_ARG, "circuit " + std::to_string(c) + ": per-circuit k outside [1, max k]");
+          return mfail(QSIM_ERR_ARG, "circuit " + std::to_string(c) + ": per-circuit k outside [1, " +
+                                         std::to_string(multi_max_k(o.dtype)) + "]");
         }
         oc.k = h_k[c];
       }
@@ -688,6 +694,18 @@ int qsim_multi_info(qsim_multi_t m, int32_t* n_circuits, int64_t* n_items_fwd, i
   if (n_items_bwd) *n_items_bwd = m->n_items_b;
   if (n_kernels_fwd) *n_kernels_fwd = m->jm.n_kinds[0];
   if (n_kernels_bwd) *n_kernels_bwd = m->jm.n_kinds[1];
+  return QSIM_OK;
+}
+
+int qsim_multi_kernel_info(qsim_multi_t m, int32_t* ctas_per_sm, int32_t* regs, int64_t* smem) {
+  if (!m) return mfail(QSIM_ERR_ARG, "plan is NULL");
+  if (!m->uploaded) return mfail(QSIM_ERR_NO_FORWARD, "the queue kernels are built by the first forward");
+  const JitKernel* k[2] = {&m->jm.fwd, &m->jm.bwd};
+  for (int d = 0; d < 2; d++) {
+    if (ctas_per_sm) ctas_per_sm[d] = k[d]->per_sm;
+    if (regs) regs[d] = k[d]->regs;
+    if (smem) smem[d] = (int64_t)k[d]->smem;
+  }
   return QSIM_OK;
 }
 
