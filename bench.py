@@ -330,10 +330,12 @@ def run_ours(args, world, rank, local):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 state, fp64 reductions)",
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded splitmix64 angles and loss weights)",
            "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": B, "gates": len(wl.gates),
                       "params": wl.n_params, "mode": args.mode, "k": desc["k"], "autotune": autotune,
+                      "precision": "complex64 state, FP32 arithmetic; <Z> and gradient sums FP32 within a tile, "
+                                   "FP64 across tiles and samples",
                       "checkpoint_passes": ckpt, "checkpoints": plan.info()["n_checkpoints"],
                       "workspace_bytes": plan.info()["workspace_bytes"],
                       "contiguous_bits": desc["c"],
@@ -479,8 +481,9 @@ def run_other(args, world, rank, local):
     unit = "gradient vectors/s" if args.workload == "landscape" else UNIT
     out = {"metric": metric, "value": samples * args.steps / (ms / 1e3), "unit": unit, "n_gpus": 1,
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32 state, fp64 reductions)",
-           "data": "synthetic (seeded splitmix64)", "config": dict(workload=name, **extra),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded splitmix64)",
+           "config": dict(workload=name, precision="complex64 state, FP32 arithmetic, FP64 sums across tiles", **extra),
            "roofline": {"bound": "hbm", "kernel": "whole step (all pass kernels)", "achieved": gbs, "peak": peak,
                         "unit": "GB/s", "frac": gbs / peak, "traffic": None,
                         "algorithmic_bytes_per_step": tot, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
