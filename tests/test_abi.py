@@ -95,3 +95,28 @@ def test_specialised_kernels_compile_on_host(q, gates, n, kw):
     src = p.kernel_source()
     assert src.count('extern "C" __global__') >= 2
     p.compile_kernels()
+
+
+def test_landscape_and_autotune_reject_bad_arguments_on_the_host(q):
+    # argument checks run before any device work, so they can be exercised without a GPU
+    import ctypes
+    from paper_2404_09213_gb300 import _lib
+    L = _lib.lib()
+    gates = W.sel_ansatz(3, 1, encode=True)                      # has input-encoded gates
+    arr = q.gate_structs(gates)
+    dummy = ctypes.c_void_p(16)
+    opts = _lib.QsimPlanOpts()
+    L.qsim_default_opts(ctypes.byref(opts))
+    rc = L.qsim_landscape(arr, len(gates), 3, ctypes.byref(opts), dummy, dummy, 4, dummy, dummy, None, None)
+    assert rc == -3 and b"input-encoded" in L.qsim_last_error()
+    rc = L.qsim_landscape(arr, len(gates), 3, ctypes.byref(opts), dummy, dummy, 0, dummy, dummy, None, None)
+    assert rc == -1
+    opts.mode = 1
+    rc = L.qsim_autotune(arr, len(gates), 3, 4, 1, 1, ctypes.byref(opts), None, None)
+    assert rc == -1 and b"fused" in L.qsim_last_error()
+    opts.mode = 0
+    rc = L.qsim_autotune(arr, len(gates), 3, 0, 1, 1, ctypes.byref(opts), None, None)
+    assert rc == -1
+    k = (ctypes.c_int32 * 1)()
+    rc = L.qsim_multi_autotune(None, None, None, 0, 4, 1, 1, None, k, None)
+    assert rc == -1

@@ -120,3 +120,29 @@ def test_export_errors(q):
         q.export_qasm([g(W.CNOT, 0, 0)], 2)                 # control == target
     with pytest.raises(q.QsimError):
         q.export_qasm([g(W.H, 3)], 2)                       # target out of range
+
+
+def test_random_circuits_round_trip(q):
+    # every gate kind, random qubits, angles of very different magnitudes, empty circuits: the parsed
+    # list is the exported one and the angles come back as the same doubles
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        n = int(rng.integers(1, 9))
+        gates, angles = [], []
+        for _ in range(int(rng.integers(0, 40))):
+            kind = int(rng.integers(0, 7))
+            t = int(rng.integers(0, n))
+            if kind in (W.CNOT, W.CZ):
+                if n < 2:
+                    continue
+                c = int((t + rng.integers(1, n)) % n)
+                gates.append(g(kind, t, c))
+            elif kind in (W.RX, W.RY, W.RZ):
+                gates.append(g(kind, t, p=len(angles)))
+                angles.append(float(rng.choice([rng.normal(), rng.uniform(-1e6, 1e6), rng.uniform(-1e-9, 1e-9)])))
+            else:
+                gates.append(g(kind, t))
+        text = q.export_qasm(gates, n, angles)
+        g2, p2, n2 = q.parse_qasm(text)
+        assert n2 == n and g2 == gates, trial
+        assert p2.tobytes() == np.array(angles, dtype=np.float64).tobytes(), trial
