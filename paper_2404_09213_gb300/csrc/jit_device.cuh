@@ -42,14 +42,6 @@ struct Args {
 __device__ __forceinline__ float fm(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fm(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-__device__ __forceinline__ void cp16(void* s, const void* g) {
-  const u32 sa = (u32)__cvta_generic_to_shared(s);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
-}
-
 // ---------------------------------------------------------------- register gates (stride S = 1 << bit)
 template <int N, int S, typename T>
 __device__ __forceinline__ void ry(T* re, T* im, T c, int f) {
@@ -363,16 +355,6 @@ struct Ctx {
   u32 tid;
   bool valid;
 };
-
-// element offset of tile element e: bits of e deposited onto the physical positions L
-template <int NT>
-__device__ __forceinline__ i64 deposit_thread(const u8* L, const u8* tbit, u32 tid) {
-  i64 g = 0;
-#pragma unroll
-  for (int j = 0; j < NT; j++)
-    if ((tid >> j) & 1u) g |= (i64)1 << L[tbit[j]];
-  return g;
-}
 
 // Block reduction of the <Z> partials of the last forward phase into zrow[0..K]: row[j] is the
 // signed sum over tile bit j, row[K] the tile total. zmap[j] >= 0: register bit; else thread bit -1-zmap[j].
