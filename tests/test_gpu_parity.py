@@ -134,27 +134,40 @@ def test_c2_fused_equals_per_gate_all_samples(q):
 
 
 # ---------------------------------------------------------------- C3 (20 qubits, batch 64) at full size
-def test_c3_full_size_sampled(q):
+_C3_REF = {}
+
+
+def _c3_reference(wl, pr, ir, g):
+    """Oracle-S states of samples 0, 1 and parameter-shift gradients of two sampled gates (cached:
+    the 20-qubit oracle is the slow part)."""
+    if not _C3_REF:
+        L = len(wl.gates)
+        first = L - 2 * wl.n - 3
+        _C3_REF["psi"] = oracle.simulate_strided(wl.gates, wl.n, pr, ir[:2])
+        pre = (first, oracle.simulate_strided(wl.gates[:first], wl.n, pr, ir[:2]))
+        _C3_REF["grads"] = {gi: shift_grad_strided(wl.gates, wl.n, pr, ir[:2], g[:2], gi, prefix=pre).sum()
+                            for gi in (L - wl.n - 1, first)}
+    return _C3_REF["psi"], _C3_REF["grads"]
+
+
+# the bench's launch configuration: batch 64, checkpoint every pass, the tile sizes its autotuner picks
+@pytest.mark.parametrize("k", [12, 11, 10])
+def test_c3_full_size_sampled(q, k):
     wl = W.config(3)
     # only samples 0 and 1 carry loss weight, so the batch-summed parameter gradient is checkable
     g = np.zeros_like(wl.grad_out)
     g[:2] = wl.grad_out[:2]
     wl.grad_out = g
-    r = run(q, wl, "c64", "fused")
+    r = run(q, wl, "c64", "fused", k=k, checkpoint_passes=1)
     pr, ir = rounded(wl, "c64")
     norms = np.linalg.norm(r["states"], axis=1)
     np.testing.assert_allclose(norms, 1.0, atol=1e-5)
-    psi = oracle.simulate_strided(wl.gates, wl.n, pr, ir[:2])
+    psi, grads = _c3_reference(wl, pr, ir, g)
     np.testing.assert_allclose(r["states"][:2], psi, atol=1e-5, rtol=0)
     np.testing.assert_allclose(r["z"][:2], oracle.expval_z(psi, wl.n), atol=1e-5, rtol=0)
-    # parameter-shift on a sample of gates: two in the last layer, one in the first trainable layer
-    L = len(wl.gates)
-    first = L - 2 * wl.n - 3
-    pre = (first, oracle.simulate_strided(wl.gates[:first], wl.n, pr, ir[:2]))
-    for gi in (L - wl.n - 1, first):
-        d = shift_grad_strided(wl.gates, wl.n, pr, ir[:2], g[:2], gi, prefix=pre)
+    # parameter shift on a sample of gates: one in the last layer, one in the first trainable layer
+    for gi, ref in grads.items():
         p = wl.gates[gi][3]
-        ref = d.sum()
         assert abs(r["dp"][p] - ref) <= 1e-4 * max(1e-3, np.abs(r["dp"]).max()), (gi, r["dp"][p], ref)
 
 
