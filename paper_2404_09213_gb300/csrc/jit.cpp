@@ -418,6 +418,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           call = "if (((tb >> " + std::to_string(op.a) + ") & 1u) && ((tb >> " + std::to_string(op.b) +
                  ") & 1u)) qj::scal<" + std::to_string(N) + ">(%R, %I, T(-1));";
           break;
+        case K_SCALE:
+          call = "qj::scal<" + std::to_string(N) + ">(%R, %I, c.cf[" + std::to_string(li) + "]);";
+          break;
       }
       auto inst = [&](const char* rr, const char* ii) {
         std::string c2 = call;

@@ -71,6 +71,8 @@ int mcuda(cudaError_t e, const char* what) {
   qsim::set_last_error(std::string(what) + ": " + cudaGetErrorString(e));
   return QSIM_ERR_CUDA;
 }
+// exec-list entry of an op: its gate in the concatenated gate list, or -1 for a rescale op
+int32_t op_gate(const DevOp& op, int64_t goff) { return op.gate < 0 ? -1 : (int32_t)(goff + op.gate); }
 }  // namespace
 
 struct qsim_multi_s {
@@ -191,9 +193,9 @@ struct qsim_multi_s {
         const auto& pp = s.passes[p];
         pass_circ.push_back(c);
         exbf.push_back((int32_t)exf.size());
-        for (int i = 0; i < pp.dev.n_ops; i++) exf.push_back((int32_t)(goff[c] + s.ops[pp.dev.op0 + i].gate));
+        for (int i = 0; i < pp.dev.n_ops; i++) exf.push_back(op_gate(s.ops[pp.dev.op0 + i], goff[c]));
         exbb.push_back((int32_t)exb.size());
-        for (int i = 0; i < pp.devb.n_ops; i++) exb.push_back((int32_t)(goff[c] + s.ops[pp.devb.op0 + i].gate));
+        for (int i = 0; i < pp.devb.n_ops; i++) exb.push_back(op_gate(s.ops[pp.devb.op0 + i], goff[c]));
         off_bits.push_back((int64_t)bits.size());
         for (int j = 0; j < pp.dev.k; j++) bits.push_back(pp.dev.Q[j]);   // logical qubits (<Z> reduction)
         for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.QN[j]);

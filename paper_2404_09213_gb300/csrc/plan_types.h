@@ -14,6 +14,13 @@ namespace qsim {
 constexpr int kMaxTileBits = 16;   // k <= 16
 constexpr int kMaxR = 5;           // at most 2^5 amplitudes per thread and array
 constexpr int kMaxQubits = 34;
+// Rotations and Hadamards run unnormalised inside a pass (a tangent or cotangent coefficient, the
+// factored cos / sin / 1/sqrt(2) applied later), so each one grows the tile's values by at most
+// sqrt(2). A K_SCALE op after every kRescaleEvery of them applies the factors gathered so far: the
+// values stay within 2^24 of their true size (2^48 for the backward's lambda-psi products), far
+// inside the FP32 range. kMaxScaledOpsPerPass bounds the specialised kernel's length.
+constexpr int kRescaleEvery = 48;
+constexpr int kMaxScaledOpsPerPass = 256;
 
 // Op kinds understood by the pass kernels. "_R" = operand is a register bit (a/b = register index),
 // "_T" = operand is a thread bit (a/b = tile bit index, value taken from the thread's base index).
@@ -29,6 +36,7 @@ enum OpKind : uint8_t {
   K_CZ_RR,      // CZ on register bits a, b
   K_CZ_RT,      // CZ on register bit a and thread bit b
   K_CZ_TT,      // CZ on thread bits a, b
+  K_SCALE,      // multiply every amplitude of the tile by the op's per-sample value (range control)
   K_NUM_KINDS
 };
 
@@ -37,7 +45,7 @@ struct DevOp {
   uint8_t a;
   uint8_t b;
   uint8_t rot;      // 1: parametric rotation (has a coefficient and a gradient)
-  int32_t gate;     // index into the plan's gate list
+  int32_t gate;     // index into the plan's gate list (-1 for K_SCALE)
   int32_t gslot;    // gradient slot within the pass (-1 if none)
 };
 

@@ -11,6 +11,8 @@ namespace qsim {
 
 static bool is_1q(int t) { return t == QSIM_RX || t == QSIM_RY || t == QSIM_RZ || t == QSIM_H || t == QSIM_X; }
 static bool is_rot(int t) { return t == QSIM_RX || t == QSIM_RY || t == QSIM_RZ; }
+// gates the pass kernels apply unnormalised (their scale is applied later, see kRescaleEvery)
+static bool is_scaled(int t) { return is_rot(t) || t == QSIM_H; }
 
 int validate_gates(const qsim_gate* g, int n_gates, int n, std::vector<Gate>& out, int& n_params,
                    int& n_inputs, std::string& err) {
@@ -161,6 +163,7 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
   d.lay0 = (int)s.layouts.size();
   std::vector<int> remaining = pp.gates;
   int gslot = 0;
+  int since_scale = 0;   // unnormalised ops since the pass start or the last K_SCALE
   // The first and the last register phase move their amplitudes straight between registers and global
   // memory: the first in the pass's input layout, the last in its output layout. The tile bits at
   // physical bits 1..3 of that layout (the low bits of a contiguous run) lead the phase's thread bits,
@@ -198,6 +201,15 @@ static int build_phases(Schedule& s, PassPlan& pp, DevPass& d, bool grads, int w
     };
     for (int gi : taken) {
       const Gate& g = s.gates[gi];
+      if (is_scaled(g.type) && since_scale == kRescaleEvery) {
+        DevOp sc{};
+        sc.kind = K_SCALE;
+        sc.gate = -1;
+        sc.gslot = -1;
+        s.ops.push_back(sc);
+        since_scale = 0;
+      }
+      since_scale += is_scaled(g.type);
       DevOp op{};
       op.gate = gi;
       op.gslot = -1;
@@ -381,6 +393,7 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
   for (int b = 0; b < c; b++) canon_low.insert(n - 1 - b);
   auto greedy = [&](std::set<int> S, std::vector<char>& dn, std::vector<int>& took) {
     std::set<int> blocked;
+    int n_scaled = 0;
     for (int i = 0; i < G; i++) {
       if (dn[i]) continue;
       int q[2], nq;
@@ -393,10 +406,12 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
       }
       std::set<int> T = S;
       for (int j = 0; j < nq; j++) T.insert(q[j]);
-      if ((int)T.size() <= k) {
+      const bool sc = is_scaled(gates[i].type);
+      if ((int)T.size() <= k && (!sc || n_scaled < kMaxScaledOpsPerPass)) {
         S = T;
         took.push_back(i);
         dn[i] = 1;
+        n_scaled += sc;
       } else {
         for (int j = 0; j < nq; j++) blocked.insert(q[j]);
       }
@@ -514,7 +529,7 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
 }
 
 std::string describe_schedule(const Schedule& s) {
-  static const char* kn[] = {"ry", "rx", "rz", "h", "x", "rz_t", "cx", "cx_t", "cz", "cz_t", "cz_tt"};
+  static const char* kn[] = {"ry", "rx", "rz", "h", "x", "rz_t", "cx", "cx_t", "cz", "cz_t", "cz_tt", "scale"};
   std::ostringstream o;
   o << "{\"n\":" << s.n << ",\"k\":" << s.k << ",\"R\":" << s.R << ",\"Rb\":" << s.Rb << ",\"c\":" << s.c
     << ",\"mode\":" << s.mode << ",\"n_params\":" << s.n_params << ",\"n_inputs\":" << s.n_inputs

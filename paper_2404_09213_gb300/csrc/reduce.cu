@@ -48,9 +48,16 @@ __global__ void coef_kernel(CoefArgs a) {
   const int e0 = a.exec_begin[p], e1 = a.exec_begin[p + 1];
   T* cfp = reinterpret_cast<T*>(a.cfp_f) + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
   uint8_t* fmp = a.fmp_f + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
+  // fs: the factors of the ops since the pass start or the last rescale op (which applies and resets them)
   double fs = 1.0;
   for (int e = e0; e < e1; e++) {
     const int g = a.exec_gates[e];
+    if (g < 0) {
+      cfp[e] = (T)fs;
+      fmp[e] = 0;
+      fs = 1.0;
+      continue;
+    }
     const int ty = a.gate_type[g];
     T v = 0;
     uint8_t f = 0;
@@ -78,16 +85,22 @@ __global__ void coef_kernel(CoefArgs a) {
     fmp[e] = f;
   }
   reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)fs;
-  // backward: ops undone in reverse order of the backward op list; gm = (product of inverse scales so far)^2
+  // backward: ops undone in reverse order of the backward op list; gm = (product of the inverse scales
+  // since the last rescale op)^2
   double bs = 1.0;
   const int b0 = a.exec_begin_b[p], b1 = a.exec_begin_b[p + 1];
   T* cfpb = reinterpret_cast<T*>(a.cfp_b) + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
   uint8_t* fmpb = a.fmp_b + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
   for (int e = b1 - 1; e >= b0; e--) {
     const int g = a.exec_gates_b[e];
+    fmpb[e] = 0;
+    if (g < 0) {   // rescale op: applies the inverse scales gathered since the last one, bs restarts
+      cfpb[e] = (T)bs;
+      bs = 1.0;
+      continue;
+    }
     const int ty = a.gate_type[g];
     cfpb[e] = 0;
-    fmpb[e] = 0;
     if (ty <= QSIM_RZ) {
       const int64_t gi = (int64_t)g * a.B + b;
       cfpb[e] = -coef[gi];   // the inverse rotation

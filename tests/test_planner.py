@@ -111,8 +111,30 @@ def check_layouts(d, n):
         assert ps["nonlocal_o"] == ps["nonlocal"] and sorted(ps["Lo"]) == sorted(ps["L"])
 
 
+RESCALE_EVERY, MAX_SCALED_PER_PASS = 48, 256
+
+
+def check_rescale(gates, ps, phases):
+    # unnormalised ops (rotations, Hadamards) between two rescale ops: exactly RESCALE_EVERY; after the
+    # last one at most that many, and a rescale op is never the pass's last op
+    ops = [op for ph in phases for op in ph["ops"]]
+    scaled = [op["kind"] != "scale" and gates[op["gate"]][0] in (W.RX, W.RY, W.RZ, W.H) for op in ops]
+    assert sum(scaled) <= MAX_SCALED_PER_PASS
+    run = 0
+    for op, sc in zip(ops, scaled):
+        if op["kind"] == "scale":
+            assert op["gate"] == -1 and op["gslot"] == -1
+            assert run == RESCALE_EVERY, run
+            run = 0
+        run += sc
+    assert run <= RESCALE_EVERY
+    assert not ops or ops[-1]["kind"] != "scale"
+
+
 def check_phases(gates, ps, phases, layouts, k, R, local):
     # phases: same gates, order per wire preserved, register bits hold the targets that need them
+    check_rescale(gates, ps, phases)
+    phases = [dict(ph, ops=[op for op in ph["ops"] if op["kind"] != "scale"]) for ph in phases]
     ph_order = [op["gate"] for ph in phases for op in ph["ops"]]
     assert sorted(ph_order) == sorted(ps["gates"])
     last_in_pass = {}
@@ -167,6 +189,22 @@ def test_index_maps_are_the_brute_force_permutation(q, n, kw):
             np.testing.assert_array_equal(m, brute[t])
             seen.append(m)
         assert np.array_equal(np.sort(np.concatenate(seen)), np.arange(1 << n))
+
+
+@pytest.mark.parametrize("n,layers,kw", [(10, 20, {}), (8, 40, {"contiguous_bits": 2}), (11, 12, {"dtype": "c128"})])
+def test_deep_narrow_circuits_rescale_and_split(q, n, layers, kw):
+    # a deep circuit on few qubits: passes hold at most MAX_SCALED_PER_PASS unnormalised ops, with a
+    # rescale op after every RESCALE_EVERY of them (checked in check_phases)
+    gates = W.ring_ansatz(n, layers) + [W.gate(W.H, (i % n,)) for i in range(50)]
+    d = q.Plan(gates, n, **kw).describe()
+    n_scaled = sum(1 for g in gates if g[0] in (W.RX, W.RY, W.RZ, W.H))
+    assert len(d["passes"]) >= -(-n_scaled // MAX_SCALED_PER_PASS)
+    n_rescale = 0
+    for ps in d["passes"]:
+        for key in ("phases", "bwd_phases"):
+            check_rescale(gates, ps, ps[key])
+        n_rescale += sum(op["kind"] == "scale" for ph in ps["phases"] for op in ph["ops"])
+    assert n_rescale >= 1
 
 
 def test_per_gate_schedule(q):
