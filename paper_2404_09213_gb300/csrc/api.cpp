@@ -505,6 +505,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   ca.n_inputs = s.n_inputs;
   ca.B = batch;
   ca.P = p->P();
+  ca.G = (int)s.gates.size();
   ca.weight_remap = p->opts.weight_remap;
   ca.coef = p->coef;
   ca.form = p->form;

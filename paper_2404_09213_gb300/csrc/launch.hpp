@@ -23,7 +23,7 @@ struct CoefArgs {
   const int32_t* exec_begin_b;  // [P + 1]
   const void* params;
   const void* inputs;
-  int n_inputs, B, P;
+  int n_inputs, B, P, G;
   int weight_remap;             // 1: trainable angles enter as pi * tanh(param); 2: input angles as well
   void* coef;                   // [G * B]
   uint8_t* form;                // [G * B]
@@ -36,8 +36,8 @@ struct CoefArgs {
   void* scale_f;                // [P * B]
   void* scale_b;                // [P * B]
   double* gm;                   // [G * B] squared backward scale at each rotation
-  // several circuits (all null for a single circuit): circuit of every pass and its offsets
-  const int32_t* pass_circ;     // [P]
+  // several circuits (all null for a single circuit): circuit of every gate and its offsets
+  const int32_t* gate_circ;     // [G]
   const int64_t* circ_param_off;   // [C] first parameter of the circuit
   const int64_t* circ_col_off;     // [C] input columns before the circuit (per sample)
   const int32_t* circ_ninputs;     // [C]

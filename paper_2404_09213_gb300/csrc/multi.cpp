@@ -87,7 +87,7 @@ struct qsim_multi_s {
   bool uploaded = false;
   JitMulti jm;
   int32_t *d_gtype = nullptr, *d_gparam = nullptr, *d_exf = nullptr, *d_exbf = nullptr, *d_exb = nullptr,
-          *d_exbb = nullptr, *d_pass_circ = nullptr, *d_ninp = nullptr;
+          *d_exbb = nullptr, *d_gate_circ = nullptr, *d_ninp = nullptr;
   int64_t *d_circ_param_off = nullptr, *d_circ_col_off = nullptr, *d_zq_off = nullptr;
   uint8_t* d_bits = nullptr;
   std::vector<int64_t> off_bits;                     // per global pass
@@ -160,7 +160,7 @@ struct qsim_multi_s {
   }
   void free_all() {
     free_ws();
-    void* ps[] = {d_gtype, d_gparam, d_exf, d_exbf, d_exb, d_exbb, d_pass_circ, d_ninp, d_circ_param_off,
+    void* ps[] = {d_gtype, d_gparam, d_exf, d_exbf, d_exb, d_exbb, d_gate_circ, d_ninp, d_circ_param_off,
                   d_circ_col_off, d_zq_off, d_bits, d_occ_gate, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ,
                   d_col_stride, d_col_index, d_col_circ_off};
     for (void* p : ps)
@@ -173,7 +173,7 @@ struct qsim_multi_s {
 
   int upload() {
     if (uploaded) return QSIM_OK;
-    std::vector<int32_t> gtype, gparam, exf, exbf, exb, exbb, pass_circ, ninp, p_ptr, p_occ, i_ptr, i_occ,
+    std::vector<int32_t> gtype, gparam, exf, exbf, exb, exbb, gate_circ, ninp, p_ptr, p_occ, i_ptr, i_occ,
         col_stride, col_index, occ_gate;
     std::vector<int64_t> cpo, cco, zqo, col_circ_off;
     std::vector<uint8_t> bits;
@@ -185,13 +185,13 @@ struct qsim_multi_s {
       for (auto& g : s.gates) {
         gtype.push_back(g.type);
         gparam.push_back(g.param);
+        gate_circ.push_back(c);
       }
       cpo.push_back(param_off[c]);
       cco.push_back(col_off[c]);
       ninp.push_back(s.n_inputs);
       for (int p = 0; p < P(c); p++) {
         const auto& pp = s.passes[p];
-        pass_circ.push_back(c);
         exbf.push_back((int32_t)exf.size());
         for (int i = 0; i < pp.dev.n_ops; i++) exf.push_back(op_gate(s.ops[pp.dev.op0 + i], goff[c]));
         exbb.push_back((int32_t)exb.size());
@@ -237,7 +237,7 @@ struct qsim_multi_s {
 #define QSIM_UP(P, V) \
   if (e == cudaSuccess) e = up(&P, V);
     QSIM_UP(d_gtype, gtype) QSIM_UP(d_gparam, gparam) QSIM_UP(d_exf, exf) QSIM_UP(d_exbf, exbf)
-    QSIM_UP(d_exb, exb) QSIM_UP(d_exbb, exbb) QSIM_UP(d_pass_circ, pass_circ) QSIM_UP(d_ninp, ninp)
+    QSIM_UP(d_exb, exb) QSIM_UP(d_exbb, exbb) QSIM_UP(d_gate_circ, gate_circ) QSIM_UP(d_ninp, ninp)
     QSIM_UP(d_circ_param_off, cpo) QSIM_UP(d_circ_col_off, cco) QSIM_UP(d_zq_off, zqo) QSIM_UP(d_bits, bits)
     QSIM_UP(d_occ_gate, occ_gate) QSIM_UP(d_p_ptr, p_ptr) QSIM_UP(d_p_occ, p_occ)
     QSIM_UP(d_i_ptr, i_ptr) QSIM_UP(d_i_occ, i_occ) QSIM_UP(d_col_stride, col_stride)
@@ -490,6 +490,7 @@ static cudaError_t multi_enqueue_fwd(qsim_multi_t m, const void* d_params, const
   ca.n_inputs = 0;
   ca.B = m->B;
   ca.P = (int)m->P_tot;
+  ca.G = (int)m->G_tot;
   ca.weight_remap = m->opts.weight_remap;
   ca.coef = m->coef;
   ca.form = m->form;
@@ -500,7 +501,7 @@ static cudaError_t multi_enqueue_fwd(qsim_multi_t m, const void* d_params, const
   ca.scale_f = m->scale_f;
   ca.scale_b = m->scale_b;
   ca.gm = m->gm;
-  ca.pass_circ = m->d_pass_circ;
+  ca.gate_circ = m->d_gate_circ;
   ca.circ_param_off = m->d_circ_param_off;
   ca.circ_col_off = m->d_circ_col_off;
   ca.circ_ninputs = m->d_ninp;

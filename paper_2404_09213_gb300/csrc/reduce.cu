@@ -30,21 +30,43 @@ __device__ __forceinline__ double remap_slope(const void* params, int64_t i, int
   return kPi * (1.0 - t * t);
 }
 
+// Stage 1, one thread per (gate, sample): the angle's sine and cosine (FP64), the coefficient and its
+// form, and the factored-out value (cos for the tangent form, sin for the cotangent form), parked in
+// gm until stage 2 turns it into the squared backward scale.
 template <typename T>
-__global__ void coef_kernel(CoefArgs a) {
+__global__ void coef_gate_kernel(CoefArgs a) {
   const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (int64_t)a.P * a.B) return;
-  const int p = (int)(id / a.B), b = (int)(id - (int64_t)p * a.B);
+  if (id >= (int64_t)a.G * a.B) return;
+  const int g = (int)(id / a.B), b = (int)(id - (int64_t)g * a.B);
+  if (a.gate_type[g] > QSIM_RZ) return;
   const T* params = reinterpret_cast<const T*>(a.params);
   const T* inputs = reinterpret_cast<const T*>(a.inputs);
   int n_inputs = a.n_inputs;
-  if (a.pass_circ) {   // several circuits: parameters and inputs of this pass's circuit
-    const int c = a.pass_circ[p];
+  if (a.gate_circ) {   // several circuits: parameters and inputs of this gate's circuit
+    const int c = a.gate_circ[g];
     if (params) params += a.circ_param_off[c];
     if (inputs) inputs += (int64_t)a.B * a.circ_col_off[c];
     n_inputs = a.circ_ninputs[c];
   }
-  T* coef = reinterpret_cast<T*>(a.coef);
+  const int pr = a.gate_param[g];
+  const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
+                            : weight(inputs[(int64_t)b * n_inputs + (-2 - pr)], a.weight_remap == 2);
+  double s, c;
+  sincos(0.5 * th, &s, &c);
+  const bool cot = fabs(s) > fabs(c);
+  reinterpret_cast<T*>(a.coef)[id] = (T)(cot ? c / s : s / c);
+  a.form[id] = cot ? 1 : 0;
+  a.gm[id] = cot ? s : c;
+}
+
+// Stage 2, one thread per (pass, sample): packs the pass's coefficients in op order and multiplies
+// the factored-out values into the per-pass scales (no trigonometry: products and copies only).
+template <typename T>
+__global__ void coef_pass_kernel(CoefArgs a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)a.P * a.B) return;
+  const int p = (int)(id / a.B), b = (int)(id - (int64_t)p * a.B);
+  const T* coef = reinterpret_cast<const T*>(a.coef);
   const int e0 = a.exec_begin[p], e1 = a.exec_begin[p + 1];
   T* cfp = reinterpret_cast<T*>(a.cfp_f) + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
   uint8_t* fmp = a.fmp_f + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
@@ -62,22 +84,10 @@ __global__ void coef_kernel(CoefArgs a) {
     T v = 0;
     uint8_t f = 0;
     if (ty <= QSIM_RZ) {
-      const int pr = a.gate_param[g];
-      const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
-                                : weight(inputs[(int64_t)b * n_inputs + (-2 - pr)], a.weight_remap == 2);
-      double s, c;
-      sincos(0.5 * th, &s, &c);
       const int64_t gi = (int64_t)g * a.B + b;
-      if (fabs(s) <= fabs(c)) {
-        v = (T)(s / c);
-        fs *= c;
-      } else {
-        v = (T)(c / s);
-        f = 1;
-        fs *= s;
-      }
-      coef[gi] = v;
-      a.form[gi] = f;
+      v = coef[gi];
+      f = a.form[gi];
+      fs *= a.gm[gi];
     } else if (ty == QSIM_H) {
       fs *= 0.70710678118654752440;
     }
@@ -86,7 +96,8 @@ __global__ void coef_kernel(CoefArgs a) {
   }
   reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)fs;
   // backward: ops undone in reverse order of the backward op list; gm = (product of the inverse scales
-  // since the last rescale op)^2
+  // since the last rescale op)^2. The pass's gates are this thread's alone (every gate sits in one
+  // pass), so reading the factor and overwriting it with gm cannot race.
   double bs = 1.0;
   const int b0 = a.exec_begin_b[p], b1 = a.exec_begin_b[p + 1];
   T* cfpb = reinterpret_cast<T*>(a.cfp_b) + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
@@ -103,15 +114,12 @@ __global__ void coef_kernel(CoefArgs a) {
     cfpb[e] = 0;
     if (ty <= QSIM_RZ) {
       const int64_t gi = (int64_t)g * a.B + b;
+      const uint8_t f = a.form[gi];
+      const double fac = a.gm[gi];
       cfpb[e] = -coef[gi];   // the inverse rotation
-      fmpb[e] = a.form[gi];
+      fmpb[e] = f;
       a.gm[gi] = bs * bs;
-      const int pr = a.gate_param[g];
-      const double th = pr >= 0 ? weight(params[pr], a.weight_remap)
-                                : weight(inputs[(int64_t)b * n_inputs + (-2 - pr)], a.weight_remap == 2);
-      double s, c;
-      sincos(0.5 * th, &s, &c);
-      bs *= (a.form[gi] == 0) ? c : -s;
+      bs *= f ? -fac : fac;
     } else if (ty == QSIM_H) {
       bs *= 0.70710678118654752440;
     }
@@ -120,12 +128,18 @@ __global__ void coef_kernel(CoefArgs a) {
 }
 
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
-  const int64_t n = (int64_t)a.P * a.B;
-  if (n == 0) return cudaSuccess;
-  const int thr = 128;
-  const unsigned blocks = (unsigned)((n + thr - 1) / thr);
-  if (dtype == QSIM_C128) coef_kernel<double><<<blocks, thr, 0, st>>>(a);
-  else coef_kernel<float><<<blocks, thr, 0, st>>>(a);
+  const int64_t ng = (int64_t)a.G * a.B, np = (int64_t)a.P * a.B;
+  if (np == 0) return cudaSuccess;
+  // stage 2 has one thread per (pass, sample), often few: small blocks spread them over more SMs
+  const int tg = 128, tp = 32;
+  const unsigned bg = (unsigned)((ng + tg - 1) / tg), bp = (unsigned)((np + tp - 1) / tp);
+  if (ng > 0) {
+    if (dtype == QSIM_C128) coef_gate_kernel<double><<<bg, tg, 0, st>>>(a);
+    else coef_gate_kernel<float><<<bg, tg, 0, st>>>(a);
+    g_kernel_launches++;
+  }
+  if (dtype == QSIM_C128) coef_pass_kernel<double><<<bp, tp, 0, st>>>(a);
+  else coef_pass_kernel<float><<<bp, tp, 0, st>>>(a);
   g_kernel_launches++;
   return cudaGetLastError();
 }
