@@ -59,80 +59,121 @@ __global__ void coef_gate_kernel(CoefArgs a) {
   a.gm[id] = cot ? s : c;
 }
 
-// Stage 2, one thread per (pass, sample): packs the pass's coefficients in op order and multiplies
-// the factored-out values into the per-pass scales (no trigonometry: products and copies only).
+// Stage 2, one warp per (pass, sample): packs the pass's coefficients in op order and multiplies the
+// factored-out values into the per-pass scales, 32 ops at a time (no trigonometry). R is the running
+// product of the factors in processing order (an inclusive warp scan plus the previous chunks'
+// carry); the scale gathered since the last rescale op is R divided by R at that op. The factors lie
+// in [1/sqrt(2), 1] and a pass holds at most 256 of them, so R stays far inside the FP64 range.
+struct ScanState {
+  double carry = 1.0;   // product of the factors of all earlier chunks
+  double rlast = 1.0;   // running product at the latest rescale op so far
+};
+
+// Returns the inclusive running product at this lane's op; rprev = the running product at the
+// latest rescale op before it (in processing order).
+__device__ __forceinline__ double scan_chunk(double fac, bool is_scale, ScanState& st, double& rprev) {
+  const unsigned full = 0xffffffffu, lane = threadIdx.x & 31u;
+  double r = fac;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double t = __shfl_up_sync(full, r, o);
+    if ((int)lane >= o) r *= t;
+  }
+  r *= st.carry;
+  const unsigned m = __ballot_sync(full, is_scale);
+  const unsigned below = m & ((1u << lane) - 1u);
+  const double rs = __shfl_sync(full, r, below ? 31 - __clz(below) : (int)lane);
+  rprev = below ? rs : st.rlast;
+  const double rl = __shfl_sync(full, r, m ? 31 - __clz(m) : 0);
+  if (m) st.rlast = rl;
+  st.carry = __shfl_sync(full, r, 31);
+  return r;
+}
+
 template <typename T>
 __global__ void coef_pass_kernel(CoefArgs a) {
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= (int64_t)a.P * a.B) return;
-  const int p = (int)(id / a.B), b = (int)(id - (int64_t)p * a.B);
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= (int64_t)a.P * a.B) return;   // whole warps leave together
+  const int lane = (int)(threadIdx.x & 31u);
+  const int p = (int)(w / a.B), b = (int)(w - (int64_t)p * a.B);
   const T* coef = reinterpret_cast<const T*>(a.coef);
+  constexpr double kH = 0.70710678118654752440;
+  // forward: op order
   const int e0 = a.exec_begin[p], e1 = a.exec_begin[p + 1];
   T* cfp = reinterpret_cast<T*>(a.cfp_f) + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
   uint8_t* fmp = a.fmp_f + (int64_t)e0 * a.B + (int64_t)b * (e1 - e0) - e0;
-  // fs: the factors of the ops since the pass start or the last rescale op (which applies and resets them)
-  double fs = 1.0;
-  for (int e = e0; e < e1; e++) {
-    const int g = a.exec_gates[e];
-    if (g < 0) {
-      cfp[e] = (T)fs;
-      fmp[e] = 0;
-      fs = 1.0;
-      continue;
-    }
-    const int ty = a.gate_type[g];
+  ScanState sf;
+  for (int base = e0; base < e1; base += 32) {
+    const int e = base + lane;
+    const int g = e < e1 ? a.exec_gates[e] : -2;   // -1: rescale op, -2: past the end
+    double fac = 1.0;
     T v = 0;
     uint8_t f = 0;
-    if (ty <= QSIM_RZ) {
-      const int64_t gi = (int64_t)g * a.B + b;
-      v = coef[gi];
-      f = a.form[gi];
-      fs *= a.gm[gi];
-    } else if (ty == QSIM_H) {
-      fs *= 0.70710678118654752440;
+    if (g >= 0) {
+      const int ty = a.gate_type[g];
+      if (ty <= QSIM_RZ) {
+        const int64_t gi = (int64_t)g * a.B + b;
+        v = coef[gi];
+        f = a.form[gi];
+        fac = a.gm[gi];
+      } else if (ty == QSIM_H) {
+        fac = kH;
+      }
     }
-    cfp[e] = v;
-    fmp[e] = f;
+    double rprev;
+    const double r = scan_chunk(fac, g == -1, sf, rprev);
+    if (g == -1) v = (T)(r / rprev);   // a rescale op applies the factors since the previous one
+    if (g >= -1) {
+      cfp[e] = v;
+      fmp[e] = f;
+    }
   }
-  reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)fs;
-  // backward: ops undone in reverse order of the backward op list; gm = (product of the inverse scales
-  // since the last rescale op)^2. The pass's gates are this thread's alone (every gate sits in one
-  // pass), so reading the factor and overwriting it with gm cannot race.
-  double bs = 1.0;
+  if (lane == 0) reinterpret_cast<T*>(a.scale_f)[(int64_t)p * a.B + b] = (T)(sf.carry / sf.rlast);
+  __syncwarp();   // every lane's forward reads of gm come before any lane overwrites it below
+  // backward: ops undone from the end of the backward op list; gm = (product of the signed inverse
+  // scales since the last rescale op, before this op)^2. Every gate sits in exactly one pass, so the
+  // factors read and overwritten here are this warp's alone.
   const int b0 = a.exec_begin_b[p], b1 = a.exec_begin_b[p + 1];
   T* cfpb = reinterpret_cast<T*>(a.cfp_b) + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
   uint8_t* fmpb = a.fmp_b + (int64_t)b0 * a.B + (int64_t)b * (b1 - b0) - b0;
-  for (int e = b1 - 1; e >= b0; e--) {
-    const int g = a.exec_gates_b[e];
-    fmpb[e] = 0;
-    if (g < 0) {   // rescale op: applies the inverse scales gathered since the last one, bs restarts
-      cfpb[e] = (T)bs;
-      bs = 1.0;
-      continue;
+  ScanState sb;
+  for (int base = 0; base < b1 - b0; base += 32) {
+    const int e = b1 - 1 - base - lane;
+    const int g = e >= b0 ? a.exec_gates_b[e] : -2;
+    double fac = 1.0;
+    T v = 0;
+    uint8_t f = 0;
+    int64_t gi = -1;
+    if (g >= 0) {
+      const int ty = a.gate_type[g];
+      if (ty <= QSIM_RZ) {
+        gi = (int64_t)g * a.B + b;
+        f = a.form[gi];
+        v = -coef[gi];   // the inverse rotation
+        fac = f ? -a.gm[gi] : a.gm[gi];
+      } else if (ty == QSIM_H) {
+        fac = kH;
+      }
     }
-    const int ty = a.gate_type[g];
-    cfpb[e] = 0;
-    if (ty <= QSIM_RZ) {
-      const int64_t gi = (int64_t)g * a.B + b;
-      const uint8_t f = a.form[gi];
-      const double fac = a.gm[gi];
-      cfpb[e] = -coef[gi];   // the inverse rotation
-      fmpb[e] = f;
+    double rprev;
+    const double r = scan_chunk(fac, g == -1, sb, rprev);
+    if (gi >= 0) {
+      const double bs = (r / fac) / rprev;   // before this op: exclude its own factor
       a.gm[gi] = bs * bs;
-      bs *= f ? -fac : fac;
-    } else if (ty == QSIM_H) {
-      bs *= 0.70710678118654752440;
+    }
+    if (g == -1) v = (T)(r / rprev);
+    if (g >= -1) {
+      cfpb[e] = v;
+      fmpb[e] = f;
     }
   }
-  reinterpret_cast<T*>(a.scale_b)[(int64_t)p * a.B + b] = (T)bs;
+  if (lane == 0) reinterpret_cast<T*>(a.scale_b)[(int64_t)p * a.B + b] = (T)(sb.carry / sb.rlast);
 }
 
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
   const int64_t ng = (int64_t)a.G * a.B, np = (int64_t)a.P * a.B;
   if (np == 0) return cudaSuccess;
-  // stage 2 has one thread per (pass, sample), often few: small blocks spread them over more SMs
-  const int tg = 128, tp = 32;
-  const unsigned bg = (unsigned)((ng + tg - 1) / tg), bp = (unsigned)((np + tp - 1) / tp);
+  const int tg = 128, tp = 128;   // stage 2: one warp per (pass, sample), four per block
+  const unsigned bg = (unsigned)((ng + tg - 1) / tg), bp = (unsigned)((np * 32 + tp - 1) / tp);
   if (ng > 0) {
     if (dtype == QSIM_C128) coef_gate_kernel<double><<<bg, tg, 0, st>>>(a);
     else coef_gate_kernel<float><<<bg, tg, 0, st>>>(a);
