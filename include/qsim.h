@@ -121,7 +121,9 @@ int qsim_plan(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits,
 int qsim_plan_info_get(qsim_plan_t plan, qsim_plan_info* info);
 
 /* JSON description of the pass schedule (local qubits, tile-bit positions, register phases and
- * the gate indices of every op), for inspection and tests. Writes at most `cap` bytes including
+ * the gate indices of every op), for inspection and tests. Ops of kind "scale" (gate -1) are the
+ * range-control rescale ops the planner inserts after every 48 rotations / Hadamards of a pass
+ * (which holds at most 256 of them). Writes at most `cap` bytes including
  * the terminating NUL into h_buf (which may be NULL when cap == 0) and the full length + 1 into
  * *needed. */
 int qsim_plan_describe(qsim_plan_t plan, char* h_buf, size_t cap, size_t* needed);
