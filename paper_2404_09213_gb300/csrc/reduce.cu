@@ -224,7 +224,10 @@ __global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Qnl, i
 cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Qnl, int n_nonlocal, int64_t tps, int n,
                            int B, double* z, cudaStream_t st) {
   if ((int64_t)B * n == 0) return cudaSuccess;
-  z_final_kernel<<<(unsigned)(B * n), 256, 0, st>>>(zpart, k, d_Qnl, n_nonlocal, tps, n, B, z);
+  // a block per (sample, qubit) over the sample's tiles: one warp when there are few (a one-pass
+  // circuit has a single tile per sample)
+  const int thr = tps >= 256 ? 256 : 32;
+  z_final_kernel<<<(unsigned)(B * n), thr, 0, st>>>(zpart, k, d_Qnl, n_nonlocal, tps, n, B, z);
   g_kernel_launches++;
   return cudaGetLastError();
 }
@@ -264,7 +267,7 @@ __global__ void grad_scatter_kernel(GradReduceArgs a) {
 
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st) {
   if (a.n_occ > 0 && a.B > 0) {
-    grad_gather_kernel<<<(unsigned)(a.n_occ * a.B), 256, 0, st>>>(a);
+    grad_gather_kernel<<<(unsigned)(a.n_occ * a.B), a.tiles_per_sample >= 256 ? 256 : 32, 0, st>>>(a);
     g_kernel_launches++;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
