@@ -171,6 +171,22 @@ def test_c3_full_size_sampled(q, k):
         assert abs(r["dp"][p] - ref) <= 1e-4 * max(1e-3, np.abs(r["dp"]).max()), (gi, r["dp"][p], ref)
 
 
+# ---------------------------------------------------------------- backward vs central finite differences
+@pytest.mark.parametrize("dtype,tol", [("c64", 1e-4), ("c128", 1e-7)])
+def test_backward_against_central_finite_differences(q, dtype, tol):
+    # the adjoint gradients against FP64 central differences of the oracle's loss (h = 1e-4: truncation
+    # error ~1e-9 relative), on a multi-pass, checkpointed plan; inputs and parameters
+    wl = W.config(3, n=10, batch=4, layers=3, dtype=dtype)
+    r = run(q, wl, dtype, "fused", k=8, checkpoint_passes=1)
+    assert r["plan"].info()["n_passes"] > 2
+    pr, ir = rounded(wl, dtype)
+    fp, fi = oracle.grad_finite_diff(wl.gates, wl.n, pr, ir, wl.grad_out, h=1e-4, method="strided")
+    for got, ref, what in ((r["dp"], fp, "dparams"), (r["di"], fi, "dinputs")):
+        rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert rel <= tol, (what, rel)
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max() + 1e-9, what
+
+
 # ---------------------------------------------------------------- C5 ansatz at 12 qubits, checkpointed
 @pytest.mark.parametrize("ckpt,rot", [(0, False), (1, False), (3, False), (0, True), (1, True), (2, True)])
 def test_c5_ansatz_12q_checkpointed(q, ckpt, rot):
