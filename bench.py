@@ -197,6 +197,14 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def fp32_peak_tflops(dev_index):
+    """FP32 peak derived from unit counts and clocks: SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
+    (the maximum SM clock of this GPU model)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    return sms * 128 * 2 * 2.070e9 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+
+
 def traffic_record(kernel):
     """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -292,7 +300,11 @@ def run_ours(args, world, rank, local):
                 "avg_launch_ms": tot_ms / n_l if n_l else None, "launches_timed": n_l,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
                 "fwd_ms_per_step": float(fwd_ms.sum()) / max(nf, 1), "bwd_ms_per_step": float(bwd_ms.sum()) / max(nb, 1),
-                "passes": len(desc["passes"])}
+                "passes": len(desc["passes"]),
+                # HBM bytes per gate: fused passes amortise one round trip over all of a pass's gates
+                "bytes_per_gate": {"fwd": sum(fb) / len(wl.gates), "bwd": sum(bb) / len(wl.gates),
+                                   "per_gate_path_fwd": 16 * B * (1 << wl.n),
+                                   "per_gate_path_bwd": 32 * B * (1 << wl.n)}}
 
     # end to end: host inputs -> device, forward + backward, results -> host, every step
     e2e = None
@@ -456,13 +468,20 @@ def run_other(args, world, rank, local):
         samples = B
         P = plan.info()["n_passes"]
         tot = B * (1 << wl.n) * (8 + 16 * (P - 1)) if args.mode == "fused" else B * (1 << wl.n) * 16 * len(wl.gates)
+        # algorithmic work: a real 2x2 rotation costs 6 flop per amplitude (CNOTs are permutations)
+        n_rot = sum(1 for gt in wl.gates if gt[0] in (W.RX, W.RY, W.RZ))
+        c2_flops = B * (1 << wl.n) * 6 * n_rot
         name = f"C2: 12 qubits, batch 1024, c64, RX encoding + 6 x (RY,RZ + CNOT ring), forward only, {args.mode}"
-        extra = {"passes": P, "mode": args.mode}
+        extra = {"passes": P, "mode": args.mode, "rotations": n_rot,
+                 "l2": "32 MiB state per step stays in L2 and shared memory (ALU-bound, no flush)"}
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
     if args.workload == "c4":
         extra["queue"] = mp.info()
+    c2_profile = args.workload == "c2" and args.mode == "fused"
+    if c2_profile:
+        plan.set_profiling(args.steps)
     clk = ClockSampler(local)
     time.sleep(0.3)
     launches0 = q.kernel_launches()
@@ -479,15 +498,27 @@ def run_other(args, world, rank, local):
     gbs = tot * args.steps / (ms / 1e3) / 1e9
     metric = {"c2": "forward samples/s", "landscape": "gradient vectors/s"}.get(args.workload, "fwd+adjoint-bwd samples/s")
     unit = "gradient vectors/s" if args.workload == "landscape" else UNIT
+    roofline = {"bound": "hbm", "kernel": "whole step (all pass kernels)", "achieved": gbs, "peak": peak,
+                "unit": "GB/s", "frac": gbs / peak, "traffic": None,
+                "algorithmic_bytes_per_step": tot, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
+    if c2_profile:
+        # the state never leaves L2 / shared memory: a roofline on the FP32 ALUs for the pass kernel
+        fwd_ms, _, nf, _ = plan.read_profile()
+        plan.set_profiling(0)
+        kern_ms = float(fwd_ms.sum()) / max(nf, 1)          # pass-kernel time per step
+        fpk, fsrc = fp32_peak_tflops(local)
+        ach = c2_flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else None
+        roofline = {"bound": "alu", "kernel": "fwd_pass_kernel", "achieved": ach, "peak": fpk, "unit": "TFLOP/s",
+                    "frac": ach / fpk if ach else None, "traffic": None,
+                    "algorithmic_flops_per_launch": c2_flops / P, "avg_launch_ms": kern_ms / P,
+                    "launches_timed": nf * P, "peak_source": fsrc,
+                    "pass_kernel_share_of_step": kern_ms / (ms / args.steps)}
     out = {"metric": metric, "value": samples * args.steps / (ms / 1e3), "unit": unit, "n_gpus": 1,
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded splitmix64)",
            "config": dict(workload=name, precision="complex64 state, FP32 arithmetic, FP64 sums across tiles", **extra),
-           "roofline": {"bound": "hbm", "kernel": "whole step (all pass kernels)", "achieved": gbs, "peak": peak,
-                        "unit": "GB/s", "frac": gbs / peak, "traffic": None,
-                        "algorithmic_bytes_per_step": tot, "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"},
-           "gpu_launches": launches, "clocks": clocks}
+           "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(out))
 
 
