@@ -60,7 +60,7 @@ enum {
   QSIM_ERR_OOM = -6,        /* workspace allocation failed or exceeds the budget      */
   QSIM_ERR_CUDA = -7,       /* a CUDA call failed (message has the CUDA error string) */
   QSIM_ERR_TIMEOUT = -8,    /* a bounded device-side wait gave up                     */
-  QSIM_ERR_UNSUPPORTED = -9 /* size outside what this build supports                  */
+  QSIM_ERR_UNSUPPORTED = -9 /* size outside what the library supports                 */
 };
 
 enum { QSIM_C64 = 0, QSIM_C128 = 1 };

@@ -1,7 +1,7 @@
 """Build the in-tree shared library ``libqsim.so`` (CUDA kernels + C ABI) for sm_103a.
 
 Every translation unit is compiled in parallel with nvcc and linked with the static CUDA runtime,
-so the library depends only on the driver. Usage: ``python -m paper_2404_09213_gb300.build``.
+so the library depends only on the CUDA driver. Usage: ``python -m paper_2404_09213_gb300.build``.
 """
 from __future__ import annotations
 
