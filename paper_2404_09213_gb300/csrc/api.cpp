@@ -87,7 +87,6 @@ struct qsim_plan_s {
   void* states = nullptr;
   int B = 0;
   cudaStream_t last_stream = nullptr;
-  // optional per-pass event timing
   // optional per-launch event timing (a log of launches; read_profile sums them per pass)
   int prof_depth = 0;            // 0 = off; else number of forward + backward calls to log
   bool profiling = false;
