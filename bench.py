@@ -205,21 +205,16 @@ def fp32_peak_tflops(dev_index):
     return sms * 128 * 2 * 2.070e9 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
 
 
-def traffic_record(kernel):
-    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the kernel source is unchanged."""
+def traffic_record(kernel, kernel_source):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the plan's generated kernel
+    program (every pass kernel, as compiled) is the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path))
-    rec = d.get(kernel)
+    rec = json.load(open(path)).get(kernel)
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2404_09213_gb300", "csrc")
-    h = hashlib.sha256()
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h", ".hpp", ".cpp")):
-            h.update(open(os.path.join(src, f), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest():
+    if rec.get("kernel_source_sha256") != hashlib.sha256(kernel_source.encode()).hexdigest():
         return None
     return rec.get("dram_bytes_per_launch_full")
 
@@ -293,7 +288,7 @@ def run_ours(args, world, rank, local):
     else:
         tot_b, tot_ms, n_l = sum(bb) * nb, float(bwd_ms.sum()), len(bb) * nb
     achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1e3) / 1e9 if tot_ms > 0 else None
-    traffic = traffic_record(kern)
+    traffic = traffic_record(kern, plan.kernel_source())
     roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "algorithmic_bytes_per_launch": tot_b / n_l if n_l else None,
