@@ -189,6 +189,18 @@ def algorithmic_bytes(plan_desc, B, n, direction, checkpoint_passes=0):
     return out
 
 
+def per_pass_table(desc, fwd_bytes, bwd_bytes, fwd_ms, bwd_ms, n_fwd, n_bwd):
+    """Per fused pass: gates, HBM bytes per gate (forward), and achieved GB/s in each direction from the
+    pass's own event-timed launches (ms summed over n_fwd / n_bwd recorded calls)."""
+    gates = [len(ps["gates"]) for ps in desc["passes"]]
+    f_ms = [float(t) / max(n_fwd, 1) for t in fwd_ms]
+    b_ms = [float(t) / max(n_bwd, 1) for t in bwd_ms]
+    return {"gates": gates,
+            "bytes_per_gate_fwd": [round(fb / max(g, 1)) for fb, g in zip(fwd_bytes, gates)],
+            "fwd_gbs": [round(fb / (t / 1e3) / 1e9, 1) if t > 0 else None for fb, t in zip(fwd_bytes, f_ms)],
+            "bwd_gbs": [round(bb / (t / 1e3) / 1e9, 1) if t > 0 else None for bb, t in zip(bwd_bytes, b_ms)]}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -299,7 +311,8 @@ def run_ours(args, world, rank, local):
                 # HBM bytes per gate: fused passes amortise one round trip over all of a pass's gates
                 "bytes_per_gate": {"fwd": sum(fb) / len(wl.gates), "bwd": sum(bb) / len(wl.gates),
                                    "per_gate_path_fwd": 16 * B * (1 << wl.n),
-                                   "per_gate_path_bwd": 32 * B * (1 << wl.n)}}
+                                   "per_gate_path_bwd": 32 * B * (1 << wl.n)},
+                "per_pass": per_pass_table(desc, fb, bb, fwd_ms, bwd_ms, nf, nb) if args.mode == "fused" else None}
 
     # end to end: host inputs -> device, forward + backward, results -> host, every step
     e2e = None
