@@ -201,6 +201,33 @@ def per_pass_table(desc, fwd_bytes, bwd_bytes, fwd_ms, bwd_ms, n_fwd, n_bwd):
             "bwd_gbs": [round(bb / (t / 1e3) / 1e9, 1) if t > 0 else None for bb, t in zip(bwd_bytes, b_ms)]}
 
 
+def pass_roofline(desc, B, wl, ckpt, mode, fwd_ms, bwd_ms, nf, nb, kernel_source, peak, peak_kind):
+    """Roofline object of the dominant pass kernel (backward in fused mode): algorithmic bytes per launch
+    over its average event-timed launch, against the measured HBM peak; plus bytes per gate and the
+    per-pass table. fwd_ms / bwd_ms: per-pass event times summed over nf / nb recorded calls."""
+    fb = algorithmic_bytes(desc, B, wl.n, "fwd")
+    bb = algorithmic_bytes(desc, B, wl.n, "bwd", ckpt)
+    kern = "bwd_pass_kernel" if mode == "fused" else "pg_bwd_kernel"
+    if fwd_ms.sum() > bwd_ms.sum():
+        kern = "fwd_pass_kernel" if mode == "fused" else "pg_gate_kernel"
+        tot_b, tot_ms, n_l = sum(fb) * nf, float(fwd_ms.sum()), len(fb) * nf
+    else:
+        tot_b, tot_ms, n_l = sum(bb) * nb, float(bwd_ms.sum()), len(bb) * nb
+    achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1e3) / 1e9 if tot_ms > 0 else None
+    return {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic_record(kern, kernel_source),
+            "algorithmic_bytes_per_launch": tot_b / n_l if n_l else None,
+            "avg_launch_ms": tot_ms / n_l if n_l else None, "launches_timed": n_l,
+            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
+            "fwd_ms_per_step": float(fwd_ms.sum()) / max(nf, 1), "bwd_ms_per_step": float(bwd_ms.sum()) / max(nb, 1),
+            "passes": len(desc["passes"]),
+            # HBM bytes per gate: fused passes amortise one round trip over all of a pass's gates
+            "bytes_per_gate": {"fwd": sum(fb) / len(wl.gates), "bwd": sum(bb) / len(wl.gates),
+                               "per_gate_path_fwd": 16 * B * (1 << wl.n),
+                               "per_gate_path_bwd": 32 * B * (1 << wl.n)},
+            "per_pass": per_pass_table(desc, fb, bb, fwd_ms, bwd_ms, nf, nb) if mode == "fused" else None}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -291,28 +318,7 @@ def run_ours(args, world, rank, local):
 
     # roofline of the dominant kernel (fused backward pass kernel in fused mode)
     peak, peak_kind = load_peaks()
-    fb = algorithmic_bytes(desc, B, wl.n, "fwd")
-    bb = algorithmic_bytes(desc, B, wl.n, "bwd", ckpt)
-    kern = "bwd_pass_kernel" if args.mode == "fused" else "pg_bwd_kernel"
-    if fwd_ms.sum() > bwd_ms.sum():
-        kern = "fwd_pass_kernel" if args.mode == "fused" else "pg_gate_kernel"
-        tot_b, tot_ms, n_l = sum(fb) * nf, float(fwd_ms.sum()), len(fb) * nf
-    else:
-        tot_b, tot_ms, n_l = sum(bb) * nb, float(bwd_ms.sum()), len(bb) * nb
-    achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1e3) / 1e9 if tot_ms > 0 else None
-    traffic = traffic_record(kern, plan.kernel_source())
-    roofline = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "algorithmic_bytes_per_launch": tot_b / n_l if n_l else None,
-                "avg_launch_ms": tot_ms / n_l if n_l else None, "launches_timed": n_l,
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",
-                "fwd_ms_per_step": float(fwd_ms.sum()) / max(nf, 1), "bwd_ms_per_step": float(bwd_ms.sum()) / max(nb, 1),
-                "passes": len(desc["passes"]),
-                # HBM bytes per gate: fused passes amortise one round trip over all of a pass's gates
-                "bytes_per_gate": {"fwd": sum(fb) / len(wl.gates), "bwd": sum(bb) / len(wl.gates),
-                                   "per_gate_path_fwd": 16 * B * (1 << wl.n),
-                                   "per_gate_path_bwd": 32 * B * (1 << wl.n)},
-                "per_pass": per_pass_table(desc, fb, bb, fwd_ms, bwd_ms, nf, nb) if args.mode == "fused" else None}
+    roofline = pass_roofline(desc, B, wl, ckpt, args.mode, fwd_ms, bwd_ms, nf, nb, plan.kernel_source(), peak, peak_kind)
 
     # end to end: host inputs -> device, forward + backward, results -> host, every step
     e2e = None

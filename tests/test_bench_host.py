@@ -33,3 +33,31 @@ def test_per_pass_table():
 def test_traffic_record_needs_the_measured_kernel_program():
     assert bench.traffic_record("bwd_pass_kernel", "// some other program") is None
     assert bench.traffic_record("no_such_kernel", "") is None
+
+
+def test_pass_roofline_on_the_bench_plan():
+    # the bench's roofline object, from the real 20-qubit plan description and synthetic event times
+    import json
+    import numpy as np
+    import workloads as W
+    from paper_2404_09213_gb300 import build
+    build.build()
+    import paper_2404_09213_gb300 as q
+    wl = W.config(3)
+    plan = q.Plan(wl.gates, wl.n, k=12, checkpoint_passes=1)
+    desc = plan.describe()
+    P = len(desc["passes"])
+    fwd_ms = np.full(P, 0.2 * 3)            # 3 recorded calls of 0.2 ms per pass
+    bwd_ms = np.full(P, 0.6 * 3)
+    r = bench.pass_roofline(desc, wl.batch, wl, 1, "fused", fwd_ms, bwd_ms, 3, 3, "// not the measured program",
+                            6758.5, "measured")
+    json.dumps(r)
+    amps = wl.batch * (1 << wl.n)
+    bb = bench.algorithmic_bytes(desc, wl.batch, wl.n, "bwd", 1)
+    assert r["kernel"] == "bwd_pass_kernel" and r["launches_timed"] == 3 * P and r["traffic"] is None
+    assert abs(r["avg_launch_ms"] - 0.6) < 1e-12
+    assert abs(r["achieved"] - sum(bb) / P / 0.6e-3 / 1e9) < 1e-6
+    assert abs(r["frac"] - r["achieved"] / 6758.5) < 1e-12
+    assert r["bytes_per_gate"]["per_gate_path_fwd"] == 16 * amps
+    assert r["per_pass"]["gates"] == [len(ps["gates"]) for ps in desc["passes"]]
+    assert sum(r["per_pass"]["gates"]) == len(wl.gates)
