@@ -236,6 +236,19 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def alu_roofline(flops_per_step, fwd_ms, n_fwd, step_ms, peak_tflops, peak_source):
+    """Roofline on the FP32 ALUs of the forward pass kernels: algorithmic flops per step over their
+    event time per step (fwd_ms: per-pass times summed over n_fwd recorded calls)."""
+    P = len(fwd_ms)
+    kern_ms = float(sum(fwd_ms)) / max(n_fwd, 1)
+    ach = flops_per_step / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else None
+    return {"bound": "alu", "kernel": "fwd_pass_kernel", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": ach / peak_tflops if ach else None, "traffic": None,
+            "algorithmic_flops_per_launch": flops_per_step / P, "avg_launch_ms": kern_ms / P,
+            "launches_timed": n_fwd * P, "peak_source": peak_source,
+            "pass_kernel_share_of_step": kern_ms / step_ms if step_ms > 0 else None}
+
+
 def fp32_peak_tflops(dev_index):
     """FP32 peak derived from unit counts and clocks: SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz
     (the maximum SM clock of this GPU model)."""
@@ -519,14 +532,7 @@ def run_other(args, world, rank, local):
         # the state never leaves L2 / shared memory: a roofline on the FP32 ALUs for the pass kernel
         fwd_ms, _, nf, _ = plan.read_profile()
         plan.set_profiling(0)
-        kern_ms = float(fwd_ms.sum()) / max(nf, 1)          # pass-kernel time per step
-        fpk, fsrc = fp32_peak_tflops(local)
-        ach = c2_flops / (kern_ms / 1e3) / 1e12 if kern_ms > 0 else None
-        roofline = {"bound": "alu", "kernel": "fwd_pass_kernel", "achieved": ach, "peak": fpk, "unit": "TFLOP/s",
-                    "frac": ach / fpk if ach else None, "traffic": None,
-                    "algorithmic_flops_per_launch": c2_flops / P, "avg_launch_ms": kern_ms / P,
-                    "launches_timed": nf * P, "peak_source": fsrc,
-                    "pass_kernel_share_of_step": kern_ms / (ms / args.steps)}
+        roofline = alu_roofline(c2_flops, fwd_ms, nf, ms / args.steps, *fp32_peak_tflops(local))
     out = {"metric": metric, "value": samples * args.steps / (ms / 1e3), "unit": unit, "n_gpus": 1,
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",

@@ -61,3 +61,12 @@ def test_pass_roofline_on_the_bench_plan():
     assert r["bytes_per_gate"]["per_gate_path_fwd"] == 16 * amps
     assert r["per_pass"]["gates"] == [len(ps["gates"]) for ps in desc["passes"]]
     assert sum(r["per_pass"]["gates"]) == len(wl.gates)
+
+
+def test_alu_roofline():
+    # 3.93 GFLOP per step in 0.2 ms of pass-kernel time (two recorded calls of one pass) at an 80 TFLOP/s peak
+    r = bench.alu_roofline(3.93e9, [0.4], 2, 0.25, 80.0, "derived")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["launches_timed"] == 2
+    assert abs(r["achieved"] - 3.93e9 / 0.2e-3 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 80.0) < 1e-12
+    assert abs(r["pass_kernel_share_of_step"] - 0.8) < 1e-12
