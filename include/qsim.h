@@ -40,9 +40,9 @@ enum { QSIM_RX = 0, QSIM_RY = 1, QSIM_RZ = 2, QSIM_H = 3, QSIM_X = 4, QSIM_CNOT 
 /* One gate: {type, targets, controls, param index}.
  *   single-qubit gates: targets[0] = qubit, others -1.
  *   CNOT: controls[0] = control, targets[0] = target.   CZ: controls[0], targets[0] (symmetric).
- *   param >= 0: index into the trainable parameter vector (shared by the batch);
+ *   param >= 0: index into the trainable parameter vector (shared by the batch), below 2^24;
  *   param == -1: no parameter (H, X, CNOT, CZ);
- *   param <= -2: encoded input, column (-2 - param) of the (B, n_inputs) input matrix. */
+ *   param <= -2: encoded input, column (-2 - param) of the (B, n_inputs) input matrix, below 2^20. */
 typedef struct {
   int32_t type;
   int32_t targets[2];

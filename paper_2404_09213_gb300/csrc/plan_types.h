@@ -14,6 +14,8 @@ namespace qsim {
 constexpr int kMaxTileBits = 16;   // k <= 16
 constexpr int kMaxR = 5;           // at most 2^5 amplitudes per thread and array
 constexpr int kMaxQubits = 34;
+constexpr int kMaxParams = 1 << 24;   // trainable parameter indices per circuit
+constexpr int kMaxInputs = 1 << 20;   // encoded input columns per circuit
 // Rotations and Hadamards run unnormalised inside a pass (a tangent or cotangent coefficient, the
 // factored cos / sin / 1/sqrt(2) applied later), so each one grows the tile's values by at most
 // sqrt(2). A K_SCALE op after every kRescaleEvery of them applies the factors gathered so far: the

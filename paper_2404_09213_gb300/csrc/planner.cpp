@@ -58,6 +58,12 @@ int validate_gates(const qsim_gate* g, int n_gates, int n, std::vector<Gate>& ou
         err = buf;
         return QSIM_ERR_PARAM;
       }
+      // the kernels index params[param] and inputs[b][-2 - param]: refuse indices no real buffer has
+      if (x.param >= kMaxParams || (x.param <= -2 && (int64_t)-2 - x.param >= kMaxInputs)) {
+        snprintf(buf, sizeof buf, "gate %d: param=%d outside [-2 - %d, %d)", i, x.param, kMaxInputs - 1, kMaxParams);
+        err = buf;
+        return QSIM_ERR_PARAM;
+      }
       if (x.param >= 0) n_params = std::max(n_params, x.param + 1);
       else n_inputs = std::max(n_inputs, -2 - x.param + 1);
     } else if (x.param != -1) {

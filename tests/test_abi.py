@@ -56,6 +56,9 @@ def test_struct_sizes_match_header(q):
     ([W.gate(W.RY, (0,))], 2, -3),                               # rotation without parameter
     ([W.gate(W.H, (0,), param=3)], 2, -3),                       # fixed gate with a parameter
     ([W.gate(W.RX, (0, 1), param=0)], 2, -2),                    # stray second target
+    ([W.gate(W.RZ, (0,), param=1 << 24)], 2, -3),                # parameter index beyond any buffer
+    ([W.gate(W.RZ, (0,), param=-2 - (1 << 20))], 2, -3),         # input column beyond any buffer
+    ([W.gate(W.RZ, (0,), param=-(1 << 31))], 2, -3),
     ([], 0, -9),                                                 # n_qubits out of range
     ([], 35, -9),
 ])
