@@ -150,7 +150,9 @@ int qsim_tile_index_map(qsim_plan_t plan, int32_t pass, int64_t tile, int64_t* h
  * Intermediate states live in the plan's workspace (and checkpoints); only the last pass writes
  * d_states. The plan remembers d_params, d_inputs and d_states for the backward: they must stay
  * unchanged until qsim_backward has been enqueued. Workspace is (re)allocated on `stream` when the
- * batch size changes. */
+ * batch size changes. Errors: QSIM_ERR_ARG for NULL or misaligned buffers, QSIM_ERR_UNSUPPORTED when
+ * batch x 2^n exceeds 2^40 amplitudes (also for qsim_expval_z and qsim_multi_forward), QSIM_ERR_OOM
+ * when the workspace does not fit. */
 int qsim_forward(qsim_plan_t plan, const void* d_params, const void* d_inputs, int32_t batch,
                  const void* d_init, void* d_states, double* d_z, void* stream);
 

@@ -474,6 +474,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   g_err.clear();
   if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
   if (batch < 0) return fail(QSIM_ERR_ARG, "batch < 0");
+  if (batch > (kMaxAmplitudes >> p->s.n)) return fail(QSIM_ERR_UNSUPPORTED, "batch x 2^n_qubits above 2^40 amplitudes");
   if (batch > 0 && (!d_states || !d_z)) return fail(QSIM_ERR_ARG, "d_states and d_z are required");
   if (p->s.n_params > 0 && !d_params) return fail(QSIM_ERR_ARG, "d_params is NULL but the circuit has parameters");
   if (p->s.n_inputs > 0 && batch > 0 && !d_inputs) return fail(QSIM_ERR_ARG, "d_inputs is NULL but the circuit has inputs");
@@ -696,6 +697,7 @@ int qsim_expval_z(const void* d_states, int32_t batch, int32_t n, int32_t dtype,
   if (n < 1 || n > kMaxQubits) return fail(QSIM_ERR_UNSUPPORTED, "n_qubits outside [1, 34]");
   if (batch < 0) return fail(QSIM_ERR_ARG, "batch < 0");
   if (dtype != QSIM_C64 && dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "bad dtype");
+  if (batch > (kMaxAmplitudes >> n)) return fail(QSIM_ERR_UNSUPPORTED, "batch x 2^n_qubits above 2^40 amplitudes");
   if (batch == 0) return QSIM_OK;
   if (!d_states || !d_z) return fail(QSIM_ERR_ARG, "NULL buffer");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -526,6 +526,8 @@ int qsim_multi_forward(qsim_multi_t m, const void* d_params, const void* d_input
   qsim::set_last_error("");
   if (!m) return mfail(QSIM_ERR_ARG, "plan is NULL");
   if (batch < 1) return mfail(QSIM_ERR_ARG, "batch must be >= 1");
+  for (const Schedule& s : m->sch)
+    if (batch > (kMaxAmplitudes >> s.n)) return mfail(QSIM_ERR_UNSUPPORTED, "batch x 2^n_qubits above 2^40 amplitudes");
   if (!d_states || !d_z) return mfail(QSIM_ERR_ARG, "d_states and d_z are required");
   if (m->n_params > 0 && !d_params) return mfail(QSIM_ERR_ARG, "d_params is NULL");
   if (m->n_cols > 0 && !d_inputs) return mfail(QSIM_ERR_ARG, "d_inputs is NULL");

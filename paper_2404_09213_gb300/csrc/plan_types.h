@@ -16,6 +16,7 @@ constexpr int kMaxR = 5;           // at most 2^5 amplitudes per thread and arra
 constexpr int kMaxQubits = 34;
 constexpr int kMaxParams = 1 << 24;   // trainable parameter indices per circuit
 constexpr int kMaxInputs = 1 << 20;   // encoded input columns per circuit
+constexpr long long kMaxAmplitudes = 1LL << 40;   // batch x 2^n of one call (8 TiB of complex64)
 // Rotations and Hadamards run unnormalised inside a pass (a tangent or cotangent coefficient, the
 // factored cos / sin / 1/sqrt(2) applied later), so each one grows the tile's values by at most
 // sqrt(2). A K_SCALE op after every kRescaleEvery of them applies the factors gathered so far: the

@@ -123,3 +123,16 @@ def test_landscape_and_autotune_reject_bad_arguments_on_the_host(q):
     k = (ctypes.c_int32 * 1)()
     rc = L.qsim_multi_autotune(None, None, None, 0, 4, 1, 1, None, k, None)
     assert rc == -1
+
+
+def test_batch_times_state_size_is_bounded(q):
+    # batch x 2^n above 2^40 amplitudes is refused before any device work (no GPU needed)
+    import ctypes
+    from paper_2404_09213_gb300 import _lib
+    L = _lib.lib()
+    p = q.Plan(W.ring_ansatz(34, 1), 34)
+    dummy = ctypes.c_void_p(256)
+    rc = L.qsim_forward(p._h, dummy, dummy, 1 << 7, None, dummy, dummy, None)
+    assert rc == -9 and "2^40" in L.qsim_last_error().decode()
+    rc = L.qsim_expval_z(dummy, 1 << 7, 34, 0, dummy, None)
+    assert rc == -9
