@@ -245,7 +245,6 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     for (int p = 0; p < lp.n_tbits; p++) o << "      case " << (int)lp.tbit[p] << ": return " << -1 - p << ";\n";
     o << "      default: return 0;\n    }\n  }\n";
   }
-  // global offset of the thread's base element and of the register bits, for a phase
   // global offset of the thread's base element and of the register bits, for a phase, in the layout
   // the pass reads (out = false: a.L, c.base) or writes (out = true: a.Lo, c.base_out)
   auto gaddr = [&](const DevPhase& ph, const std::string& var, bool out) {
