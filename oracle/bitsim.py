@@ -1,5 +1,7 @@
 """Brute-force per-basis-index simulator (pure Python loops) for pinning the oracle on tiny inputs.
 
+Test infrastructure only (the FP64 oracle): the library's product path never imports it.
+
 It applies each gate by walking every amplitude index and reading the target/control bits with
 integer shifts (bit of qubit q = (x >> (n-1-q)) & 1, MSb-0 as in Sec. "Symbols"). It shares no
 array reshaping or Kronecker code with ``kron`` / ``strided``; only the 2x2 matrices are reused.

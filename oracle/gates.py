@@ -1,5 +1,7 @@
 """Gate matrices and their Kronecker expansion (Sec. "Gate Matrix Caching").
 
+Test infrastructure only (the FP64 oracle): the library's product path never imports it.
+
 Conventions (Secs. "Symbols" and "Concept of Shapes" of the paper): qubit w is the w-th most significant bit of an
 amplitude index, so on W qubits a single-qubit gate G on qubit w is I_{2^w} (x) G (x) I_{2^(W-1-w)}.
 The printed exponent in Eq. 2 (I_{2^(W-w)} after the gate) would give dimension 2^(W+1); the reading

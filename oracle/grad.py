@@ -1,5 +1,7 @@
 """Loss and reference gradients (Sec. "Hybrid Machine Learning": parameter-shift rule and backpropagation).
 
+Test infrastructure only (the FP64 oracle): the library's product path never imports it.
+
 L = sum_{b,i} g_{b,i} <Z_i>_b. Trainable parameters are shared by the batch, so dL/dparams sums
 over samples; encoded inputs belong to one sample each, so dL/dinputs is per sample.
 

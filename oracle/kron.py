@@ -1,5 +1,7 @@
 """Oracle-K: dense Kronecker-expanded simulation (Sec. "Gate Matrix Caching", Eq. 2).
 
+Test infrastructure only (the FP64 oracle): the library's product path never imports it.
+
 Each gate is expanded to its full 2^W x 2^W matrix and applied to every state by a dense product,
 in circuit order. Gates whose angle is shared by the whole batch are applied to all samples at once
 ((2^W x 2^W) @ (2^W x B)); gates driven by an input column get one matrix per sample. Practical up

@@ -1,5 +1,7 @@
 """Measurement layer (Sec. "Hybrid Machine Learning"): Pauli-Z expectation values of every qubit.
 
+Test infrastructure only (the FP64 oracle): the library's product path never imports it.
+
 <Z_i>_b = sum_x |psi_b[x]|^2 (1 - 2 bit_i(x)), where bit_i(x) is the i-th most significant of the n
 index bits (MSb-0, Sec. "Symbols"), i.e. (x >> (n-1-i)) & 1.
 """

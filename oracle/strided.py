@@ -1,5 +1,7 @@
 """Oracle-S: per-gate strided simulation by reshaping (Sec. "Concept of Shapes").
 
+Test infrastructure only (the FP64 oracle): the library's product path never imports it.
+
 The paper applies a single-qubit gate G on qubit w by viewing the state as (..., 2, ...) with the
 w-th axis separate and multiplying by G over that axis. Here the batched state (B, 2^W) is viewed as
 (B, 2^w, 2, 2^(W-1-w)) and the middle axis is contracted with G. Controlled gates act on the
