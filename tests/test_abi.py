@@ -136,3 +136,22 @@ def test_batch_times_state_size_is_bounded(q):
     assert rc == -9 and "2^40" in L.qsim_last_error().decode()
     rc = L.qsim_expval_z(dummy, 1 << 7, 34, 0, dummy, None)
     assert rc == -9
+
+
+def test_multi_plan_host_side(q):
+    # planning several circuits and their buffer offsets need no GPU; errors name the circuit
+    circuits = [(W.ring_ansatz(3, 1), 3), (W.hea_cz_ansatz(5, 2), 5), ([W.gate(W.H, (0,))], 1)]
+    mp = q.MultiPlan(circuits)
+    off = mp.offsets(4)
+    n_par = [W.count_params(g) for g, _ in circuits]
+    n_in = [W.count_inputs(g) for g, _ in circuits]
+    assert list(off["params"]) == list(np.cumsum([0] + n_par))
+    assert list(off["inputs"]) == list(4 * np.cumsum([0] + n_in))
+    assert list(off["states"]) == list(4 * np.cumsum([0] + [2 ** n for _, n in circuits]))
+    assert list(off["z"]) == list(4 * np.cumsum([0] + [n for _, n in circuits]))
+    with pytest.raises(q.QsimError, match="circuit 1"):
+        q.MultiPlan([(W.ring_ansatz(3, 1), 3), ([W.gate(W.RX, (7,), param=0)], 3)])
+    with pytest.raises(q.QsimError, match="30 qubits"):
+        q.MultiPlan([(W.ring_ansatz(31, 1), 31)])
+    with pytest.raises(q.QsimError):
+        q.MultiPlan(circuits, ks=[4, 0, 1])                      # per-circuit k outside [1, max]
