@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--checkpoint-passes", type=int, default=1,
                     help="store the state every this many forward passes (1: every pass, so backward passes "
                          "read stored states instead of writing uncomputed ones; 0: none)")
+    ap.add_argument("--pauli-frame", action="store_true",
+                    help="fused passes run the tangent form of every rotation only (cotangent Paulis in a frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default="")
@@ -284,11 +286,11 @@ def run_ours(args, world, rank, local):
     k, autotune = args.k, None
     if args.mode == "fused" and k == 0:   # tile size from the library's autotuner (untimed setup)
         k, ms = q.autotune(wl.gates, wl.n, wl.batch, reps=2, contiguous_bits=args.contiguous_bits,
-                           checkpoint_passes=args.checkpoint_passes)
+                           checkpoint_passes=args.checkpoint_passes, pauli_frame=int(args.pauli_frame))
         autotune = {"k_candidates": [10, 11, 12], "ms_per_fwd_bwd": ms, "chosen_k": k}
     ckpt = args.checkpoint_passes if args.mode == "fused" else 0
     plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits,
-                  checkpoint_passes=ckpt)
+                  checkpoint_passes=ckpt, pauli_frame=args.pauli_frame and args.mode == "fused")
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
     x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
@@ -376,6 +378,7 @@ def run_ours(args, world, rank, local):
                       "precision": "complex64 state, FP32 arithmetic; <Z> and gradient sums FP32 within a tile, "
                                    "FP64 across tiles and samples",
                       "checkpoint_passes": ckpt, "checkpoints": plan.info()["n_checkpoints"],
+                      "pauli_frame": bool(args.pauli_frame and args.mode == "fused"),
                       "workspace_bytes": plan.info()["workspace_bytes"],
                       "contiguous_bits": desc["c"],
                       "l2": "inputs larger than L2: 512 MiB state per step (L2 129 MB), no flush needed",
@@ -484,7 +487,7 @@ def run_other(args, world, rank, local):
     else:
         wl = W.config(2)
         B = wl.batch
-        plan = q.Plan(wl.gates, wl.n, mode=args.mode)
+        plan = q.Plan(wl.gates, wl.n, mode=args.mode, pauli_frame=args.pauli_frame and args.mode == "fused")
         p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
         x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
         states = torch.empty((B, 1 << wl.n), dtype=torch.complex64, device=dev)

@@ -94,6 +94,12 @@ typedef struct {
                                 k >= 2 * contiguous_bits + 2, but each pass holds more gates and phases);
                                 0 (default): the contiguous_bits lowest bits hold the same qubits in every
                                 pass. Multi-circuit plans always keep them fixed */
+  int32_t pauli_frame;       /* 1: every rotation runs the tangent form only; a cotangent-form rotation equals the
+                                tangent form with coefficient -cot(theta/2) followed by -iP, and those Paulis are
+                                carried per sample as a Pauli frame F (stored states are F^dag times the true
+                                state; the returned states have F applied). Fused single-circuit plans only.
+                                0 (default): both forms, chosen per rotation and sample at run time */
+  int32_t reserved;          /* must be 0 */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
 } qsim_plan_opts;
 
@@ -322,6 +328,13 @@ int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n
                         const qsim_plan_opts* opts, int32_t* h_k, void* stream);
 
 void qsim_plan_destroy(qsim_plan_t plan);
+
+/* Test hook (host only): the Pauli-frame walk of pauli_frame plans over one op list. types / q0 (target)
+ * / q1 (control, -1 for single-qubit gates) as in qsim_gate, cot[i] = 1 for a rotation in the cotangent
+ * form. Writes sigma[i] = -1 where the frame anticommutes with rotation i's Pauli (else +1) and the final
+ * frame F = i^k prod_q X_q^(x bit q) Z_q^(z bit q). QSIM_ERR_ARG on NULL arguments. */
+int qsim_frame_walk_host(const int32_t* types, const int32_t* q0, const int32_t* q1, const uint8_t* cot,
+                         int32_t n_ops, int8_t* sigma, uint64_t* x, uint64_t* z, int32_t* k);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* qsim_last_error(void);

@@ -57,7 +57,7 @@ class Plan:
 
     def __init__(self, gates, n_qubits, *, dtype="c64", mode="fused", k=0, contiguous_bits=0,
                  checkpoint_passes=0, mem_budget_bytes=0, sample_block=0, bwd_reg_bits=0,
-                 fwd_reg_bits=0, weight_remap=False, max_regs=0, rotate_low_bits=False):
+                 fwd_reg_bits=0, weight_remap=False, max_regs=0, rotate_low_bits=False, pauli_frame=False):
         L = _lib.lib()
         self.gates = list(gates)
         self.n = int(n_qubits)
@@ -77,6 +77,7 @@ class Plan:
         opts.weight_remap = 1 if weight_remap else 0
         opts.max_regs = max_regs
         opts.rotate_low_bits = 1 if rotate_low_bits else 0
+        opts.pauli_frame = 1 if pauli_frame else 0
         h = ctypes.c_void_p()
         arr = gate_structs(self.gates)
         _lib.check(L.qsim_plan(arr, len(self.gates), self.n, ctypes.byref(opts), ctypes.byref(h)))

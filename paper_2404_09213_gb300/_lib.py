@@ -30,6 +30,7 @@ class QsimPlanOpts(ctypes.Structure):
                 ("sample_block", ctypes.c_int32), ("bwd_reg_bits", ctypes.c_int32),
                 ("fwd_reg_bits", ctypes.c_int32), ("weight_remap", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("max_regs", ctypes.c_int32), ("rotate_low_bits", ctypes.c_int32),
+                ("pauli_frame", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_int64)]
 
 
@@ -107,6 +108,9 @@ SIGNATURES = {
     "qsim_multi_set_test_hooks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
     "qsim_multi_destroy": (None, [ctypes.c_void_p]),
     "qsim_plan_destroy": (None, [ctypes.c_void_p]),
+    "qsim_frame_walk_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32)]),
     "qsim_last_error": (ctypes.c_char_p, []),
 }
 

@@ -53,6 +53,8 @@ struct qsim_plan_s {
   JitPlan jit;
   int32_t* d_gate_type = nullptr;
   int32_t* d_gate_param = nullptr;
+  int32_t* d_gate_q0 = nullptr;   // target qubit of every gate (Pauli frame walk)
+  int32_t* d_gate_q1 = nullptr;   // control qubit (-1 for single-qubit gates)
   int32_t* d_exec_gates = nullptr;
   int32_t* d_exec_begin = nullptr;
   int32_t* d_occ_gate = nullptr;
@@ -78,6 +80,14 @@ struct qsim_plan_s {
   double* G = nullptr;
   void* W = nullptr;
   void* Lam = nullptr;
+  // Pauli frame (pauli_frame plans): the last pass's output in the stored representation F^dag (true
+  // state), the frame signs and final frames, and the loss weights with the frame's signs
+  void* S_end = nullptr;
+  int8_t* sigma = nullptr;
+  uint64_t* frame_x = nullptr;
+  uint64_t* frame_z = nullptr;
+  int32_t* frame_k = nullptr;
+  double* gsign = nullptr;
   std::vector<void*> ckpt;
   int64_t ws_bytes = 0;
   // saved forward context
@@ -141,9 +151,15 @@ struct qsim_plan_s {
   int64_t state_bytes(int B_) const { return (int64_t)B_ * ((int64_t)1 << s.n) * el; }
 
   void free_ws() {
-    void* ptrs[] = {coef, form, cfp_f, fmp_f, cfp_b, fmp_b, scale_f, scale_b, gm, zpart, gpart, G, W, Lam};
+    void* ptrs[] = {coef, form, cfp_f, fmp_f, cfp_b, fmp_b, scale_f, scale_b, gm, zpart, gpart, G, W, Lam,
+                    S_end, sigma, frame_x, frame_z, frame_k, gsign};
     for (void* p : ptrs)
       if (p) cudaFree(p);
+    S_end = nullptr;
+    sigma = nullptr;
+    frame_x = frame_z = nullptr;
+    frame_k = nullptr;
+    gsign = nullptr;
     for (void* p : ckpt)
       if (p) cudaFree(p);
     coef = cfp_f = cfp_b = nullptr;
@@ -158,7 +174,7 @@ struct qsim_plan_s {
   void free_all() {
     free_ws();
     destroy_events();
-    void* ptrs[] = {d_gate_type, d_gate_param, d_exec_gates, d_exec_begin, d_exec_gates_b,
+    void* ptrs[] = {d_gate_type, d_gate_param, d_gate_q0, d_gate_q1, d_exec_gates, d_exec_begin, d_exec_gates_b,
                     d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Qnl_last};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -169,10 +185,12 @@ struct qsim_plan_s {
   int upload_schedule() {
     if (uploaded) return QSIM_OK;
     cudaError_t e = cudaSuccess;
-    std::vector<int32_t> gtype, gparam, exec, exec_begin, exec_b, exec_begin_b;
+    std::vector<int32_t> gtype, gparam, gq0, gq1, exec, exec_begin, exec_b, exec_begin_b;
     for (auto& g : s.gates) {
       gtype.push_back(g.type);
       gparam.push_back(g.param);
+      gq0.push_back(g.t0);
+      gq1.push_back(g.c0);
     }
     for (auto& pp : s.passes) {
       exec_begin.push_back((int32_t)exec.size());
@@ -217,6 +235,8 @@ struct qsim_plan_s {
     QSIM_UP(d_exec_begin_b, exec_begin_b)
     QSIM_UP(d_gate_type, gtype)
     QSIM_UP(d_gate_param, gparam)
+    QSIM_UP(d_gate_q0, gq0)
+    QSIM_UP(d_gate_q1, gq1)
     QSIM_UP(d_exec_gates, exec)
     QSIM_UP(d_exec_begin, exec_begin)
     QSIM_UP(d_occ_gate, occ_gate)
@@ -262,6 +282,11 @@ struct qsim_plan_s {
         {reinterpret_cast<void**>(&gpart), s.total_gslots * B_ * tps() * 8},
         {reinterpret_cast<void**>(&G), (int64_t)n_occ * B_ * 8},
         {&W, sb}, {&Lam, sb},
+        {&S_end, s.pauli_frame ? sb : 0}, {reinterpret_cast<void**>(&sigma), s.pauli_frame ? G_ * B_ : 0},
+        {reinterpret_cast<void**>(&frame_x), s.pauli_frame ? (int64_t)B_ * 8 : 0},
+        {reinterpret_cast<void**>(&frame_z), s.pauli_frame ? (int64_t)B_ * 8 : 0},
+        {reinterpret_cast<void**>(&frame_k), s.pauli_frame ? (int64_t)B_ * 4 : 0},
+        {reinterpret_cast<void**>(&gsign), s.pauli_frame ? (int64_t)B_ * s.n * 8 : 0},
     };
     for (auto& it : items) {
       if (it.bytes <= 0) continue;
@@ -386,10 +411,13 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   p->opts = o;
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
       o.sample_block < 0 || o.weight_remap < 0 || o.weight_remap > 2 || o.max_regs < 0 ||
-      (o.max_regs > 0 && o.max_regs < 32) || (o.rotate_low_bits != 0 && o.rotate_low_bits != 1)) {
+      (o.max_regs > 0 && o.max_regs < 32) || (o.rotate_low_bits != 0 && o.rotate_low_bits != 1) ||
+      (o.pauli_frame != 0 && o.pauli_frame != 1) || (o.pauli_frame == 1 && o.mode != QSIM_FUSED) ||
+      o.reserved != 0) {
     delete p;
     return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0..2, "
-                              "max_regs 0 or >= 32, rotate_low_bits 0 or 1");
+                              "max_regs 0 or >= 32, rotate_low_bits 0 or 1, pauli_frame 0 or 1 (fused mode), "
+                              "reserved 0");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
@@ -516,9 +544,22 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   ca.scale_f = p->scale_f;
   ca.scale_b = p->scale_b;
   ca.gm = p->gm;
+  if (s.pauli_frame) {
+    ca.gate_q0 = p->d_gate_q0;
+    ca.gate_q1 = p->d_gate_q1;
+    ca.sigma = p->sigma;
+    ca.frame_x = p->frame_x;
+    ca.frame_z = p->frame_z;
+    ca.frame_k = p->frame_k;
+  }
   if (s.gates.size() > 0 && ca.P > 0) {
     e = launch_coef(ca, s.dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "coefficient kernel");
+  } else if (s.pauli_frame) {   // no gates: the identity frame
+    e = cudaMemsetAsync(p->frame_x, 0, (size_t)batch * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->frame_z, 0, (size_t)batch * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->frame_k, 0, (size_t)batch * 4, st);
+    if (e != cudaSuccess) return cuda_fail(e, "frame reset");
   }
   const char* sf = reinterpret_cast<const char*>(p->scale_f);
   if (s.mode == QSIM_PER_GATE) {
@@ -545,7 +586,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
         // the caller's buffer.
         const int seg = p->seg_of(q);
         void* sbuf = (seg == p->n_segments - 1) ? (P_ > 1 ? p->W : d_states) : p->ckpt[seg];
-        void* out = (q == P_ - 1) ? d_states : sbuf;
+        void* out = (q == P_ - 1) ? (s.pauli_frame ? p->S_end : d_states) : sbuf;
         const void* in;
         if (q == p->seg_begin[seg]) in = (seg == 0) ? d_init : p->ckpt[seg - 1];
         else in = sbuf;
@@ -561,8 +602,13 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
       }
     }
     const DevPass& last = s.passes.back().dev;
-    e = launch_z_final(p->zpart, last.k, p->d_Qnl_last, last.n_nonlocal, last.tiles_per_sample, s.n, batch, d_z, st);
+    e = launch_z_final(p->zpart, last.k, p->d_Qnl_last, last.n_nonlocal, last.tiles_per_sample, s.n, batch, d_z, st,
+                       s.pauli_frame ? p->frame_x : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "<Z> reduction");
+    if (s.pauli_frame) {   // the returned states: F applied to the stored representation
+      e = launch_frame_fixup(p->S_end, d_states, p->frame_x, p->frame_z, p->frame_k, s.n, batch, s.dtype, st);
+      if (e != cudaSuccess) return cuda_fail(e, "frame fix-up");
+    }
   }
   p->has_fwd = true;
   if (p->calls_left(0)) p->n_fwd_calls++;
@@ -593,13 +639,18 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
     }
   } else {
     const int P_ = p->P();
+    if (s.pauli_frame) {   // lambda starts from g_{b,q} with the sign the final frame gives Z_q
+      e = launch_frame_gsign(d_grad_out, p->frame_x, s.n, B, p->gsign, st);
+      if (e != cudaSuccess) return cuda_fail(e, "frame signs");
+    }
     const int G = p->group_size(B);
     for (int b0 = 0; b0 < B; b0 += G) {
       const int nb = std::min(G, B - b0);
       for (int q = P_ - 1; q >= 0; q--) {
         const int seg = p->seg_of(q);
         const bool seg_last = (q == p->seg_begin[seg + 1] - 1);
-        const void* pin = seg_last ? ((seg == p->n_segments - 1) ? p->states : p->ckpt[seg]) : p->W;
+        const void* pend = s.pauli_frame ? p->S_end : p->states;   // the stored representation
+        const void* pin = seg_last ? ((seg == p->n_segments - 1) ? pend : p->ckpt[seg]) : p->W;
         const void* lin = (q == P_ - 1) ? nullptr : p->Lam;
         // the previous pass restarts from its checkpoint when this pass begins a segment: psi not stored
         void* pout = (q == 0 || q == p->seg_begin[seg]) ? nullptr : p->W;
@@ -609,7 +660,7 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
         ja.out = pout;
         ja.lam_in = lin;
         ja.lam_out = lout;
-        ja.grad_out = d_grad_out;
+        ja.grad_out = s.pauli_frame ? p->gsign : d_grad_out;
         ja.gpart = p->gpart;
         ja.b0 = b0;
         const int rec = p->prof_begin(1, q, st);

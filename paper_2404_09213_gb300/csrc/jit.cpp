@@ -372,7 +372,8 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       const DevOp& op = s.ops[oi];
       const int li = oi - d.op0;
       const int SA = 1 << op.a, SB = 1 << op.b;
-      std::string C = "c.cf[" + std::to_string(li) + "], c.fm[" + std::to_string(li) + "]";
+      // with a Pauli frame every rotation takes the tangent form (a literal 0 removes the other branch)
+      std::string C = "c.cf[" + std::to_string(li) + "], " + (s.pauli_frame ? std::string("0") : "c.fm[" + std::to_string(li) + "]");
       std::string call;
       std::ostringstream g;
       switch (op.kind) {

@@ -41,13 +41,29 @@ struct CoefArgs {
   const int64_t* circ_param_off;   // [C] first parameter of the circuit
   const int64_t* circ_col_off;     // [C] input columns before the circuit (per sample)
   const int32_t* circ_ninputs;     // [C]
+  // Pauli frame (all null without one): per gate its target and control qubit, per (gate, sample) the sign
+  // the frame gives the rotation's coefficient, per sample the final frame F = i^k X^x Z^z (bit q = qubit q)
+  const int32_t* gate_q0;       // [G] target qubit
+  const int32_t* gate_q1;       // [G] control qubit (-1 for single-qubit gates)
+  int8_t* sigma;                // [G * B]
+  uint64_t* frame_x;            // [B]
+  uint64_t* frame_z;            // [B]
+  int32_t* frame_k;             // [B]
 };
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st);
+
+// ---- Pauli frame: the returned states F S from the stored representation S (out of place), and the
+// loss weights g_{b,q} with the sign (-1)^x_q the frame gives Z_q (lambda starts from them)
+cudaError_t launch_frame_fixup(const void* S, void* out, const uint64_t* fx, const uint64_t* fz, const int32_t* fk,
+                               int n, int B, int dtype, cudaStream_t st);
+cudaError_t launch_frame_gsign(const double* grad_out, const uint64_t* fx, int n, int B, double* out,
+                               cudaStream_t st);
 
 // ---- <Z> final reduction from per-tile partials: z[b][q]
 // d_Q_and_nonlocal: logical qubit of every tile bit, then of every tile-index bit, of the last pass
 cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Q_and_nonlocal, int n_nonlocal,
-                           int64_t tiles_per_sample, int n, int B, double* z, cudaStream_t st);
+                           int64_t tiles_per_sample, int n, int B, double* z, cudaStream_t st,
+                           const uint64_t* frame_x = nullptr);
 
 // ---- gradient reductions
 struct GradReduceArgs {

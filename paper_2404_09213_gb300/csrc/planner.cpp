@@ -335,6 +335,7 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
   s.dtype = o.dtype;
   s.mode = o.mode;
   s.max_regs = o.max_regs;
+  s.pauli_frame = o.pauli_frame == 1 && o.mode == QSIM_FUSED;
   int k = o.k > 0 ? o.k : 12;
   int c = o.contiguous_bits > 0 ? o.contiguous_bits : 4;
   if (k > kMaxTileBits) {

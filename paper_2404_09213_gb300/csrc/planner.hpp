@@ -27,6 +27,7 @@ struct PassPlan {
 struct Schedule {
   int n = 0, k = 0, R = 0, Rb = 0, c = 0, dtype = 0, mode = 0;
   int max_regs = 0;                  // register cap of the pass kernels (0: none)
+  bool pauli_frame = false;          // rotations run the tangent form only (cotangent Paulis in a frame)
   int n_params = 0, n_inputs = 0;
   std::vector<Gate> gates;
   std::vector<PassPlan> passes;

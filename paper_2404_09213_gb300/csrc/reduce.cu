@@ -115,6 +115,11 @@ __global__ void coef_pass_kernel(CoefArgs a) {
         v = coef[gi];
         f = a.form[gi];
         fac = a.gm[gi];
+        if (a.sigma) {   // Pauli frame: tangent form, coefficient sigma * tan or -sigma * cot
+          const T sg = (T)a.sigma[gi];
+          v = f ? -sg * v : sg * v;
+          f = 0;
+        }
       } else if (ty == QSIM_H) {
         fac = kH;
       }
@@ -150,6 +155,12 @@ __global__ void coef_pass_kernel(CoefArgs a) {
         f = a.form[gi];
         v = -coef[gi];   // the inverse rotation
         fac = f ? -a.gm[gi] : a.gm[gi];
+        if (a.sigma) {   // Pauli frame: the negated tangent-form coefficient; cos or sin as it is
+          const T sg = (T)a.sigma[gi];
+          v = f ? sg * coef[gi] : -sg * coef[gi];
+          fac = a.gm[gi];
+          f = 0;
+        }
       } else if (ty == QSIM_H) {
         fac = kH;
       }
@@ -158,7 +169,7 @@ __global__ void coef_pass_kernel(CoefArgs a) {
     const double r = scan_chunk(fac, g == -1, sb, rprev);
     if (gi >= 0) {
       const double bs = (r / fac) / rprev;   // before this op: exclude its own factor
-      a.gm[gi] = bs * bs;
+      a.gm[gi] = a.sigma ? (double)a.sigma[gi] * bs * bs : bs * bs;   // the frame's sign of P
     }
     if (g == -1) v = (T)(r / rprev);
     if (g >= -1) {
@@ -169,6 +180,75 @@ __global__ void coef_pass_kernel(CoefArgs a) {
   if (lane == 0) reinterpret_cast<T*>(a.scale_b)[(int64_t)p * a.B + b] = (T)(sb.carry / sb.rlast);
 }
 
+// Pauli frame F = i^k X^x Z^z (per qubit X^x_q Z^z_q, bit q = qubit q), one op at a time in execution
+// order. A rotation returns the sign of its Pauli under F (-1 where they anticommute), and a
+// cotangent-form rotation then left-multiplies F by -iP; H, X, CNOT and CZ conjugate F. Compiled for the
+// device (frame_walk_kernel) and the host (qsim_frame_walk_host, a test hook).
+struct Frame {
+  uint64_t x = 0, z = 0;
+  int k = 0;
+};
+
+__host__ __device__ inline int frame_step(Frame& f, int ty, int q, int c, int cot) {
+  const uint64_t bq = 1ull << q;
+  const int xq = (int)((f.x >> q) & 1u), zq = (int)((f.z >> q) & 1u);
+  int sigma = 1;
+  if (ty <= QSIM_RZ) {
+    const int anti = ty == QSIM_RX ? zq : ty == QSIM_RZ ? xq : (xq ^ zq);
+    sigma = anti ? -1 : 1;
+    if (cot) {
+      if (ty == QSIM_RZ) {
+        f.z ^= bq;
+        f.k += 2 * xq;
+      } else if (ty == QSIM_RX) {
+        f.x ^= bq;
+      } else {
+        f.x ^= bq;
+        f.z ^= bq;
+        f.k += 1 + 2 * xq;
+      }
+      f.k += 3;   // the factor -i
+    }
+  } else if (ty == QSIM_H) {   // X <-> Z, XZ -> -XZ
+    if (xq & zq) f.k += 2;
+    if (xq != zq) {
+      f.x ^= bq;
+      f.z ^= bq;
+    }
+  } else if (ty == QSIM_X) {   // Z -> -Z
+    if (zq) f.k += 2;
+  } else if (ty == QSIM_CNOT) {   // control c, target q: X_c -> X_c X_q, Z_q -> Z_c Z_q
+    if ((f.x >> c) & 1u) f.x ^= bq;
+    if (zq) f.z ^= 1ull << c;
+  } else if (ty == QSIM_CZ) {   // X_q -> X_q Z_c, X_c -> Z_q X_c
+    const int xc = (int)((f.x >> c) & 1u);
+    if (xq & xc) f.k += 2;
+    if (xq) f.z ^= 1ull << c;
+    if (xc) f.z ^= bq;
+  }
+  f.k &= 3;
+  return sigma;
+}
+
+// one thread per sample over every op of every pass in execution order
+__global__ void frame_walk_kernel(CoefArgs a) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  Frame f;
+  for (int e = a.exec_begin[0]; e < a.exec_begin[a.P]; e++) {
+    const int g = a.exec_gates[e];
+    if (g < 0) continue;   // rescale op
+    const int ty = a.gate_type[g];
+    const int64_t gi = (int64_t)g * a.B + b;
+    const int cot = ty <= QSIM_RZ ? a.form[gi] : 0;
+    const int sg = frame_step(f, ty, a.gate_q0[g], a.gate_q1[g], cot);
+    if (ty <= QSIM_RZ) a.sigma[gi] = (int8_t)sg;
+  }
+  a.frame_x[b] = f.x;
+  a.frame_z[b] = f.z;
+  a.frame_k[b] = f.k;
+}
+
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
   const int64_t ng = (int64_t)a.G * a.B, np = (int64_t)a.P * a.B;
   if (np == 0) return cudaSuccess;
@@ -177,6 +257,10 @@ cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
   if (ng > 0) {
     if (dtype == QSIM_C128) coef_gate_kernel<double><<<bg, tg, 0, st>>>(a);
     else coef_gate_kernel<float><<<bg, tg, 0, st>>>(a);
+    g_kernel_launches++;
+  }
+  if (a.sigma) {   // the frame's signs must exist before the coefficients are packed
+    frame_walk_kernel<<<(unsigned)((a.B + 63) / 64), 64, 0, st>>>(a);
     g_kernel_launches++;
   }
   if (dtype == QSIM_C128) coef_pass_kernel<double><<<bp, tp, 0, st>>>(a);
@@ -203,7 +287,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // z[b][q] from per-tile partials: block per (b, q).
 __global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Qnl, int n_nonlocal, int64_t tps,
-                               int n, int B, double* z) {
+                               int n, int B, double* z, const uint64_t* frame_x) {
   __shared__ double sh[32];
   const int b = blockIdx.x / n, q = blockIdx.x - (blockIdx.x / n) * n;
   int tbit = -1, nlbit = -1;   // qubit q is tile bit tbit or tile-index bit nlbit of the last pass
@@ -218,16 +302,80 @@ __global__ void z_final_kernel(const double* zpart, int k, const uint8_t* Qnl, i
     else acc += ((t >> nlbit) & 1) ? -row[k] : row[k];
   }
   acc = block_sum(acc, sh);
+  if (frame_x && ((frame_x[b] >> q) & 1u)) acc = -acc;   // F^dag Z_q F = -Z_q where F holds X or Y on q
   if (threadIdx.x == 0) z[(int64_t)b * n + q] = acc;
 }
 
 cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Qnl, int n_nonlocal, int64_t tps, int n,
-                           int B, double* z, cudaStream_t st) {
+                           int B, double* z, cudaStream_t st, const uint64_t* frame_x) {
   if ((int64_t)B * n == 0) return cudaSuccess;
   // a block per (sample, qubit) over the sample's tiles: one warp when there are few (a one-pass
   // circuit has a single tile per sample)
   const int thr = tps >= 256 ? 256 : 32;
-  z_final_kernel<<<(unsigned)(B * n), thr, 0, st>>>(zpart, k, d_Qnl, n_nonlocal, tps, n, B, z);
+  z_final_kernel<<<(unsigned)(B * n), thr, 0, st>>>(zpart, k, d_Qnl, n_nonlocal, tps, n, B, z, frame_x);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ Pauli frame: returned states, loss signs
+// out[b][i] = i^k (-1)^popc(zi & (i ^ xi)) S[b][i ^ xi], with xi, zi the frame's masks in index bits (qubit q
+// at index bit n - 1 - q)
+template <typename T>
+__global__ void frame_fixup_kernel(const T* S, T* out, const uint64_t* fx, const uint64_t* fz, const int32_t* fk,
+                                   int n, int B) {
+  const int64_t per = (int64_t)1 << n;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= per * B) return;
+  const int64_t b = id >> n, i = id & (per - 1);
+  // qubit q sits at index bit n - 1 - q: a 64-bit reversal, then a shift
+  const uint64_t xi = (uint64_t)__brevll((unsigned long long)fx[b]) >> (64 - n);
+  const uint64_t zi = (uint64_t)__brevll((unsigned long long)fz[b]) >> (64 - n);
+  const int64_t j = (int64_t)((uint64_t)i ^ xi);
+  const T* src = S + 2 * (b * per + j);
+  T re = src[0], im = src[1];
+  if (__popcll((unsigned long long)(zi & (uint64_t)j)) & 1) {
+    re = -re;
+    im = -im;
+  }
+  T r2 = re, i2 = im;   // times i^k
+  switch (fk[b] & 3) {
+    case 1: r2 = -im; i2 = re; break;
+    case 2: r2 = -re; i2 = -im; break;
+    case 3: r2 = im; i2 = -re; break;
+    default: break;
+  }
+  T* dst = out + 2 * (b * per + i);
+  dst[0] = r2;
+  dst[1] = i2;
+}
+
+cudaError_t launch_frame_fixup(const void* S, void* out, const uint64_t* fx, const uint64_t* fz, const int32_t* fk,
+                               int n, int B, int dtype, cudaStream_t st) {
+  const int64_t tot = ((int64_t)1 << n) * B;
+  if (tot == 0) return cudaSuccess;
+  const int thr = 256;
+  const unsigned blocks = (unsigned)((tot + thr - 1) / thr);
+  if (dtype == QSIM_C128)
+    frame_fixup_kernel<double><<<blocks, thr, 0, st>>>((const double*)S, (double*)out, fx, fz, fk, n, B);
+  else
+    frame_fixup_kernel<float><<<blocks, thr, 0, st>>>((const float*)S, (float*)out, fx, fz, fk, n, B);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+__global__ void frame_gsign_kernel(const double* g, const uint64_t* fx, int n, int B, double* out) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)n * B) return;
+  const int64_t b = id / n;
+  const int q = (int)(id - b * n);
+  out[id] = ((fx[b] >> q) & 1u) ? -g[id] : g[id];
+}
+
+cudaError_t launch_frame_gsign(const double* grad_out, const uint64_t* fx, int n, int B, double* out,
+                               cudaStream_t st) {
+  const int64_t tot = (int64_t)n * B;
+  if (tot == 0) return cudaSuccess;
+  frame_gsign_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(grad_out, fx, n, B, out);
   g_kernel_launches++;
   return cudaGetLastError();
 }
@@ -537,4 +685,18 @@ cudaError_t launch_landscape_gather(const double* dinputs, int P, int V, double*
 }
 
 }  // namespace qsim
+
+// Host test hook: the frame walk over one op list (types, target / control qubits, cotangent flags),
+// returning each op's sign and the final frame.
+extern "C" int qsim_frame_walk_host(const int32_t* types, const int32_t* q0, const int32_t* q1, const uint8_t* cot,
+                                    int32_t n_ops, int8_t* sigma, uint64_t* x, uint64_t* z, int32_t* k) {
+  if (n_ops < 0 || (n_ops > 0 && (!types || !q0 || !q1 || !cot || !sigma)) || !x || !z || !k) return QSIM_ERR_ARG;
+  qsim::Frame f;
+  for (int i = 0; i < n_ops; i++) sigma[i] = (int8_t)qsim::frame_step(f, types[i], q0[i], q1[i], cot[i]);
+  *x = f.x;
+  *z = f.z;
+  *k = f.k;
+  return QSIM_OK;
+}
+
 

@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(q):
 def test_struct_sizes_match_header(q):
     from paper_2404_09213_gb300 import _lib
     assert ctypes.sizeof(_lib.QsimGate) == 24
-    assert ctypes.sizeof(_lib.QsimPlanOpts) == 56
+    assert ctypes.sizeof(_lib.QsimPlanOpts) == 64
     assert ctypes.sizeof(_lib.QsimPlanInfo) == 48
 
 
@@ -98,6 +98,17 @@ def test_specialised_kernels_compile_on_host(q, gates, n, kw):
     src = p.kernel_source()
     assert src.count('extern "C" __global__') >= 2
     p.compile_kernels()
+
+
+def test_pauli_frame_kernels_take_the_tangent_form_only(q):
+    # with a Pauli frame no rotation reads its per-sample form: the cotangent branch is compiled out
+    gates = W.ring_ansatz(10, 2)
+    src0 = q.Plan(gates, 10, k=8).kernel_source()
+    src1 = q.Plan(gates, 10, k=8, pauli_frame=True).kernel_source()
+    assert "c.fm[" in src0 and "c.fm[" not in src1
+    q.Plan(gates, 10, k=8, pauli_frame=True).compile_kernels()
+    with pytest.raises(q.QsimError):
+        q.Plan(gates, 10, mode="per_gate", pauli_frame=True)
 
 
 def test_landscape_and_autotune_reject_bad_arguments_on_the_host(q):

@@ -86,6 +86,27 @@ def test_random_circuits_rotating_layouts(q, seed, n, dtype, k, c):
     _random_case(q, seed, n, dtype, "fused", k, c, rotate_low_bits=True)
 
 
+# rotations in the tangent form only, the cotangent forms' Paulis carried in a per-sample Pauli frame;
+# with and without a checkpoint every pass (the backward starts from the stored representation)
+@pytest.mark.parametrize("seed,n,dtype,k,c,ckpt", [(30, 1, "c64", 1, 1, 0), (31, 5, "c128", 4, 2, 0),
+                                                   (32, 7, "c64", 5, 3, 1), (33, 9, "c128", 7, 3, 1),
+                                                   (34, 10, "c64", 8, 4, 0), (35, 12, "c64", 12, 4, 0),
+                                                   (36, 11, "c64", 6, 2, 2), (37, 13, "c128", 11, 4, 1)])
+def test_random_circuits_pauli_frame(q, seed, n, dtype, k, c, ckpt):
+    _random_case(q, seed, n, dtype, "fused", k, c, pauli_frame=True, checkpoint_passes=ckpt)
+
+
+def test_pauli_frame_agrees_with_both_forms(q):
+    # the same 14-qubit checkpointed workload both ways: results within the complex64 tolerances
+    wl = W.config(3, n=14, batch=4)
+    a = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1)
+    b = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1, pauli_frame=True)
+    np.testing.assert_allclose(b["states"], a["states"], atol=2e-5, rtol=0)
+    np.testing.assert_allclose(b["z"], a["z"], atol=2e-5, rtol=0)
+    check_grad(b["dp"], a["dp"], "c64", "dparams, frame vs both forms")
+    check_grad(b["di"], a["di"], "c64", "dinputs, frame vs both forms")
+
+
 def _random_case(q, seed, n, dtype, mode, k, c, **kw):
     rng = np.random.default_rng(100 + seed)
     n_par, n_in, B = 7, 3, 3
@@ -213,18 +234,20 @@ def test_bitwise_deterministic(q):
     assert np.array_equal(a["z"], b["z"]) and np.array_equal(a["dp"], b["dp"]) and np.array_equal(a["di"], b["di"])
 
 
-def test_inplace_init_and_empty_circuit(q):
+@pytest.mark.parametrize("frame", [False, True])
+def test_inplace_init_and_empty_circuit(q, frame):
     n, B = 9, 2
     rng = np.random.default_rng(1)
     s = rng.normal(size=(B, 2 ** n)) + 1j * rng.normal(size=(B, 2 ** n))
     s /= np.linalg.norm(s, axis=1, keepdims=True)
     st = torch.tensor(s, dtype=torch.complex64, device="cuda")
-    plan = q.Plan([], n)
+    plan = q.Plan([], n, pauli_frame=frame)
     out, z = plan.forward(None, None, init=st, states=st)
     torch.cuda.synchronize()
     np.testing.assert_allclose(z.cpu().numpy(), oracle.expval_z(st.cpu().numpy().astype(complex), n), atol=1e-6)
+    np.testing.assert_allclose(out.cpu().numpy(), s.astype(np.complex64), atol=1e-6)
     wl = W.config(3, n=n, batch=B, layers=2)
-    plan = q.Plan(wl.gates, n, k=6)
+    plan = q.Plan(wl.gates, n, k=6, pauli_frame=frame)
     p, x, g = tensors(wl, "c64")
     st2 = torch.tensor(s, dtype=torch.complex64, device="cuda")
     out, z = plan.forward(p, x, init=st2, states=st2)

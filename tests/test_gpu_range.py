@@ -39,11 +39,11 @@ def worst_case(name, n, layers, batch, dtype, seed, hadamards=0):
     return wl
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_deep_circuit_worst_case_growth(q, dtype):
+@pytest.mark.parametrize("dtype,frame", [("c64", False), ("c128", False), ("c64", True)])
+def test_deep_circuit_worst_case_growth(q, dtype, frame):
     wl = worst_case("deep8", 8, 32, 3, dtype, seed=41, hadamards=40)   # 520 rotations + 40 H on 8 qubits
     p, x, g = tensors(wl, dtype)
-    plan = q.Plan(wl.gates, wl.n, dtype=dtype)
+    plan = q.Plan(wl.gates, wl.n, dtype=dtype, pauli_frame=frame)
     d = plan.describe()
     assert len(d["passes"]) >= 3
     assert any(op["kind"] == "scale" for ps in d["passes"] for ph in ps["phases"] for op in ph["ops"])
