@@ -107,6 +107,7 @@ SIGNATURES = {
     "qsim_multi_set_test_hooks": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
     "qsim_multi_destroy": (None, [ctypes.c_void_p]),
     "qsim_plan_destroy": (None, [ctypes.c_void_p]),
+    "qsim_landscape_clear_cache": (None, []),
     "qsim_last_error": (ctypes.c_char_p, []),
 }
 
