@@ -298,12 +298,18 @@ int qsim_export_qasm(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits
  *   d_base (n_params,), d_values (n_values,): float32 (complex64) / float64 (complex128), device.
  *   d_weights (n_qubits,) float64, device.  d_grid (n_params, n_values) float64, device, written.
  *   d_z: NULL, or (n_params * n_values, n_qubits) float64: <Z> of every evaluated vector, row k*V+v.
- * Allocates stream-ordered scratch for n_params * n_values states and returns after the work is
- * complete (it synchronises `stream`). Errors: those of qsim_plan / qsim_forward / qsim_backward,
- * QSIM_ERR_PARAM (input-encoded gates, no parameters), QSIM_ERR_OOM. */
+ * The plan (compiled kernels, workspace) and the buffers for n_params * n_values states are kept for the
+ * last 4 distinct circuits (gate list, qubits, options, n_values), so repeated sweeps skip planning,
+ * kernel loading and allocation; the work is enqueued on `stream` (asynchronous; a later call on
+ * another stream waits for it). qsim_landscape_clear_cache releases them. Errors: those of
+ * qsim_plan / qsim_forward / qsim_backward, QSIM_ERR_PARAM (input-encoded gates, no parameters),
+ * QSIM_ERR_OOM. */
 int qsim_landscape(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, const qsim_plan_opts* opts,
                    const void* d_base, const void* d_values, int32_t n_values, const double* d_weights,
                    double* d_grid, double* d_z, void* stream);
+
+/* Release the plans and buffers qsim_landscape keeps (waits for their last use). */
+void qsim_landscape_clear_cache(void);
 
 /* Tile-size autotuner (the fused pass's k). Plans the circuit with *opts for each candidate k in
  * {max_k - 2, max_k - 1, max_k} (max_k = 12 complex64, 11 complex128), runs one untimed forward

@@ -342,7 +342,16 @@ def landscape(gates, n_qubits, base, values, weights, *, dtype="c64", weight_rem
     arr = gate_structs(gates)
     _lib.check(_lib.lib().qsim_landscape(arr, len(gates), int(n_qubits), ctypes.byref(o), _ptr(base), _ptr(values),
                                          V, _ptr(weights), _ptr(grid), _ptr(zt), _stream(stream)))
+    if stream is not None and stream != torch.cuda.current_stream():
+        # the work is asynchronous on `stream`: keep the inputs' memory until it has run
+        for t in (base, values, weights, grid) + ((zt,) if z else ()):
+            t.record_stream(stream)
     return (grid, zt) if z else grid
+
+
+def landscape_clear_cache():
+    """Release the plans and buffers kept by :func:`landscape` for repeated sweeps."""
+    _lib.lib().qsim_landscape_clear_cache()
 
 
 def parse_qasm(text):

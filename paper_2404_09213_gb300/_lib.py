@@ -111,6 +111,7 @@ SIGNATURES = {
     "qsim_frame_walk_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64),
                                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32)]),
+    "qsim_landscape_clear_cache": (None, []),
     "qsim_last_error": (ctypes.c_char_p, []),
 }
 

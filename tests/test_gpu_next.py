@@ -122,3 +122,29 @@ def test_gradient_landscape_single_precision_and_errors(q):
     assert torch.isfinite(grid).all() and grid.shape == (P, 4)
     with pytest.raises(q.QsimError):
         q.landscape(W.sel_ansatz(4, 1, encode=True), 4, base, values, torch.ones(4, dtype=torch.float64, device="cuda"))
+
+
+def test_gradient_landscape_repeated_calls_reuse_the_plan(q):
+    # the same circuit swept three times (the plan and buffers are kept), once on a side stream
+    n = 3
+    gates = W.sel_ansatz(n, 2, encode=False)
+    P = W.count_params(gates)
+    rng = np.random.default_rng(8)
+    weights = rng.uniform(-1, 1, n)
+    values = np.linspace(-3.0, 3.0, 5)
+    side = torch.cuda.Stream()
+    none = np.zeros((1, 0))
+    for it in range(3):
+        base = rng.uniform(-math.pi, math.pi, P)
+        args = (gates, n, torch.tensor(base, device="cuda", dtype=torch.float64),
+                torch.tensor(values, device="cuda", dtype=torch.float64), torch.tensor(weights, device="cuda"))
+        grid = q.landscape(*args, dtype="c128", stream=side if it == 1 else None)
+        torch.cuda.synchronize()
+        grid = grid.cpu().numpy()
+        for kk in (0, P // 2, P - 1):
+            for v in (0, 4):
+                th = base.copy()
+                th[kk] = values[v]
+                dp, _ = oracle.grad_param_shift(gates, n, th, none, weights[None], param_subset=[kk])
+                assert abs(grid[kk, v] - dp[kk]) <= 1e-11, (it, kk, v)
+    q.landscape_clear_cache()
