@@ -52,9 +52,12 @@ def parse():
     ap.add_argument("--checkpoint-passes", type=int, default=1,
                     help="store the state every this many forward passes (1: every pass, so backward passes "
                          "read stored states instead of writing uncomputed ones; 0: none)")
-    ap.add_argument("--pauli-frame", action="store_true",
-                    help="fused passes run the tangent form of every rotation only (cotangent Paulis in a frame)")
+    ap.add_argument("--no-pauli-frame", action="store_true",
+                    help="fused passes pick each rotation's tangent or cotangent form per sample at run time "
+                         "(default: the tangent form only, cotangent Paulis carried in a per-sample frame)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-per-gate", action="store_true", help="skip timing the per-gate path next to the fused one")
+    ap.add_argument("--per-gate-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default="")
     return ap.parse_args()
@@ -144,30 +147,43 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle (bounded sample)
-def oracle_rate(wl, gate_budget_s=12.0, max_gates=None):
-    """Oracle-S forward of one sample over a prefix of the circuit, timed, extrapolated to the
-    fwd+bwd samples/s of the full workload (backward = parameter shift: 2 forwards per rotation)."""
+def _oracle_job(args):
+    """One sample's forward + adjoint backward through a gate list (FP64 oracle); seconds."""
+    gates, n, params, x_row, g_row = args
     import oracle
-    gates = wl.gates
-    n = wl.n
     t0 = time.perf_counter()
-    done = 0
-    psi = None
-    chunk = 10
-    while done < len(gates) and (max_gates is None or done < max_gates):
-        nxt = min(len(gates), done + chunk)
-        psi = oracle.simulate_strided(gates[done:nxt], n, wl.params, wl.inputs[:1], init=psi)
-        done = nxt
-        if time.perf_counter() - t0 > gate_budget_s:
-            break
-    dt = time.perf_counter() - t0
-    per_gate = dt / done
-    n_rot = sum(1 for g in gates if g[0] <= 2)
-    per_sample = per_gate * len(gates) * (1 + 2 * n_rot)
-    sample = (f"Oracle-S (numpy FP64, strided) forward of 1 sample through {done} of {len(gates)} gates in "
-              f"{dt:.2f} s; extrapolated to fwd+bwd per sample = {1 + 2 * n_rot} full forwards "
-              f"(1 + parameter shift of {n_rot} rotations)")
-    return 1.0 / per_sample, sample, dt
+    oracle.grad_adjoint(gates, n, params, x_row[None, :], g_row[None, :])
+    return time.perf_counter() - t0
+
+
+def _oracle_pool(cores):
+    import multiprocessing as mp
+    # spawn: the parent has used CUDA, and a forked child of such a process can hang
+    pool = mp.get_context("spawn").Pool(cores)
+    pool.map(_oracle_job, [([], 1, np.zeros(0), np.zeros(1), np.zeros(1))] * cores)   # import oracle in every worker
+    return pool
+
+
+def oracle_bounded(wl, pool, cores, per_core_s=1.5, calib=None):
+    """The FP64 oracle's forward + adjoint backward (oracle.grad_adjoint), one sample per host core in
+    parallel, over a window of the circuit sized to ~per_core_s seconds per core; extrapolated to the
+    whole circuit (its cost is a sum over gates). Returns (samples/s, wall seconds, description)."""
+    G = len(wl.gates)
+    if calib is None:
+        calib = _oracle_job((wl.gates[:20], wl.n, wl.params, wl.inputs[0], wl.grad_out[0])) / 20
+    g_t = max(4, min(G, int(per_core_s / max(calib, 1e-6))))
+    a = max(0, min(G - g_t, G // 2 - g_t // 2))   # a window from the middle: every gate kind of the circuit
+    jobs = [(wl.gates[a:a + g_t], wl.n, wl.params, wl.inputs[b % wl.batch], wl.grad_out[b % wl.batch])
+            for b in range(cores)]
+    t0 = time.perf_counter()
+    pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    rate = cores / (wall * G / g_t)
+    desc = (f"FP64 oracle (numpy, strided gates; forward + adjoint backward, oracle.grad_adjoint): {cores} samples in "
+            f"parallel processes, one per host core, each through gates {a}..{a + g_t - 1} of {G} (from |0...0>) in {wall:.2f} s wall; "
+            f"extrapolated x{G / g_t:.2f} to the whole circuit")
+    return rate, wall, desc, {"extrapolated": True, "gates_timed": g_t, "gates_total": G, "samples_timed": cores,
+                              "wall_s_timed": wall}, calib
 
 
 # ------------------------------------------------------------------ our arm
@@ -273,6 +289,14 @@ def traffic_record(kernel, kernel_source):
     return rec.get("dram_bytes_per_launch_full")
 
 
+def c3_config(wl, world):
+    """The workload as both arms name it (implementation choices are reported under "plan")."""
+    return {"workload": WORKLOAD, "n_qubits": wl.n, "batch": wl.batch, "gates": len(wl.gates),
+            "params": wl.n_params, "inputs_per_sample": wl.n_inputs,
+            "l2": "inputs larger than L2: 512 MiB state per step (L2 129 MB), no flush needed",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_ours(args, world, rank, local):
     import torch
     import workloads as W
@@ -286,11 +310,11 @@ def run_ours(args, world, rank, local):
     k, autotune = args.k, None
     if args.mode == "fused" and k == 0:   # tile size from the library's autotuner (untimed setup)
         k, ms = q.autotune(wl.gates, wl.n, wl.batch, reps=2, contiguous_bits=args.contiguous_bits,
-                           checkpoint_passes=args.checkpoint_passes, pauli_frame=int(args.pauli_frame))
+                           checkpoint_passes=args.checkpoint_passes, pauli_frame=int((not args.no_pauli_frame)))
         autotune = {"k_candidates": [10, 11, 12], "ms_per_fwd_bwd": ms, "chosen_k": k}
     ckpt = args.checkpoint_passes if args.mode == "fused" else 0
     plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits,
-                  checkpoint_passes=ckpt, pauli_frame=args.pauli_frame and args.mode == "fused")
+                  checkpoint_passes=ckpt, pauli_frame=(not args.no_pauli_frame) and args.mode == "fused")
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
     x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
@@ -369,21 +393,46 @@ def run_ours(args, world, rank, local):
         d2h = hz.numel() * 8 + hdp.numel() * 8 + hdi.numel() * 8
         e2e = {"value": replica_value(world, B, args.steps, sec * 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the plain one-kernel-per-gate path on the same GPU, same workload and precision, timed in this
+    # process (the denominator of the fused path's speed-up)
+    per_gate = None
+    if args.mode == "fused" and not args.no_per_gate:
+        pg = q.Plan(wl.gates, wl.n, dtype="c64", mode="per_gate")
+
+        def pg_step():
+            pg.forward(p, x, states=states, z=z, stream=stream)
+            pg.backward(g, dparams=dp, dinputs=di, stream=stream)
+        for _ in range(3):
+            pg_step()
+        torch.cuda.synchronize()
+        barrier(world)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.per_gate_steps):
+            pg_step()
+        f1.record(stream)
+        torch.cuda.synchronize()
+        pg_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.per_gate_steps
+        pg_value = replica_value(world, B, 1, pg_ms)
+        per_gate = {"value": value / pg_value, "unit": "x (fused samples/s over per-gate samples/s)",
+                    "per_gate_samples_per_s": pg_value, "per_gate_ms_per_step": pg_ms,
+                    "steps": args.per_gate_steps, "warmup": 3,
+                    "path": "one kernel per gate over the whole batch, same precision and reductions"}
+        del pg
+
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded splitmix64 angles and loss weights)",
-           "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": B, "gates": len(wl.gates),
-                      "params": wl.n_params, "mode": args.mode, "k": desc["k"], "autotune": autotune,
-                      "precision": "complex64 state, FP32 arithmetic; <Z> and gradient sums FP32 within a tile, "
-                                   "FP64 across tiles and samples",
-                      "checkpoint_passes": ckpt, "checkpoints": plan.info()["n_checkpoints"],
-                      "pauli_frame": bool(args.pauli_frame and args.mode == "fused"),
-                      "workspace_bytes": plan.info()["workspace_bytes"],
-                      "contiguous_bits": desc["c"],
-                      "l2": "inputs larger than L2: 512 MiB state per step (L2 129 MB), no flush needed",
-                      "parallelism": f"replicas x{world}"},
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+           "config": c3_config(wl, world),
+           "plan": {"mode": args.mode, "k": desc["k"], "autotune": autotune,
+                    "precision": "complex64 state, FP32 arithmetic; <Z> and gradient sums FP32 within a tile, "
+                                 "FP64 across tiles and samples",
+                    "checkpoint_passes": ckpt, "checkpoints": plan.info()["n_checkpoints"],
+                    "pauli_frame": bool((not args.no_pauli_frame) and args.mode == "fused"),
+                    "workspace_bytes": plan.info()["workspace_bytes"], "contiguous_bits": desc["c"]},
+           "roofline": roofline, "vs_per_gate": per_gate, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     return out, wl
 
 
@@ -487,7 +536,7 @@ def run_other(args, world, rank, local):
     else:
         wl = W.config(2)
         B = wl.batch
-        plan = q.Plan(wl.gates, wl.n, mode=args.mode, pauli_frame=args.pauli_frame and args.mode == "fused")
+        plan = q.Plan(wl.gates, wl.n, mode=args.mode, pauli_frame=(not args.no_pauli_frame) and args.mode == "fused")
         p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
         x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
         states = torch.empty((B, 1 << wl.n), dtype=torch.complex64, device=dev)
@@ -553,22 +602,29 @@ def main():
             return
         import workloads as W
         wl = W.config(3)
-        for _ in range(args.warmup):
-            oracle_rate(wl, gate_budget_s=0.0, max_gates=1)
-        rates = []
-        samples = None
+        cores = os.cpu_count() or 1
         t0 = time.perf_counter()
+        pool = _oracle_pool(cores)
+        calib = None
+        for _ in range(args.warmup):
+            _, _, _, _, calib = oracle_bounded(wl, pool, cores, per_core_s=0.2, calib=calib)
+        rates, walls = [], []
         for _ in range(args.steps):
-            r, samples, _ = oracle_rate(wl, gate_budget_s=1.0, max_gates=60)
+            r, wall, sample, ext, calib = oracle_bounded(wl, pool, cores, calib=calib)
             rates.append(r)
+            walls.append(wall)
+        pool.close()
         dt = time.perf_counter() - t0
         v = statistics.median(rates)
+        ext["steps_timed"] = args.steps
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_qubits": wl.n, "batch": wl.batch},
-                "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples},
+                "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(walls), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded splitmix64)",
+                "config": c3_config(wl, 1),
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, **ext},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "note": "each step runs the bounded sample above (ms_per_step is its wall time); value is the "
+                        "oracle's whole-circuit fwd+bwd samples/s extrapolated from it",
                 "wall_s": dt}
         print(json.dumps(line))
         return
@@ -579,8 +635,11 @@ def main():
     out, wl = run_ours(args, world, rank, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            v, sample, _ = oracle_rate(wl, gate_budget_s=12.0)
-            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+            cores = os.cpu_count() or 1
+            pool = _oracle_pool(cores)
+            v, _, sample, ext, _ = oracle_bounded(wl, pool, cores, per_core_s=max(1.0, 20.0 / cores))
+            pool.close()
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample, **ext}
         line = json.dumps(out)
         print(line)
         if args.json_out:

@@ -204,8 +204,10 @@ int64_t qsim_kernel_launches(void);
  *   sums, i.e. batch * 2^(n-12) * 13 <= 524288 for n >= 12, batch * (n+1) <= 524288 below). Larger
  *   requests return QSIM_ERR_UNSUPPORTED and leave d_z untouched; use qsim_expval_z for them.
  *   Every GPU that loads the library holds that array until the process exits.
- *   The first call on each device looks up the array's device address (a one-time set-up with that
- *   device current); make that first call before any stream capture.
+ *   The first call on each device looks up the array's device address (a set-up with that device
+ *   current, cached per device and keyed on the current context, so the first call after the
+ *   device's context is re-created, e.g. after cudaDeviceReset, looks it up again); make the first
+ *   call on a device, and the first after such a reset, before any stream capture.
  *   All calls share the array and it keeps the last call's contents: calls that can overlap on the
  *   GPU (other streams, other host threads) race and must be ordered by the caller. No entry of the
  *   array has to start at zero (each call writes every partial it reads).
@@ -247,7 +249,10 @@ int qsim_multi_forward(qsim_multi_t plan, const void* d_params, const void* d_in
 int qsim_multi_backward(qsim_multi_t plan, const double* d_grad_out, double* d_dparams, double* d_dinputs,
                         void* stream);
 
-/* Synchronize the last stream; QSIM_OK or QSIM_ERR_TIMEOUT if a queue wait gave up (status cleared). */
+/* Synchronize the last stream; QSIM_OK or QSIM_ERR_TIMEOUT if a queue wait gave up (status cleared).
+ * Once one wait has given up, every later queue job that would wait skips its work instead (its
+ * results are not valid), in this call and in later calls until this function has read and cleared
+ * the status: so a lost dependency costs one time limit, not one per pass. */
 int qsim_multi_sync_status(qsim_multi_t plan);
 
 /* Queue statistics: circuits, work items per direction, distinct specialised pass codes per direction. */

@@ -17,6 +17,8 @@ It computes, plainly and slowly, what the accelerated path computes:
                 (exact for exp(-i theta P / 2)) and by central finite differences (Sec. "Hybrid Machine Learning"
                 mentions both; the reading that the shift rule is exact, not a finite difference,
                 is recorded in the design notes).
+* ``adjoint``   the same gradient by the adjoint sweep (psi and lambda uncomputed gate by gate, FP64);
+                pinned against the exact parameter shift, it gives every gradient entry at 20+ qubits.
 * ``bitsim``    a pure-Python per-basis-index simulator used only to pin the other two on tiny inputs.
 * ``remapping`` quantum weight remapping angle = pi * tanh(weight) and its chain rule (Sec. "Additional Optimizations").
 
@@ -29,9 +31,10 @@ from .kron import simulate_kron
 from .strided import simulate_strided
 from .measure import expval_z, expval_zz
 from .grad import loss, grad_param_shift, grad_finite_diff, forward_z
+from .adjoint import grad_adjoint
 from .remapping import remap, remap_slope, forward_z_remapped, grad_remapped
 
 __all__ = ["gate_matrix_2x2", "expand_1q", "expand_controlled", "full_gate_matrix", "rx", "ry",
            "rz", "hadamard", "pauli_x", "gate_angle", "simulate_kron", "simulate_strided",
-           "expval_z", "expval_zz", "loss", "grad_param_shift", "grad_finite_diff", "forward_z",
+           "expval_z", "expval_zz", "loss", "grad_param_shift", "grad_finite_diff", "forward_z", "grad_adjoint",
            "remap", "remap_slope", "forward_z_remapped", "grad_remapped"]

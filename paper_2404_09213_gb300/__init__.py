@@ -52,12 +52,16 @@ class Plan:
     ``dtype`` "c64" (complex64 state, float32 angles) or "c128"; ``mode`` "fused" or "per_gate";
     ``k`` qubits per fused pass (default 12 for c64, 11 for c128); ``checkpoint_passes`` > 0 stores
     the forward state every that many passes for the backward to restart from; ``weight_remap``
-    feeds every trainable weight w in as the angle pi * tanh(w) (gradients are dL/dw).
+    feeds every trainable weight w in as the angle pi * tanh(w) (gradients are dL/dw);
+    ``pauli_frame`` (default: on in fused mode) runs every rotation in the tangent form and carries the
+    cotangent forms' Paulis per sample (one kernel variant per rotation instead of two).
     """
 
     def __init__(self, gates, n_qubits, *, dtype="c64", mode="fused", k=0, contiguous_bits=0,
                  checkpoint_passes=0, mem_budget_bytes=0, sample_block=0, bwd_reg_bits=0,
-                 fwd_reg_bits=0, weight_remap=False, max_regs=0, rotate_low_bits=False, pauli_frame=False):
+                 fwd_reg_bits=0, weight_remap=False, max_regs=0, rotate_low_bits=False, pauli_frame=None):
+        if pauli_frame is None:
+            pauli_frame = mode == "fused"
         L = _lib.lib()
         self.gates = list(gates)
         self.n = int(n_qubits)
@@ -301,7 +305,9 @@ def _opts(dtype, **kw):
 
 
 def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64", stream=None, **opts):
-    """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate])."""
+    """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate]).
+    Plans are timed with the Pauli frame on unless ``pauli_frame=0`` is passed (as :class:`Plan`)."""
+    opts.setdefault("pauli_frame", 1)
     o = _opts(dtype, **opts)
     ms = (ctypes.c_float * 3)()
     arr = gate_structs(gates)

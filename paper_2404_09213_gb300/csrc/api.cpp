@@ -552,14 +552,11 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
     ca.frame_z = p->frame_z;
     ca.frame_k = p->frame_k;
   }
-  if (s.gates.size() > 0 && ca.P > 0) {
+  // every pass reads its per-sample scale (and, with a Pauli frame, the frame) from the packing kernel,
+  // so it runs even for a gate list without rotations or an empty one (scales 1, identity frame)
+  if (ca.P > 0) {
     e = launch_coef(ca, s.dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "coefficient kernel");
-  } else if (s.pauli_frame) {   // no gates: the identity frame
-    e = cudaMemsetAsync(p->frame_x, 0, (size_t)batch * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->frame_z, 0, (size_t)batch * 8, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->frame_k, 0, (size_t)batch * 4, st);
-    if (e != cudaSuccess) return cuda_fail(e, "frame reset");
   }
   const char* sf = reinterpret_cast<const char*>(p->scale_f);
   if (s.mode == QSIM_PER_GATE) {

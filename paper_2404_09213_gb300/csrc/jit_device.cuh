@@ -4,7 +4,8 @@
 //
 // A CTA owns one tile: the 2^K amplitudes of one sample whose index bits outside the pass's local
 // set are fixed (the reshape to (rest, group) of the paper's Sec. "Circuit Splitting", with the group axis held
-// in shared memory). Load: 16-byte cp.async copies of runs of 2^c contiguous amplitudes. Compute:
+// in shared memory). Load: 16-byte L2-cached global loads (ld.global.cg) of runs of 2^c contiguous
+// amplitudes straight into registers. Compute:
 // register phases of 2^R amplitudes per thread; rotations use the scaled one-FMA forms
 //   RY: [[1,-t],[t,1]] / [[u,-1],[1,u]],  RX: [[1,-it],[-it,1]] / [[u,-i],[-i,u]],
 //   RZ: diag(1-it, 1+it) / diag(u-i, u+i),   t = tan(theta/2), u = cot(theta/2),
@@ -593,11 +594,13 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Thread 0: wait until the item's dependency is complete. false = gave up (status set to timeout).
+// Thread 0: wait until the item's dependency is complete. false = gave up (status set to timeout), or
+// another item has already recorded an error, so later items stop waiting at once.
 __device__ __forceinline__ bool wait_dependency(const MultiArgs& m, const Item& it) {
   if (it.wait < 0) return true;
   const unsigned long long t0 = gtimer();
   while (ld_acquire(m.counters + it.wait) < it.wait_target) {
+    if (ld_acquire(m.status) != 0) return false;
     if ((long long)(gtimer() - t0) > m.timeout_ns) {
       atomicExch(m.status, -8);
       return false;

@@ -471,6 +471,17 @@ int qsim_multi_offsets(qsim_multi_t m, int32_t batch, int64_t* po, int64_t* io, 
 
 int qsim_multi_set_test_hooks(qsim_multi_t m, int64_t withhold_item, int64_t timeout_ns) {
   if (!m) return mfail(QSIM_ERR_ARG, "plan is NULL");
+  // captured graphs hold the old values in their kernel parameters: drop them (the next call with
+  // graphs on captures again), after any replay still in flight has finished
+  if (m->gx_f || m->gx_b) {
+    cudaError_t e = cudaStreamSynchronize(m->last);
+    if (e != cudaSuccess) return mcuda(e, "stream synchronize");
+    if (m->gx_f) cudaGraphExecDestroy(m->gx_f);
+    if (m->gx_b) cudaGraphExecDestroy(m->gx_b);
+    m->gx_f = m->gx_b = nullptr;
+    m->key_f.clear();
+    m->key_b.clear();
+  }
   m->withhold = withhold_item;
   m->timeout_ns = timeout_ns > 0 ? timeout_ns : 4000000000LL;
   return QSIM_OK;

@@ -591,7 +591,33 @@ static __device__ __align__(256) double g_noalloc_zpart[kNoAllocZPartials];
 
 namespace {
 std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {};   // per device: address of g_noalloc_zpart on that device
+struct NoAllocSlot {
+  void* ctx = nullptr;   // context the address was looked up in
+  void* ptr = nullptr;   // address of g_noalloc_zpart on that device, in that context
+};
+NoAllocSlot g_noalloc[256];   // per device
+
+// The driver's cuCtxGetCurrent, reached through the runtime (no link against the driver library):
+// the current context identifies the module instance that holds the array.
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<CtxGetCurrentFn>(f);
+  }();
+  return fn;
+}
+
+void* current_ctx() {
+  void* c = nullptr;
+  CtxGetCurrentFn fn = ctx_get_current();
+  if (fn && fn(&c) != 0) c = nullptr;
+  return c;
+}
 }  // namespace
 
 cudaError_t launch_expval_z_noalloc(const void* states, int n, int B, int dtype, double* z, cudaStream_t st) {
@@ -601,17 +627,24 @@ cudaError_t launch_expval_z_noalloc(const void* states, int n, int B, int dtype,
   if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
   void* ptr = nullptr;
   {
-    // one-time set-up per device, with that device current: the host-side name of the array is
-    // not a device address, so its device address is looked up once and cached
+    // set-up per device, with that device current: the host-side name of the array is not a device
+    // address, so its device address is looked up and cached. The cache is keyed on the current
+    // context, so a context re-created after cudaDeviceReset (a new instance of the array) is looked
+    // up again instead of reusing a stale address.
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-      e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_zpart);
+    NoAllocSlot& slot = g_noalloc[dev];
+    void* ctx = current_ctx();
+    if (!slot.ptr || !ctx || ctx != slot.ctx) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_zpart);   // also makes the primary context current
       if (e != cudaSuccess) {
-        g_noalloc_ptr[dev] = nullptr;
+        slot = NoAllocSlot{};
         return e;
       }
+      slot.ptr = p;
+      slot.ctx = current_ctx();
     }
-    ptr = g_noalloc_ptr[dev];
+    ptr = slot.ptr;
   }
   return launch_expval_z(states, n, B, dtype, reinterpret_cast<double*>(ptr), z, st);
 }

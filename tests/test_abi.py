@@ -103,7 +103,7 @@ def test_specialised_kernels_compile_on_host(q, gates, n, kw):
 def test_pauli_frame_kernels_take_the_tangent_form_only(q):
     # with a Pauli frame no rotation reads its per-sample form: the cotangent branch is compiled out
     gates = W.ring_ansatz(10, 2)
-    src0 = q.Plan(gates, 10, k=8).kernel_source()
+    src0 = q.Plan(gates, 10, k=8, pauli_frame=False).kernel_source()
     src1 = q.Plan(gates, 10, k=8, pauli_frame=True).kernel_source()
     assert "c.fm[" in src0 and "c.fm[" not in src1
     q.Plan(gates, 10, k=8, pauli_frame=True).compile_kernels()

@@ -100,6 +100,46 @@ def test_c4_full_against_single_circuit_path(q):
         np.testing.assert_allclose(split(z, off["z"], c).cpu().numpy().reshape(B, w.n), zr, atol=1e-5)
 
 
+def test_c4_full_against_oracle_above_12_qubits(q):
+    # the whole 256-circuit launch, with the FP64 oracle on sample 0 of three circuits above 12 qubits:
+    # the first 22-qubit circuit of the set, the shortest 22-qubit one and the first between 15 and 18
+    # qubits. Their other samples carry no loss weight, so the circuit's batch-summed parameter gradient
+    # is sample 0's alone.
+    from oracle_pool import shift_derivatives
+    wls = W.multi_circuit_config()
+    B = 4
+    big = [i for i, w in enumerate(wls) if w.n == 22]
+    check = [big[0], min(big, key=lambda i: len(wls[i].gates)),
+             next(i for i, w in enumerate(wls) if 15 <= w.n <= 18)]
+    for c in check:
+        wls[c].grad_out = np.array(wls[c].grad_out, copy=True)
+        wls[c].grad_out[1:] = 0.0
+    mp, [(states, z, dp, di)] = run_multi(q, wls, B)
+    off = mp.offsets(B)
+    for c in check:
+        w = wls[c]
+        pr, ir = w.params.astype(np.float32).astype(float), w.inputs.astype(np.float32).astype(float)
+        psi = oracle.simulate_strided(w.gates, w.n, pr, ir[:1])
+        zc = split(z, off["z"], c).cpu().numpy().reshape(B, w.n)
+        np.testing.assert_allclose(zc[:1], oracle.expval_z(psi, w.n), atol=1e-5, rtol=0)
+        sc = split(states, off["states"], c).cpu().numpy().reshape(B, 2 ** w.n)
+        np.testing.assert_allclose(sc[:1], psi, atol=1e-5, rtol=0)
+        adp, adi = oracle.grad_adjoint(w.gates, w.n, pr, ir[:1], w.grad_out[:1])
+        gdp = split(dp, off["params"], c).cpu().numpy()
+        gdi = split(di, off["inputs"], c).cpu().numpy().reshape(B, w.n_inputs)
+        check_grad(gdp, adp, "c64", f"C4[{c}] ({w.n} qubits) dparams, sample 0")
+        check_grad(gdi[0], adi[0], "c64", f"C4[{c}] ({w.n} qubits) dinputs, sample 0")
+        assert not np.any(gdi[1:]), "samples without loss weight must get zero input gradients"
+        # a few entries by the exact shift rule: two parameters of the last layer and one input column
+        rot = [i for i, gt in enumerate(w.gates) if gt[3] >= 0]
+        enc = [i for i, gt in enumerate(w.gates) if gt[3] <= -2]
+        d = shift_derivatives(w.gates, w.n, pr, ir[:1], w.grad_out[:1], [rot[-1], rot[-2], enc[w.n // 2]])
+        for i, v in d.items():
+            ref = v[0]
+            got = gdp[w.gates[i][3]] if w.gates[i][3] >= 0 else gdi[0, -2 - w.gates[i][3]]
+            assert abs(got - ref) <= 1e-4 * np.abs(adp).max() + 1e-7, (c, i, got, ref)
+
+
 def test_multi_graph_replay_is_identical(q):
     wls = small_set(6, seed=3)
     mp, outs = run_multi(q, wls, 4, graph=True, reps=3)

@@ -86,20 +86,20 @@ def test_random_circuits_rotating_layouts(q, seed, n, dtype, k, c):
     _random_case(q, seed, n, dtype, "fused", k, c, rotate_low_bits=True)
 
 
-# rotations in the tangent form only, the cotangent forms' Paulis carried in a per-sample Pauli frame;
-# with and without a checkpoint every pass (the backward starts from the stored representation)
+# without the Pauli frame (fused plans use it by default): every rotation picks its tangent or cotangent
+# form per sample at run time, as the multi-circuit queue kernels do; with and without checkpoints
 @pytest.mark.parametrize("seed,n,dtype,k,c,ckpt", [(30, 1, "c64", 1, 1, 0), (31, 5, "c128", 4, 2, 0),
                                                    (32, 7, "c64", 5, 3, 1), (33, 9, "c128", 7, 3, 1),
                                                    (34, 10, "c64", 8, 4, 0), (35, 12, "c64", 12, 4, 0),
                                                    (36, 11, "c64", 6, 2, 2), (37, 13, "c128", 11, 4, 1)])
-def test_random_circuits_pauli_frame(q, seed, n, dtype, k, c, ckpt):
-    _random_case(q, seed, n, dtype, "fused", k, c, pauli_frame=True, checkpoint_passes=ckpt)
+def test_random_circuits_both_forms(q, seed, n, dtype, k, c, ckpt):
+    _random_case(q, seed, n, dtype, "fused", k, c, pauli_frame=False, checkpoint_passes=ckpt)
 
 
 def test_pauli_frame_agrees_with_both_forms(q):
     # the same 14-qubit checkpointed workload both ways: results within the complex64 tolerances
     wl = W.config(3, n=14, batch=4)
-    a = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1)
+    a = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1, pauli_frame=False)
     b = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1, pauli_frame=True)
     np.testing.assert_allclose(b["states"], a["states"], atol=2e-5, rtol=0)
     np.testing.assert_allclose(b["z"], a["z"], atol=2e-5, rtol=0)
@@ -156,40 +156,68 @@ def test_c2_fused_equals_per_gate_all_samples(q):
 
 # ---------------------------------------------------------------- C3 (20 qubits, batch 64) at full size
 _C3_REF = {}
+C3_SAMPLES = 2          # samples carrying loss weight (their oracle states and gradients are computed)
 
 
 def _c3_reference(wl, pr, ir, g):
-    """Oracle-S states of samples 0, 1 and parameter-shift gradients of two sampled gates (cached:
-    the 20-qubit oracle is the slow part)."""
+    """FP64 oracle for samples 0, 1 of C3 (cached: the 20-qubit oracle is the slow part): Oracle-S
+    states, every parameter and input gradient by the adjoint sweep, and the exact parameter shift on
+    a seeded subset of 32 parameters and 4 input columns (parallel over the host's cores)."""
     if not _C3_REF:
-        L = len(wl.gates)
-        first = L - 2 * wl.n - 3
-        _C3_REF["psi"] = oracle.simulate_strided(wl.gates, wl.n, pr, ir[:2])
-        pre = (first, oracle.simulate_strided(wl.gates[:first], wl.n, pr, ir[:2]))
-        _C3_REF["grads"] = {gi: shift_grad_strided(wl.gates, wl.n, pr, ir[:2], g[:2], gi, prefix=pre).sum()
-                            for gi in (L - wl.n - 1, first)}
-    return _C3_REF["psi"], _C3_REF["grads"]
+        from oracle_pool import shift_derivatives
+        S = C3_SAMPLES
+        _C3_REF["psi"] = oracle.simulate_strided(wl.gates, wl.n, pr, ir[:S])
+        _C3_REF["adj"] = oracle.grad_adjoint(wl.gates, wl.n, pr, ir[:S], g[:S])
+        rng = np.random.default_rng(0x240409213)
+        psub = sorted(rng.choice(wl.n_params, 32, replace=False).tolist())
+        csub = sorted(rng.choice(wl.n_inputs, 4, replace=False).tolist())
+        which = [i for i, gt in enumerate(wl.gates)
+                 if (gt[3] >= 0 and gt[3] in psub) or (gt[3] <= -2 and -2 - gt[3] in csub)]
+        d = shift_derivatives(wl.gates, wl.n, pr, ir[:S], g[:S], which)
+        dps = {wl.gates[i][3]: v.sum() for i, v in d.items() if wl.gates[i][3] >= 0}
+        dis = {-2 - wl.gates[i][3]: v for i, v in d.items() if wl.gates[i][3] <= -2}
+        _C3_REF["shift"] = (psub, np.array([dps[p] for p in psub]), csub, np.stack([dis[c] for c in csub], axis=1))
+    return _C3_REF["psi"], _C3_REF["adj"], _C3_REF["shift"]
+
+
+def _elementwise_rel(got, ref, floor=0.05):
+    """Worst per-element relative error over entries with |ref| >= floor * max|ref|."""
+    got, ref = np.ravel(got), np.ravel(ref)
+    m = np.abs(ref) >= floor * np.abs(ref).max()
+    return float(np.max(np.abs(got[m] - ref[m]) / np.abs(ref[m])))
 
 
 # the bench's launch configuration: batch 64, checkpoint every pass, the tile sizes its autotuner picks
 @pytest.mark.parametrize("k", [12, 11, 10])
-def test_c3_full_size_sampled(q, k):
+def test_c3_full_size_against_oracle(q, k):
     wl = W.config(3)
+    S = C3_SAMPLES
     # only samples 0 and 1 carry loss weight, so the batch-summed parameter gradient is checkable
     g = np.zeros_like(wl.grad_out)
-    g[:2] = wl.grad_out[:2]
+    g[:S] = wl.grad_out[:S]
     wl.grad_out = g
     r = run(q, wl, "c64", "fused", k=k, checkpoint_passes=1)
     pr, ir = rounded(wl, "c64")
     norms = np.linalg.norm(r["states"], axis=1)
     np.testing.assert_allclose(norms, 1.0, atol=1e-5)
-    psi, grads = _c3_reference(wl, pr, ir, g)
-    np.testing.assert_allclose(r["states"][:2], psi, atol=1e-5, rtol=0)
-    np.testing.assert_allclose(r["z"][:2], oracle.expval_z(psi, wl.n), atol=1e-5, rtol=0)
-    # parameter shift on a sample of gates: one in the last layer, one in the first trainable layer
-    for gi, ref in grads.items():
-        p = wl.gates[gi][3]
-        assert abs(r["dp"][p] - ref) <= 1e-4 * max(1e-3, np.abs(r["dp"]).max()), (gi, r["dp"][p], ref)
+    psi, (adp, adi), (psub, sdp, csub, sdi) = _c3_reference(wl, pr, ir, g)
+    np.testing.assert_allclose(r["states"][:S], psi, atol=1e-5, rtol=0)
+    np.testing.assert_allclose(r["z"][:S], oracle.expval_z(psi, wl.n), atol=1e-5, rtol=0)
+    # the oracle's two gradient methods agree (adjoint sweep vs exact shift rule)
+    np.testing.assert_allclose(adp[psub], sdp, atol=1e-10 * np.abs(sdp).max())
+    np.testing.assert_allclose(adi[:, csub], sdi, atol=1e-10 * np.abs(sdi).max())
+    # all 400 parameter gradients and all 2 x 20 input gradients against the oracle, on the oracle's scale
+    check_grad(r["dp"], adp, "c64", "C3 dparams (all 400)")
+    for b in range(S):
+        check_grad(r["di"][b], adi[b], "c64", f"C3 dinputs sample {b}")
+    assert not np.any(r["di"][S:]), "samples without loss weight must get zero input gradients"
+    # the seeded subset against the shift rule directly
+    check_grad(r["dp"][psub], sdp, "c64", "C3 dparams, 32 by parameter shift")
+    check_grad(r["di"][:S, csub], sdi, "c64", "C3 dinputs, 4 columns by parameter shift")
+    # per element: every entry at least 5 % of the largest is within 1e-4 relative
+    ep, ei = _elementwise_rel(r["dp"], adp), _elementwise_rel(r["di"][:S], adi)
+    print(f"C3 k={k}: worst per-element relative gradient error dparams {ep:.2e} dinputs {ei:.2e}")
+    assert ep <= 1e-4 and ei <= 1e-4, (ep, ei)
 
 
 # ---------------------------------------------------------------- backward vs central finite differences

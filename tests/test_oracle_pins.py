@@ -312,6 +312,77 @@ def test_param_shift_with_shared_parameter_and_strided():
         np.testing.assert_allclose(a, b, atol=1e-8)
 
 
+# ---------------------------------------------------------------- adjoint sweep (oracle.grad_adjoint)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_adjoint_equals_param_shift_kron(seed):
+    # every gate type, shared parameters, input columns and (seed 1) a random initial state, against
+    # the exact shift rule evaluated on the dense Kronecker oracle (no code in common with the sweep)
+    rng = np.random.default_rng(40 + seed)
+    n, B = 5, 3
+    gates = _random_circuit(rng, n, 45, 4, 2)
+    params = rng.uniform(0, 2 * math.pi, 4)
+    inputs = rng.uniform(0, math.pi, (B, 2))
+    g = rng.uniform(-1, 1, (B, n))
+    init = None
+    if seed == 1:
+        init = rng.normal(size=(B, 2 ** n)) + 1j * rng.normal(size=(B, 2 ** n))
+        init /= np.linalg.norm(init, axis=1, keepdims=True)
+    da, ia = oracle.grad_adjoint(gates, n, params, inputs, g, init=init)
+    dk, ik = oracle.grad_param_shift(gates, n, params, inputs, g, method="kron", init=init)
+    np.testing.assert_allclose(da, dk, atol=1e-12)
+    np.testing.assert_allclose(ia, ik, atol=1e-12)
+
+
+def test_adjoint_product_state_closed_form():
+    # RX(x_q) then RY(t_q) on every qubit, no entanglers: <Z_q> = cos x_q cos t_q, so
+    # dL/dt_q = -g_q cos x_q sin t_q and dL/dx_q = -g_q sin x_q cos t_q
+    rng = np.random.default_rng(7)
+    n, B = 4, 2
+    gates = [W.gate(W.RX, (q,), param=W.input_param(q)) for q in range(n)]
+    gates += [W.gate(W.RY, (q,), param=q) for q in range(n)]
+    t = rng.uniform(0, 2 * math.pi, n)
+    x = rng.uniform(0, math.pi, (B, n))
+    g = rng.uniform(-1, 1, (B, n))
+    dp, di = oracle.grad_adjoint(gates, n, t, x, g)
+    np.testing.assert_allclose(dp, (-g * np.cos(x) * np.sin(t)).sum(axis=0), atol=1e-14)
+    np.testing.assert_allclose(di, -g * np.sin(x) * np.cos(t), atol=1e-14)
+
+
+def _adjoint_pins_pass():
+    try:
+        test_adjoint_equals_param_shift_kron(0)
+        test_adjoint_product_state_closed_form()
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("mistake", ["no_dagger", "real_part", "lambda_not_uncomputed", "pauli_wrong_axis"])
+def test_planted_adjoint_mistakes_are_caught(monkeypatch, mistake):
+    import oracle.adjoint as A
+    assert _adjoint_pins_pass()
+    if mistake == "no_dagger":
+        orig = A._gate_dagger
+        monkeypatch.setattr(A, "_gate_dagger", lambda g, p, x, b: np.conj(np.swapaxes(orig(g, p, x, b), -1, -2)))
+    elif mistake == "real_part":
+        monkeypatch.setattr(A, "np", type("npx", (), {**{k: getattr(np, k) for k in dir(np) if not k.startswith("__")},
+                                                    "imag": staticmethod(np.real)}))
+    elif mistake == "lambda_not_uncomputed":
+        orig1 = A._apply_1q
+        monkeypatch.setattr(A, "_apply_1q", lambda psi, n, w, G: psi if psi is A._LAST_LAM else orig1(psi, n, w, G))
+        orig_lo = A._loss_observable
+
+        def keep(psi, n, g):
+            lam = orig_lo(psi, n, g)
+            A._LAST_LAM = lam
+            return lam
+        monkeypatch.setattr(A, "_LAST_LAM", None, raising=False)
+        monkeypatch.setattr(A, "_loss_observable", keep)
+    elif mistake == "pauli_wrong_axis":
+        monkeypatch.setattr(A, "_PAULI", {W.RX: OG.PY, W.RY: OG.PX, W.RZ: OG.PZ})
+    assert not _adjoint_pins_pass(), f"planted adjoint mistake {mistake} was not caught by any pin"
+
+
 # ---------------------------------------------------------------- planted mistakes
 def _pins_pass():
     try:
@@ -407,3 +478,18 @@ def test_planted_remap_slope_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(R, "remap_slope", lambda w: np.pi * (1.0 - np.tanh(np.asarray(w, dtype=np.float64))))
     with pytest.raises(AssertionError):
         test_remap_single_rx_closed_form(1.1)
+
+
+# ---------------------------------------------------------------- parallel shift-rule helper of the GPU tests
+def test_parallel_shift_derivatives_equal_serial_shift_rule():
+    from oracle_pool import shift_derivatives
+    wl = W.config(3, n=6, batch=2, layers=2)          # every parameter and input column used once
+    which = [i for i, g in enumerate(wl.gates) if g[3] != -1]
+    d = shift_derivatives(wl.gates, wl.n, wl.params, wl.inputs, wl.grad_out, which, processes=2)
+    dp, di = oracle.grad_param_shift(wl.gates, wl.n, wl.params, wl.inputs, wl.grad_out, method="kron")
+    for i, v in d.items():
+        p = wl.gates[i][3]
+        if p >= 0:
+            assert abs(v.sum() - dp[p]) < 1e-12
+        else:
+            np.testing.assert_allclose(v, di[:, -2 - p], atol=1e-12)
