@@ -55,11 +55,24 @@ def parse():
     ap.add_argument("--no-pauli-frame", action="store_true",
                     help="fused passes pick each rotation's tangent or cotangent form per sample at run time "
                          "(default: the tangent form only, cotangent Paulis carried in a per-sample frame)")
+    ap.add_argument("--scalar-bwd", action="store_true",
+                    help="backward pass kernels update psi and lambda with scalar FMAs (default: packed FP32x2 pairs)")
+    ap.add_argument("--no-product-prefix", action="store_true",
+                    help="run every gate inside the fused passes (default: single-qubit gates before a qubit's first "
+                         "two-qubit gate are merged into its prefix state and the first pass starts from the product)")
+    ap.add_argument("--split-diagonal", action="store_true",
+                    help="apply runs of diagonal ops one op at a time (default: one factor per amplitude per run)")
+    ap.add_argument("--bwd-reg-bits", type=int, default=0, help="amplitudes per thread in backward phases = 2^bits (0: default)")
+    ap.add_argument("--fwd-reg-bits", type=int, default=0, help="amplitudes per thread in forward phases = 2^bits (0: default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true", help="skip timing the per-gate path next to the fused one")
     ap.add_argument("--per-gate-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--json-out", default="")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="with --impl reference: time the FP64 oracles on the host cores over every configuration "
+                         "(Oracle-K: C1, C2 on samples 0..31, the 12-qubit C3 / C5 ansatze; Oracle-S: C3) and print "
+                         "one JSON line")
     return ap.parse_args()
 
 
@@ -186,6 +199,66 @@ def oracle_bounded(wl, pool, cores, per_core_s=1.5, calib=None):
                               "wall_s_timed": wall}, calib
 
 
+def _oracle_window_job(args):
+    """Seconds for one oracle call: method 'kron' / 'strided' forward, or 'adjoint' fwd+bwd, over a gate list."""
+    method, gates, n, params, inputs, g = args
+    import oracle
+    t0 = time.perf_counter()
+    if method == "adjoint":
+        oracle.grad_adjoint(gates, n, params, inputs, g)
+    elif method == "kron":
+        oracle.simulate_kron(gates, n, params, inputs)
+    else:
+        oracle.simulate_strided(gates, n, params, inputs)
+    return time.perf_counter() - t0
+
+
+def oracle_table(cores, budget_s=8.0):
+    """Samples/s of the FP64 oracles per configuration, each from a timed window of the circuit scaled to
+    the whole circuit (forward: x G / g; parameter-shift backward: 2 forwards per rotation), the windows
+    of one row run as parallel processes (one per core, each on its own samples)."""
+    import workloads as W
+    pool = _oracle_pool(cores)
+    rows = []
+
+    def window(wl, method, samples_per_job, jobs):
+        G = len(wl.gates)
+        one = _oracle_window_job((method, wl.gates[:4], wl.n, wl.params, wl.inputs[:samples_per_job],
+                                  wl.grad_out[:samples_per_job])) / 4
+        g_t = max(4, min(G, int(budget_s / max(one, 1e-6))))
+        a = max(0, min(G - g_t, G // 2 - g_t // 2))
+        args = [(method, wl.gates[a:a + g_t], wl.n, wl.params,
+                 wl.inputs[(j * samples_per_job) % wl.batch:][:samples_per_job],
+                 wl.grad_out[(j * samples_per_job) % wl.batch:][:samples_per_job]) for j in range(jobs)]
+        t0 = time.perf_counter()
+        pool.map(_oracle_window_job, args, chunksize=1)
+        wall = time.perf_counter() - t0
+        return wall * G / g_t, g_t, G, wall
+
+    def add(name, wl, method, spj, jobs, shift_factor, what):
+        t_full, g_t, G, wall = window(wl, method, spj, jobs)
+        samples = spj * jobs
+        rate = samples / (t_full * shift_factor)
+        rows.append({"config": name, "oracle": what, "samples_per_s": rate, "samples_timed": samples,
+                     "gates_timed": g_t, "gates_total": G, "wall_s_timed": wall,
+                     "extrapolated": g_t < G or shift_factor != 1})
+
+    c1 = W.config(1)
+    n_rot1 = sum(1 for gt in c1.gates if gt[0] <= 2)
+    add("C1 4q B8 c128", c1, "kron", c1.batch, 1, 1 + 2 * n_rot1, "Oracle-K forward + parameter-shift backward")
+    c2 = W.config(2)
+    add("C2 12q, samples 0..31", c2, "kron", 32 // cores if cores <= 32 else 1, min(cores, 32), 1, "Oracle-K forward")
+    for c in (3, 5):
+        wl = W.config(c, n=12, batch=max(2, cores))
+        n_rot = sum(1 for gt in wl.gates if gt[0] <= 2)
+        add(f"C{c} ansatz at 12 qubits", wl, "kron", 1, cores, 1 + 2 * n_rot, "Oracle-K forward + parameter-shift backward")
+        add(f"C{c} ansatz at 12 qubits", wl, "adjoint", 1, cores, 1, "Oracle-S forward + adjoint backward")
+    c3 = W.config(3)
+    add("C3 20q, samples 0..15", c3, "strided", 1, min(cores, 16), 1, "Oracle-S forward")
+    pool.close()
+    return rows
+
+
 # ------------------------------------------------------------------ our arm
 def algorithmic_bytes(plan_desc, B, n, direction, checkpoint_passes=0):
     """Bytes each fused pass must move (complex64, 8 B per amplitude and state read or written).
@@ -310,11 +383,16 @@ def run_ours(args, world, rank, local):
     k, autotune = args.k, None
     if args.mode == "fused" and k == 0:   # tile size from the library's autotuner (untimed setup)
         k, ms = q.autotune(wl.gates, wl.n, wl.batch, reps=2, contiguous_bits=args.contiguous_bits,
-                           checkpoint_passes=args.checkpoint_passes, pauli_frame=int((not args.no_pauli_frame)))
+                           checkpoint_passes=args.checkpoint_passes, pauli_frame=int((not args.no_pauli_frame)),
+                           scalar_bwd=int(args.scalar_bwd), product_prefix=int(not args.no_product_prefix),
+                           bwd_reg_bits=args.bwd_reg_bits, fwd_reg_bits=args.fwd_reg_bits,
+                           split_diagonal=int(args.split_diagonal))
         autotune = {"k_candidates": [10, 11, 12], "ms_per_fwd_bwd": ms, "chosen_k": k}
     ckpt = args.checkpoint_passes if args.mode == "fused" else 0
     plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits,
-                  checkpoint_passes=ckpt, pauli_frame=(not args.no_pauli_frame) and args.mode == "fused")
+                  checkpoint_passes=ckpt, pauli_frame=(not args.no_pauli_frame) and args.mode == "fused",
+                  scalar_bwd=args.scalar_bwd, product_prefix=args.mode == "fused" and not args.no_product_prefix,
+                  bwd_reg_bits=args.bwd_reg_bits, fwd_reg_bits=args.fwd_reg_bits, split_diagonal=args.split_diagonal)
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
     x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
@@ -431,6 +509,11 @@ def run_ours(args, world, rank, local):
                                  "FP64 across tiles and samples",
                     "checkpoint_passes": ckpt, "checkpoints": plan.info()["n_checkpoints"],
                     "pauli_frame": bool((not args.no_pauli_frame) and args.mode == "fused"),
+                    "packed_bwd": bool((not args.no_pauli_frame) and args.mode == "fused" and not args.scalar_bwd),
+                    "product_prefix": bool(args.mode == "fused" and not args.no_product_prefix),
+                    "merged_diagonal_runs": bool((not args.no_pauli_frame) and args.mode == "fused" and not args.split_diagonal),
+                    "prefix_gates": sum(len(x) for x in desc.get("prefix", [])),
+                    "reg_bits": {"fwd": desc.get("R"), "bwd": desc.get("Rb")},
                     "workspace_bytes": plan.info()["workspace_bytes"], "contiguous_bits": desc["c"]},
            "roofline": roofline, "vs_per_gate": per_gate, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     return out, wl
@@ -547,11 +630,15 @@ def run_other(args, world, rank, local):
         samples = B
         P = plan.info()["n_passes"]
         tot = B * (1 << wl.n) * (8 + 16 * (P - 1)) if args.mode == "fused" else B * (1 << wl.n) * 16 * len(wl.gates)
-        # algorithmic work: a real 2x2 rotation costs 6 flop per amplitude (CNOTs are permutations)
-        n_rot = sum(1 for gt in wl.gates if gt[0] in (W.RX, W.RY, W.RZ))
+        # algorithmic work of the pass kernel: a real 2x2 rotation costs 6 flop per amplitude (CNOTs are
+        # permutations), counted over the rotations the pass applies (not those merged into prefix states)
+        desc = plan.describe()
+        n_rot = sum(1 for ps in desc["passes"] for gi in ps["gates"] if wl.gates[gi][0] in (W.RX, W.RY, W.RZ))
+        n_rot_circuit = sum(1 for gt in wl.gates if gt[0] in (W.RX, W.RY, W.RZ))
         c2_flops = B * (1 << wl.n) * 6 * n_rot
         name = f"C2: 12 qubits, batch 1024, c64, RX encoding + 6 x (RY,RZ + CNOT ring), forward only, {args.mode}"
-        extra = {"passes": P, "mode": args.mode, "rotations": n_rot,
+        extra = {"passes": P, "mode": args.mode, "rotations_in_passes": n_rot, "rotations": n_rot_circuit,
+                 "prefix_gates": sum(len(x) for x in desc.get("prefix", [])),
                  "l2": "32 MiB state per step stays in L2 and shared memory (ALU-bound, no flush)"}
     for _ in range(max(args.warmup, 3)):
         step()
@@ -597,6 +684,11 @@ def run_other(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_init(args.gpus)
+    if args.impl == "reference" and args.oracle_table:
+        if rank == 0:
+            cores = os.cpu_count() or 1
+            print(json.dumps({"oracle_table": oracle_table(cores), "cores": cores}))
+        return
     if args.impl == "reference":
         if rank != 0:
             return

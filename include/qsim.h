@@ -75,8 +75,9 @@ typedef struct {
                                 0: no checkpoints; -1: choose from mem_budget_bytes */
   int32_t sample_block;      /* >0: samples per launch group; every pass runs over one group before the next
                                 group starts (keeps a group's states in L2); 0 = the whole batch per launch */
-  int32_t bwd_reg_bits;      /* amplitudes per thread in backward phases = 2^bits (0 = default: 4 for complex64,
-                                3 for complex128); more bits mean fewer shared-memory round trips per pass */
+  int32_t bwd_reg_bits;      /* amplitudes per thread in backward phases = 2^bits (0 = default: 5 for complex64
+                                single-circuit plans, 4 for complex64 multi-circuit plans, 3 for complex128);
+                                more bits mean fewer shared-memory round trips per pass */
   int32_t fwd_reg_bits;      /* amplitudes per thread in forward phases = 2^bits (0 = default: 5 for complex64,
                                 4 for complex128); fewer bits mean fewer registers and more resident warps */
   int32_t weight_remap;      /* 1: every trainable angle enters as theta' = pi * tanh(theta) (quantum weight
@@ -99,7 +100,23 @@ typedef struct {
                                 carried per sample as a Pauli frame F (stored states are F^dag times the true
                                 state; the returned states have F applied). Fused single-circuit plans only.
                                 0 (default): both forms, chosen per rotation and sample at run time */
-  int32_t reserved;          /* must be 0 */
+  int32_t scalar_bwd;        /* complex64 pauli_frame plans: 0 (default) the backward pass kernels hold psi and lambda
+                                as register pairs (Re psi, Re lambda), (Im psi, Im lambda) and update both with one
+                                packed FP32x2 FMA; 1: separate scalar FMAs. Other plans ignore it; 0 or 1 */
+  int32_t product_prefix;    /* 1: the single-qubit gates that act on a qubit before its first two-qubit gate are
+                                merged, per sample, into that qubit's state phi_q = G_m...G_1|0> (FP64); the
+                                first fused pass writes the product state of all phi_q instead of starting from
+                                |0...0> and applying them, and their gradients come from one contraction of the
+                                adjoint state with the other qubits' phi (Sec. "Gate Matrix Caching": the
+                                embedding's per-qubit matrices; the paper merges partial matrices, here the
+                                merged per-qubit gates act on |0> and collapse to a vector). A forward given an
+                                initial state runs an internal plan without it. Fused single-circuit plans only;
+                                0 (default): every gate runs inside the fused passes */
+  int32_t split_diagonal;    /* pauli_frame plans: 0 (default) a run of consecutive diagonal ops (RZ, CZ) in a register
+                                phase is applied as one complex factor per amplitude, built from per-bit factors,
+                                and in the backward all of the run's RZ gradients come from one pass over the
+                                amplitudes (Im(conj(lambda) psi) is unchanged through diagonal ops up to a known
+                                real factor); 1: every op on its own. 0 or 1 */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
 } qsim_plan_opts;
 

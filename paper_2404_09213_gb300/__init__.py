@@ -54,14 +54,20 @@ class Plan:
     the forward state every that many passes for the backward to restart from; ``weight_remap``
     feeds every trainable weight w in as the angle pi * tanh(w) (gradients are dL/dw);
     ``pauli_frame`` (default: on in fused mode) runs every rotation in the tangent form and carries the
-    cotangent forms' Paulis per sample (one kernel variant per rotation instead of two).
+    cotangent forms' Paulis per sample (one kernel variant per rotation instead of two); with it, complex64
+    backward kernels update psi and lambda together with packed FP32x2 FMAs unless ``scalar_bwd``;
+    ``product_prefix`` (default: on in fused mode) merges each qubit's single-qubit gates before its first
+    two-qubit gate into its state phi_q, and the first pass starts from the product of the phi_q.
     """
 
     def __init__(self, gates, n_qubits, *, dtype="c64", mode="fused", k=0, contiguous_bits=0,
                  checkpoint_passes=0, mem_budget_bytes=0, sample_block=0, bwd_reg_bits=0,
-                 fwd_reg_bits=0, weight_remap=False, max_regs=0, rotate_low_bits=False, pauli_frame=None):
+                 fwd_reg_bits=0, weight_remap=False, max_regs=0, rotate_low_bits=False, pauli_frame=None,
+                 scalar_bwd=False, product_prefix=None, split_diagonal=False):
         if pauli_frame is None:
             pauli_frame = mode == "fused"
+        if product_prefix is None:
+            product_prefix = mode == "fused"
         L = _lib.lib()
         self.gates = list(gates)
         self.n = int(n_qubits)
@@ -82,6 +88,9 @@ class Plan:
         opts.max_regs = max_regs
         opts.rotate_low_bits = 1 if rotate_low_bits else 0
         opts.pauli_frame = 1 if pauli_frame else 0
+        opts.scalar_bwd = 1 if scalar_bwd else 0
+        opts.product_prefix = 1 if product_prefix else 0
+        opts.split_diagonal = 1 if split_diagonal else 0
         h = ctypes.c_void_p()
         arr = gate_structs(self.gates)
         _lib.check(L.qsim_plan(arr, len(self.gates), self.n, ctypes.byref(opts), ctypes.byref(h)))
@@ -308,6 +317,8 @@ def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64",
     """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate]).
     Plans are timed with the Pauli frame on unless ``pauli_frame=0`` is passed (as :class:`Plan`)."""
     opts.setdefault("pauli_frame", 1)
+    opts.setdefault("product_prefix", 1)
+    opts.setdefault("split_diagonal", 0)
     o = _opts(dtype, **opts)
     ms = (ctypes.c_float * 3)()
     arr = gate_structs(gates)

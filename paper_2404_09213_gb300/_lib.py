@@ -30,7 +30,8 @@ class QsimPlanOpts(ctypes.Structure):
                 ("sample_block", ctypes.c_int32), ("bwd_reg_bits", ctypes.c_int32),
                 ("fwd_reg_bits", ctypes.c_int32), ("weight_remap", ctypes.c_int32),
                 ("graph", ctypes.c_int32), ("max_regs", ctypes.c_int32), ("rotate_low_bits", ctypes.c_int32),
-                ("pauli_frame", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("pauli_frame", ctypes.c_int32), ("scalar_bwd", ctypes.c_int32),
+                ("product_prefix", ctypes.c_int32), ("split_diagonal", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_int64)]
 
 

@@ -62,6 +62,15 @@ struct qsim_plan_s {
   int32_t *d_p_ptr = nullptr, *d_p_occ = nullptr, *d_i_ptr = nullptr, *d_i_occ = nullptr;
   uint8_t* d_Qnl_last = nullptr;
   int n_occ = 0;
+  // product-state prefix: CSR over qubits of the prefix gates, their gradient occurrences, and the first
+  // pass's tile / tile-index qubits
+  int32_t *d_pfx_begin = nullptr, *d_pfx_gate = nullptr, *d_pfx_occ = nullptr;
+  uint8_t* d_Qnl_first = nullptr;
+  void* phi = nullptr;         // [B][n][4] prefix states (state precision)
+  double* ppart = nullptr;     // [B][tps of pass 0][2k + 1][2] backward partials of the first pass
+  // a prefix plan given an initial state runs this plan (same gates and options, no prefix) instead
+  qsim_plan_s* alt = nullptr;
+  bool via_alt = false;
   // batch workspace
   int B_cap = -1;
   int n_segments = 1;
@@ -152,10 +161,12 @@ struct qsim_plan_s {
 
   void free_ws() {
     void* ptrs[] = {coef, form, cfp_f, fmp_f, cfp_b, fmp_b, scale_f, scale_b, gm, zpart, gpart, G, W, Lam,
-                    S_end, sigma, frame_x, frame_z, frame_k, gsign};
+                    S_end, sigma, frame_x, frame_z, frame_k, gsign, phi, ppart};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     S_end = nullptr;
+    phi = nullptr;
+    ppart = nullptr;
     sigma = nullptr;
     frame_x = frame_z = nullptr;
     frame_k = nullptr;
@@ -175,7 +186,8 @@ struct qsim_plan_s {
     free_ws();
     destroy_events();
     void* ptrs[] = {d_gate_type, d_gate_param, d_gate_q0, d_gate_q1, d_exec_gates, d_exec_begin, d_exec_gates_b,
-                    d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Qnl_last};
+                    d_exec_begin_b, d_occ_gate, d_occ_slot, d_p_ptr, d_p_occ, d_i_ptr, d_i_occ, d_Qnl_last,
+                    d_pfx_begin, d_pfx_gate, d_pfx_occ, d_Qnl_first};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     jit_free(jit);
@@ -210,7 +222,8 @@ struct qsim_plan_s {
     n_occ = (int)s.grad_gate.size();
     std::vector<int32_t> occ_gate(s.grad_gate.begin(), s.grad_gate.end());
     std::vector<int64_t> occ_slot(n_occ);
-    for (int j = 0; j < n_occ; j++) occ_slot[j] = s.passes[s.grad_pass[j]].devb.gpart_offset + s.grad_slot[j];
+    for (int j = 0; j < n_occ; j++)
+      occ_slot[j] = s.grad_pass[j] < 0 ? -1 : s.passes[s.grad_pass[j]].devb.gpart_offset + s.grad_slot[j];
     std::vector<int32_t> p_ptr(s.n_params + 1, 0), i_ptr(s.n_inputs + 1, 0), p_occ, i_occ;
     for (int p = 0; p < s.n_params; p++) {
       for (int j = 0; j < n_occ; j++)
@@ -229,6 +242,25 @@ struct qsim_plan_s {
       for (int j = 0; j < d.n_nonlocal; j++) lnl.push_back(d.QN[j]);
       lnl.push_back(0);
     }
+    std::vector<int32_t> pfx_begin, pfx_gate, pfx_occ;
+    std::vector<uint8_t> lnf;
+    if (s.has_prefix) {
+      pfx_begin.push_back(0);
+      for (int q = 0; q < s.n; q++) {
+        for (int gi : s.prefix[q]) {
+          int occ = -1;
+          for (int j = 0; j < n_occ; j++)
+            if (s.grad_pass[j] < 0 && s.grad_gate[j] == gi) occ = j;
+          pfx_gate.push_back(gi);
+          pfx_occ.push_back(occ);
+        }
+        pfx_begin.push_back((int32_t)pfx_gate.size());
+      }
+      const DevPass& d = s.passes.front().dev;
+      for (int j = 0; j < d.k; j++) lnf.push_back(d.Q[j]);
+      for (int j = 0; j < d.n_nonlocal; j++) lnf.push_back(d.QN[j]);
+      lnf.push_back(0);
+    }
 #define QSIM_UP(PTR, VEC) \
   if (e == cudaSuccess) e = upload(&PTR, VEC);
     QSIM_UP(d_exec_gates_b, exec_b)
@@ -246,6 +278,10 @@ struct qsim_plan_s {
     QSIM_UP(d_i_ptr, i_ptr)
     QSIM_UP(d_i_occ, i_occ)
     QSIM_UP(d_Qnl_last, lnl)
+    QSIM_UP(d_pfx_begin, pfx_begin)
+    QSIM_UP(d_pfx_gate, pfx_gate)
+    QSIM_UP(d_pfx_occ, pfx_occ)
+    QSIM_UP(d_Qnl_first, lnf)
 #undef QSIM_UP
     if (e != cudaSuccess) return cuda_fail(e, "uploading the plan");
     if (s.mode == QSIM_FUSED) {
@@ -287,6 +323,9 @@ struct qsim_plan_s {
         {reinterpret_cast<void**>(&frame_z), s.pauli_frame ? (int64_t)B_ * 8 : 0},
         {reinterpret_cast<void**>(&frame_k), s.pauli_frame ? (int64_t)B_ * 4 : 0},
         {reinterpret_cast<void**>(&gsign), s.pauli_frame ? (int64_t)B_ * s.n * 8 : 0},
+        {&phi, s.has_prefix ? (int64_t)B_ * s.n * 4 * sc : 0},
+        {reinterpret_cast<void**>(&ppart),
+         s.has_prefix ? (int64_t)B_ * s.passes.front().devb.tiles_per_sample * (2 * s.k + 1) * 2 * 8 : 0},
     };
     for (auto& it : items) {
       if (it.bytes <= 0) continue;
@@ -348,6 +387,30 @@ struct qsim_plan_s {
     a.n_nonlocal = d.n_nonlocal;
     a.n = s.n;
     a.B = B;
+    return a;
+  }
+
+  PrefixArgs prefix_args(const void* params_, const void* inputs_) const {
+    PrefixArgs a{};
+    const DevPass& d = s.passes.front().devb;
+    a.gate_type = d_gate_type;
+    a.gate_param = d_gate_param;
+    a.pfx_begin = d_pfx_begin;
+    a.pfx_gate = d_pfx_gate;
+    a.pfx_occ = d_pfx_occ;
+    a.params = params_;
+    a.inputs = inputs_;
+    a.n_inputs = s.n_inputs;
+    a.weight_remap = opts.weight_remap;
+    a.n = s.n;
+    a.B = B;
+    a.phi = phi;
+    a.ppart = ppart;
+    a.Qnl = d_Qnl_first;
+    a.K = d.k;
+    a.n_nonlocal = d.n_nonlocal;
+    a.tps = d.tiles_per_sample;
+    a.G = G;
     return a;
   }
 
@@ -413,14 +476,19 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
       o.sample_block < 0 || o.weight_remap < 0 || o.weight_remap > 2 || o.max_regs < 0 ||
       (o.max_regs > 0 && o.max_regs < 32) || (o.rotate_low_bits != 0 && o.rotate_low_bits != 1) ||
       (o.pauli_frame != 0 && o.pauli_frame != 1) || (o.pauli_frame == 1 && o.mode != QSIM_FUSED) ||
-      o.reserved != 0) {
+      (o.scalar_bwd != 0 && o.scalar_bwd != 1) || (o.product_prefix != 0 && o.product_prefix != 1) ||
+      (o.product_prefix == 1 && o.mode != QSIM_FUSED) || (o.split_diagonal != 0 && o.split_diagonal != 1)) {
     delete p;
     return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0..2, "
                               "max_regs 0 or >= 32, rotate_low_bits 0 or 1, pauli_frame 0 or 1 (fused mode), "
-                              "reserved 0");
+                              "scalar_bwd 0 or 1, product_prefix 0 or 1 (fused mode), split_diagonal 0 or 1");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
-  const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : bwd_R_for(16, o.dtype);
+  // single-circuit complex64 backward kernels hold 2^5 amplitudes of psi and lambda per thread: fewer
+  // shared-memory exchanges per pass than 2^4, with 2 CTAs of 128 threads per SM instead of 2 of 256
+  // (measured faster on the 20-qubit workload); the multi-circuit queue kernels, capped at 128
+  // registers, keep 2^4
+  const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : (o.dtype == QSIM_C64 ? 5 : bwd_R_for(16, o.dtype));
   rc = build_schedule(gv, n_qubits, o, Rf, Rb, p->s, err, o.rotate_low_bits == 1);
   if (rc) {
     delete p;
@@ -508,9 +576,25 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
   if (p->s.n_inputs > 0 && batch > 0 && !d_inputs) return fail(QSIM_ERR_ARG, "d_inputs is NULL but the circuit has inputs");
   if (((uintptr_t)d_states & 15) || ((uintptr_t)d_init & 15)) return fail(QSIM_ERR_ARG, "state buffers must be 16-byte aligned");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  p->has_fwd = false;
+  p->via_alt = false;
+  if (p->s.has_prefix && d_init != nullptr) {
+    // the prefix assumes the |0...0> start: an initial state runs the same circuit planned without it
+    if (!p->alt) {
+      std::vector<qsim_gate> gl;
+      for (const Gate& g : p->s.gates) gl.push_back(qsim_gate{g.type, {g.t0, g.t1}, {g.c0, g.c1}, g.param});
+      qsim_plan_opts o = p->opts;
+      o.product_prefix = 0;
+      qsim_plan_t a = nullptr;
+      const int rc0 = qsim_plan(gl.data(), (int32_t)gl.size(), p->s.n, &o, &a);
+      if (rc0) return rc0;
+      p->alt = a;
+    }
+    p->via_alt = true;
+    return qsim_forward(p->alt, d_params, d_inputs, batch, d_init, d_states, d_z, stream);
+  }
   int rc = p->upload_schedule();
   if (rc) return rc;
-  p->has_fwd = false;
   if (batch == 0) return QSIM_OK;
   rc = p->ensure_ws(batch);
   if (rc) return rc;
@@ -558,6 +642,10 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
     e = launch_coef(ca, s.dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "coefficient kernel");
   }
+  if (s.has_prefix) {   // phi_q of every sample and qubit: the first pass starts from their product
+    e = launch_prefix_phi(p->prefix_args(d_params, d_inputs), s.dtype, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prefix state kernel");
+  }
   const char* sf = reinterpret_cast<const char*>(p->scale_f);
   if (s.mode == QSIM_PER_GATE) {
     e = launch_pg_init(d_states, d_init, s.n, batch, s.dtype, st);
@@ -591,6 +679,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
         ja.in = in;
         ja.out = out;
         ja.zpart = (q == P_ - 1) ? p->zpart : nullptr;
+        ja.phi = (q == 0 && s.has_prefix) ? p->phi : nullptr;
         ja.b0 = b0;
         const int rec = p->prof_begin(0, q, st);
         e = jit_launch(p->jit.fwd[q], s.passes[q].dev.tiles_per_sample * nb, ja, st);
@@ -615,6 +704,7 @@ int qsim_forward(qsim_plan_t p, const void* d_params, const void* d_inputs, int3
 int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, double* d_dinputs, void* stream) {
   g_err.clear();
   if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  if (p->via_alt) return qsim_backward(p->alt, d_grad_out, d_dparams, d_dinputs, stream);
   if (!p->has_fwd) return fail(QSIM_ERR_NO_FORWARD, "backward called without a preceding forward on this plan");
   const int B = p->B;
   if (!d_grad_out) return fail(QSIM_ERR_ARG, "d_grad_out is NULL");
@@ -658,6 +748,10 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
         ja.lam_in = lin;
         ja.lam_out = lout;
         ja.grad_out = s.pauli_frame ? p->gsign : d_grad_out;
+        if (q == 0 && s.has_prefix) {   // the first pass also contracts lambda with the prefix states
+          ja.phi = p->phi;
+          ja.ppart = p->ppart;
+        }
         ja.gpart = p->gpart;
         ja.b0 = b0;
         const int rec = p->prof_begin(1, q, st);
@@ -688,7 +782,9 @@ int qsim_backward(qsim_plan_t p, const double* d_grad_out, double* d_dparams, do
   ga.inputs = p->inputs;
   ga.weight_remap = p->opts.weight_remap;
   ga.dtype = s.dtype;
-  e = launch_grad_reduce(ga, st);
+  e = launch_grad_gather(ga, st);
+  if (e == cudaSuccess && s.has_prefix) e = launch_prefix_grad(p->prefix_args(p->params, p->inputs), s.dtype, st);
+  if (e == cudaSuccess) e = launch_grad_scatter(ga, st);
   if (e != cudaSuccess) return cuda_fail(e, "gradient reduction");
   if (p->calls_left(1)) p->n_bwd_calls++;
   return QSIM_OK;
@@ -735,6 +831,7 @@ int64_t qsim_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
 
 int qsim_sync_status(qsim_plan_t p) {
   if (!p) return fail(QSIM_ERR_ARG, "plan is NULL");
+  if (p->via_alt) return qsim_sync_status(p->alt);
   cudaError_t e = cudaStreamSynchronize(p->last_stream);
   if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
   return QSIM_OK;
@@ -783,6 +880,8 @@ int qsim_expval_z_noalloc(const void* d_states, int32_t batch, int32_t n, int32_
 
 void qsim_plan_destroy(qsim_plan_t p) {
   if (!p) return;
+  qsim_plan_destroy(p->alt);
+  p->alt = nullptr;
   if (p->uploaded || p->B_cap >= 0) {
     cudaStreamSynchronize(p->last_stream);
     p->free_all();

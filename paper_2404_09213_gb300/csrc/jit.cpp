@@ -213,7 +213,9 @@ static int grad_level(const DevPass& d, int dtype, int cta) {
   return cap;
 }
 
-static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0) {
+// prefix: this is the first pass of a product-prefix plan (its forward starts from the product state, its
+// backward writes the prefix partials)
+static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0, bool prefix = false) {
   const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
   const int P = d.n_phases;
   std::ostringstream o;
@@ -265,15 +267,24 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       if ((i >> r) & 1) e += " ^ " + offs + "u" + std::to_string(r);
     return "(" + e + ")";
   };
+  // names of psi / lambda components of register element i in the backward
+  const bool pk = bwd && s.packed_bwd;
+  auto PR = [&](int i) { return pk ? "X[" + std::to_string(i) + "].x" : "pr[" + std::to_string(i) + "]"; };
+  auto PQ = [&](int i) { return pk ? "Y[" + std::to_string(i) + "].x" : "pq[" + std::to_string(i) + "]"; };
+  auto LR = [&](int i) { return pk ? "X[" + std::to_string(i) + "].y" : "lr[" + std::to_string(i) + "]"; };
+  auto LQ = [&](int i) { return pk ? "Y[" + std::to_string(i) + "].y" : "lq[" + std::to_string(i) + "]"; };
   if (!bwd) {
     o << "  template <typename T> static __device__ __forceinline__ void fwd_phases(qj::Ctx<T>& c) {\n"
       << "    const qj::Args& a = *c.a;\n    const qj::u32 tid = c.tid;\n"
       << "    T re[" << N << "], im[" << N << "];\n";
   } else {
     o << "  template <typename T, typename A> static __device__ __forceinline__ void bwd_phases(qj::Ctx<T>& c, A* red) {\n"
-      << "    const qj::Args& a = *c.a;\n    const qj::u32 tid = c.tid;\n"
-      << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n"
-      << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n    (void)lane; (void)warp;\n";
+      << "    const qj::Args& a = *c.a;\n    const qj::u32 tid = c.tid;\n";
+    if (pk)   // (Re psi, Re lambda) and (Im psi, Im lambda) register pairs
+      o << "    float2 X[" << N << "], Y[" << N << "];\n";
+    else
+      o << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n";
+    o << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n    (void)lane; (void)warp;\n";
   }
   for (int step = 0; step < P; step++) {
     const int ph = bwd ? P - 1 - step : step;
@@ -306,6 +317,14 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
              std::to_string(op->a) + ";\n";
       return t;
     };
+    // register bit r of a folded CNOT target holds the element with that bit flipped where the control is
+    // set: the prefix factors of that qubit swap their two values there
+    auto fold_swap = [&](int r) {
+      std::string t = "0u";
+      for (const DevOp* op : fold)
+        if (op->a == r) t += " ^ ((tb >> " + std::to_string(op->b) + ") & 1u)";
+      return t;
+    };
     o << "      const qj::u32 tb = 0u";
     for (int jb = 0; jb < Ph.n_tbits; jb++) o << " | (((tid >> " << jb << ") & 1u) << " << (int)Ph.tbit[jb] << ")";
     o << ";\n      (void)tb;\n";
@@ -314,7 +333,24 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     // ---- load
     if (first) {
       if (!bwd) {
-        o << "      if (a.in == nullptr) {\n";
+        // product-state prefix: psi(x) = prod_q phi_q(x_q), the tile-index and thread bits' factors in one
+        // product, then a butterfly over the register bits
+        if (prefix) {
+        o << "      if (a.in == nullptr && a.phi != nullptr) {\n"
+          << "        const T* ph = reinterpret_cast<const T*>(a.phi) + c.b * a.n * 4;\n"
+          << "        T br, bi;\n        qj::phi_nonlocal<T>(a, ph, c.t, br, bi);\n";
+        for (int jb = 0; jb < Ph.n_tbits; jb++)
+          o << "        { const T* f = ph + 4 * a.Q[" << (int)Ph.tbit[jb] << "] + 2 * ((tid >> " << jb
+            << ") & 1u); qj::cmul(br, bi, f[0], f[1]); }\n";
+        o << "        re[0] = br; im[0] = bi;\n";
+        for (int r = 0; r < R; r++)
+          o << "        { const qj::u32 sw = " << fold_swap(r) << "; const T* f = ph + 4 * a.Q[" << (int)Ph.rbit[r]
+            << "];\n          const T f0r = f[2 * sw], f0i = f[2 * sw + 1], f1r = f[2 - 2 * sw], f1i = f[3 - 2 * sw];\n"
+            << "          for (int i = 0; i < " << (1 << r) << "; i++) { re[i + " << (1 << r) << "] = re[i]; im[i + "
+            << (1 << r) << "] = im[i]; qj::cmul(re[i + " << (1 << r) << "], im[i + " << (1 << r)
+            << "], f1r, f1i); qj::cmul(re[i], im[i], f0r, f0i); }\n        }\n";
+        }
+        o << (prefix ? "      } else if (a.in == nullptr) {\n" : "      if (a.in == nullptr) {\n");
         for (int i = 0; i < N; i++) o << "        re[" << i << "] = T(0); im[" << i << "] = T(0);\n";
         o << "        if (tb == 0u && c.t == 0) re[0] = T(1);\n      } else {\n"
           << "        const T* in = reinterpret_cast<const T*>(a.in);\n";
@@ -327,12 +363,12 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       } else {
         o << "      {\n        const T* in = reinterpret_cast<const T*>(a.in);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::ldg_pair(in + 2 * " << goff("gb", "gb", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
-            << "], pq[" << i + 1 << "]);\n";
+          o << "        qj::ldg_pair(in + 2 * " << goff("gb", "gb", i) << ", " << PR(i) << ", " << PQ(i) << ", " << PR(i + 1)
+            << ", " << PQ(i + 1) << ");\n";
         o << "      }\n      if (a.lam_in != nullptr) {\n        const T* li = reinterpret_cast<const T*>(a.lam_in);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::ldg_pair(li + 2 * " << goff("gb", "gb", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
-            << "], lq[" << i + 1 << "]);\n";
+          o << "        qj::ldg_pair(li + 2 * " << goff("gb", "gb", i) << ", " << LR(i) << ", " << LQ(i) << ", " << LR(i + 1)
+            << ", " << LQ(i + 1) << ");\n";
         // lambda = d(e) psi, d(e) = gq[K] + sum_j (bit_j(e) ? -g_j : g_j)
         o << "      }\n      qj::stage_bwd<T, " << K << ", " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
         o << "      if (a.lam_in == nullptr) {\n        double dt = c.gq[" << K << "];\n";
@@ -347,7 +383,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           o << "        { const T m = (T)(2.0 * c.gq[" << (int)Ph.rbit[r] << "]); for (int i = 0; i < " << (1 << r)
             << "; i++) dd[i + " << (1 << r) << "] = dd[i] - m; }\n";
         for (int i = 0; i < N; i++)
-          o << "        lr[" << i << "] = dd[" << i << "] * pr[" << i << "]; lq[" << i << "] = dd[" << i << "] * pq[" << i << "];\n";
+          o << "        " << LR(i) << " = dd[" << i << "] * " << PR(i) << "; " << LQ(i) << " = dd[" << i << "] * " << PQ(i) << ";\n";
         o << "      }\n";
       }
     } else {
@@ -358,6 +394,8 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         const uint32_t cc = lay_eval(Li, K, dep_of(Ph, i));
         if (!bwd) {
           o << "      qj::ldpx<" << ad << ">(c.tile, si, " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+        } else if (pk) {
+          o << "      qj::ldppx<" << ad << ">(c.tile, si, " << cc << "u, X[" << i << "], Y[" << i << "], X[" << i + 1 << "], Y[" << i + 1 << "]);\n";
         } else {
           o << "      qj::ldpx<" << ad << ">(c.tile, si, " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
           o << "      qj::ldpx<" << ad << ">(c.tile2, si, " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
@@ -368,7 +406,15 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     std::vector<int> order;
     for (int oi = Ph.op_begin + (int)fold.size(); oi < Ph.op_end; oi++) order.push_back(oi);
     if (bwd) std::reverse(order.begin(), order.end());
-    for (int oi : order) {
+    // gradient partial of a rotation op (backward): one per thread, or summed over 2^gs lanes first
+    auto emit_grad = [&](const DevOp& op, const std::string& expr) {
+      if (gs == 0)
+        o << "      red[" << op.gslot * NTHR << " + tid] = " << expr << ";\n";
+      else
+        o << "      { A g = qj::part_sum<" << (1 << gs) << ", A, CTA>(" << expr << "); if ((tid & " << ((1 << gs) - 1)
+          << "u) == 0u) red[" << op.gslot * (NTHR >> gs) << " + (tid >> " << gs << ")] = g; }\n";
+    };
+    auto emit_op = [&](int oi) {
       const DevOp& op = s.ops[oi];
       const int li = oi - d.op0;
       const int SA = 1 << op.a, SB = 1 << op.b;
@@ -422,6 +468,29 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           call = "qj::scal<" + std::to_string(N) + ">(%R, %I, c.cf[" + std::to_string(li) + "]);";
           break;
       }
+      if (pk) {   // packed backward: the same ops on (psi, lambda) pairs, tangent form only
+        const std::string Ns = std::to_string(N), As = std::to_string(SA), Bs = std::to_string(SB);
+        const std::string cf = "c.cf[" + std::to_string(li) + "]";
+        const std::string tba = "((tb >> " + std::to_string(op.a) + ") & 1u)", tbb = "((tb >> " + std::to_string(op.b) + ") & 1u)";
+        g.str("");
+        switch (op.kind) {
+          case K_RY_R: call = "qj::ry_p<" + Ns + ", " + As + ">(X, Y, " + cf + ");"; g << "qj::g_ry_p<" << N << ", " << SA << ">(X, Y)"; break;
+          case K_RX_R: call = "qj::rx_p<" + Ns + ", " + As + ">(X, Y, " + cf + ");"; g << "qj::g_rx_p<" << N << ", " << SA << ">(X, Y)"; break;
+          case K_RZ_R: call = "qj::rz_p<" + Ns + ", " + As + ">(X, Y, " + cf + ");"; g << "qj::g_rz_p<" << N << ", " << SA << ">(X, Y)"; break;
+          case K_H_R: call = "qj::hd_p<" + Ns + ", " + As + ">(X, Y);"; break;
+          case K_X_R: call = "qj::swp_p<" + Ns + ", " + As + ", 0>(X, Y);"; break;
+          case K_RZ_T:
+            call = "qj::rz_tp<" + Ns + ">(X, Y, " + cf + ", " + tba + " ? -1.f : 1.f);";
+            g << "((" << tba << " ? -1.f : 1.f) * qj::g_im_p<" << N << ">(X, Y))";
+            break;
+          case K_CNOT_RR: call = "qj::swp_p<" + Ns + ", " + As + ", " + Bs + ">(X, Y);"; break;
+          case K_CNOT_RT: call = "qj::cnot_tp<" + Ns + ", " + As + ">(X, Y, " + tbb + " != 0u);"; break;
+          case K_CZ_RR: call = "qj::cz_p<" + Ns + ", " + As + ", " + Bs + ">(X, Y);"; break;
+          case K_CZ_RT: call = "qj::cz_tp<" + Ns + ", " + As + ">(X, Y, " + tbb + " != 0u);"; break;
+          case K_CZ_TT: call = "if (" + tba + " && " + tbb + ") qj::scal_p<" + Ns + ">(X, Y, -1.f);"; break;
+          case K_SCALE: call = "qj::scal_p<" + Ns + ">(X, Y, " + cf + ");"; break;
+        }
+      }
       auto inst = [&](const char* rr, const char* ii) {
         std::string c2 = call;
         size_t p;
@@ -432,13 +501,168 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       if (!bwd) {
         o << "      " << inst("re", "im") << "\n";
       } else {
-        if (op.rot && gs == 0)
-          o << "      red[" << op.gslot * NTHR << " + tid] = " << g.str() << ";\n";
-        else if (op.rot)
-          o << "      { A g = qj::part_sum<" << (1 << gs) << ", A, CTA>(" << g.str() << "); if ((tid & " << ((1 << gs) - 1)
-            << "u) == 0u) red[" << op.gslot * (NTHR >> gs) << " + (tid >> " << gs << ")] = g; }\n";
-        o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
+        if (op.rot) emit_grad(op, g.str());
+        if (pk) o << "      " << call << "\n";
+        else o << "      " << inst("pr", "pq") << " " << inst("lr", "lq") << "\n";
       }
+    };
+    // A run of diagonal ops (tangent-form RZ: amplitude times 1 - i cs, cs = +-c by the qubit's bit; CZ:
+    // sign flips) is one diagonal factor D per amplitude: a thread-uniform part (RZ and CZ on thread bits)
+    // times one factor per register bit that an RZ or a register-thread CZ touches, combined by a
+    // butterfly over those bits; register-register CZs commute with the rest and are applied after.
+    // Backward: conj(lambda) psi of every amplitude only gains the real factor 1 + c^2 from each RZ
+    // undone, so all of the run's RZ gradients come from sums of w = Im(conj(lambda) psi) taken once at
+    // the start, each times the product rho of 1 + c^2 of the run's RZs undone before it.
+    auto emit_diag_run = [&](const std::vector<int>& run) {
+      std::vector<int> used;   // register bits with a per-bit factor
+      std::vector<int> wused;  // register bits with an RZ gradient (backward)
+      for (int oi : run) {
+        const DevOp& op = s.ops[oi];
+        const int rb = op.kind == K_RZ_R ? op.a : op.kind == K_CZ_RT ? op.a : -1;
+        if (rb >= 0 && std::find(used.begin(), used.end(), rb) == used.end()) used.push_back(rb);
+        if (op.kind == K_RZ_R && std::find(wused.begin(), wused.end(), (int)op.a) == wused.end()) wused.push_back(op.a);
+      }
+      std::sort(used.begin(), used.end());
+      auto uname = [&](int r, int b, char part) {
+        return "u" + std::to_string(r) + "_" + std::to_string(b) + part;
+      };
+      o << "      { // diagonal run of " << run.size() << " ops\n        T tr = T(1), ti = T(0);\n";
+      for (int r : used)
+        o << "        T " << uname(r, 0, 'r') << " = T(1), " << uname(r, 0, 'i') << " = T(0), " << uname(r, 1, 'r')
+          << " = T(1), " << uname(r, 1, 'i') << " = T(0);\n";
+      if (bwd) {
+        o << "        A wt = A(0);";
+        for (size_t k2 = 0; k2 < wused.size(); k2++) o << " A w" << wused[k2] << " = A(0);";
+        o << "\n";
+        for (int i = 0; i < N; i++) {
+          o << "        { const A w = (A)" << LR(i) << " * (A)" << PQ(i) << " - (A)" << LQ(i) << " * (A)" << PR(i) << "; wt += w;";
+          for (int r : wused) o << " w" << r << ((i >> r) & 1 ? " -= w;" : " += w;");
+          o << " }\n";
+        }
+        o << "        T rho = T(1);\n";
+      }
+      std::vector<const DevOp*> czrr;
+      for (int oi : run) {
+        const DevOp& op = s.ops[oi];
+        const std::string cf = "c.cf[" + std::to_string(oi - d.op0) + "]";
+        switch (op.kind) {
+          case K_RZ_R:
+            if (bwd) {
+              emit_grad(op, "(A)w" + std::to_string(op.a) + " * (A)rho");
+              o << "        rho *= T(1) + " << cf << " * " << cf << ";\n";
+            }
+            o << "        { const T cc = " << cf << "; qj::cmul(" << uname(op.a, 0, 'r') << ", " << uname(op.a, 0, 'i')
+              << ", T(1), -cc); qj::cmul(" << uname(op.a, 1, 'r') << ", " << uname(op.a, 1, 'i') << ", T(1), cc); }\n";
+            break;
+          case K_RZ_T: {
+            const std::string sg = "(((tb >> " + std::to_string(op.a) + ") & 1u) ? T(-1) : T(1))";
+            if (bwd) {
+              emit_grad(op, "(A)" + sg + " * (A)wt * (A)rho");
+              o << "        rho *= T(1) + " << cf << " * " << cf << ";\n";
+            }
+            o << "        { const T cc = " << sg << " * " << cf << "; qj::cmul(tr, ti, T(1), -cc); }\n";
+            break;
+          }
+          case K_CZ_TT:
+            o << "        if (((tb >> " << (int)op.a << ") & 1u) && ((tb >> " << (int)op.b << ") & 1u)) { tr = -tr; ti = -ti; }\n";
+            break;
+          case K_CZ_RT:
+            o << "        if ((tb >> " << (int)op.b << ") & 1u) { " << uname(op.a, 1, 'r') << " = -" << uname(op.a, 1, 'r')
+              << "; " << uname(op.a, 1, 'i') << " = -" << uname(op.a, 1, 'i') << "; }\n";
+            break;
+          default:   // K_CZ_RR
+            czrr.push_back(&op);
+            break;
+        }
+      }
+      // D over the used register bits (compressed index), then every amplitude times its D
+      const int nu = (int)used.size();
+      o << "        T dr[" << (1 << nu) << "], di[" << (1 << nu) << "];\n        dr[0] = tr; di[0] = ti;\n";
+      for (int k2 = 0; k2 < nu; k2++)
+        o << "        for (int j = 0; j < " << (1 << k2) << "; j++) { dr[j + " << (1 << k2) << "] = dr[j]; di[j + " << (1 << k2)
+          << "] = di[j]; qj::cmul(dr[j + " << (1 << k2) << "], di[j + " << (1 << k2) << "], " << uname(used[k2], 1, 'r') << ", "
+          << uname(used[k2], 1, 'i') << "); qj::cmul(dr[j], di[j], " << uname(used[k2], 0, 'r') << ", " << uname(used[k2], 0, 'i')
+          << "); }\n";
+      for (int i = 0; i < N; i++) {
+        int idx = 0;
+        for (int k2 = 0; k2 < nu; k2++)
+          if ((i >> used[k2]) & 1) idx |= 1 << k2;
+        const std::string D = "dr[" + std::to_string(idx) + "], di[" + std::to_string(idx) + "]";
+        if (!bwd) {
+          o << "        qj::cmul(re[" << i << "], im[" << i << "], " << D << ");\n";
+        } else if (pk) {
+          o << "        { const float2 x = X[" << i << "], y = Y[" << i << "]; X[" << i << "] = qj::pfma(qj::f2(-di[" << idx
+            << "]), y, __fmul2_rn(qj::f2(dr[" << idx << "]), x)); Y[" << i << "] = qj::pfma(qj::f2(di[" << idx
+            << "]), x, __fmul2_rn(qj::f2(dr[" << idx << "]), y)); }\n";
+        } else {
+          o << "        qj::cmul(pr[" << i << "], pq[" << i << "], " << D << "); qj::cmul(lr[" << i << "], lq[" << i << "], " << D << ");\n";
+        }
+      }
+      for (const DevOp* op : czrr) {
+        const std::string t = std::to_string(N) + ", " + std::to_string(1 << op->a) + ", " + std::to_string(1 << op->b);
+        if (!bwd) o << "        qj::cz<" << t << ">(re, im);\n";
+        else if (pk) o << "        qj::cz_p<" << t << ">(X, Y);\n";
+        else o << "        qj::cz<" << t << ">(pr, pq); qj::cz<" << t << ">(lr, lq);\n";
+      }
+      o << "      }\n";
+    };
+    auto is_diag = [&](int oi) {
+      const int kd = s.ops[oi].kind;
+      return kd == K_RZ_R || kd == K_RZ_T || kd == K_CZ_RR || kd == K_CZ_RT || kd == K_CZ_TT;
+    };
+    for (size_t x = 0; x < order.size();) {
+      size_t y = x;
+      int n_rz = 0;
+      if (s.merge_diag)
+        while (y < order.size() && is_diag(order[y])) n_rz += s.ops[order[y++]].rot;
+      if (n_rz >= 2) {
+        emit_diag_run(std::vector<int>(order.begin() + x, order.begin() + y));
+        x = y;
+      } else {
+        emit_op(order[x++]);
+      }
+    }
+    // ---- prefix partials (backward of the first pass of a product-prefix plan; a.ppart set only there)
+    if (bwd && last && prefix) {
+      const int NT = Ph.n_tbits, NS = 2 * K + 1;
+      o << "      if (a.ppart != nullptr) {\n"
+        << "        const T* ph = reinterpret_cast<const T*>(a.phi) + c.b * a.n * 4;\n"
+        << "        T wr[" << N << "], wi[" << N << "], fr[" << R << "][2], fi[" << R << "][2], Sr, Si, nr[" << R << "][2], ni["
+        << R << "][2];\n";
+      for (int i = 0; i < N; i++) o << "        wr[" << i << "] = " << LR(i) << "; wi[" << i << "] = -" << LQ(i) << ";\n";
+      // a folded CNOT's target register holds the element with that bit flipped where the control is set:
+      // its factor swaps its two values there (for the other qubits' contractions), and its own two
+      // partials swap slots (swr)
+      o << "        qj::u32 swr[" << R << "];\n";
+      for (int r = 0; r < R; r++)
+        o << "        { const qj::u32 sw = " << fold_swap(r) << "; swr[" << r << "] = sw; const T* f = ph + 4 * a.Q["
+          << (int)Ph.rbit[r] << "]; fr[" << r << "][0] = f[2 * sw]; fi[" << r << "][0] = f[2 * sw + 1]; fr[" << r
+          << "][1] = f[2 - 2 * sw]; fi[" << r << "][1] = f[3 - 2 * sw]; }\n";
+      o << "        qj::prefix_contract<T, " << N << ", " << R << ">(wr, wi, fr, fi, Sr, Si, nr, ni);\n";
+      o << "        T gr[" << std::max(NT, 1) << "], gi[" << std::max(NT, 1) << "], Ftr = T(1), Fti = T(0);\n";
+      for (int jb = 0; jb < NT; jb++)
+        o << "        { const T* f = ph + 4 * a.Q[" << (int)Ph.tbit[jb] << "] + 2 * ((tid >> " << jb << ") & 1u); gr[" << jb
+          << "] = f[0]; gi[" << jb << "] = f[1]; qj::cmul(Ftr, Fti, f[0], f[1]); }\n";
+      o << "        T* ws = reinterpret_cast<T*>(c.tile);\n        __syncthreads();\n";
+      for (int r = 0; r < R; r++)
+        for (int b = 0; b < 2; b++)
+          o << "        { T vr = Ftr, vi = Fti; qj::cmul(vr, vi, nr[" << r << "][" << b << " ^ swr[" << r << "]], ni[" << r
+            << "][" << b << " ^ swr[" << r << "]]); qj::prefix_put<T, " << NTHR << ", S_SELF::CTA>(vr, vi, "
+            << 2 * (int)Ph.rbit[r] + b << ", ws, " << NS << ", tid); }\n";
+      for (int jb = 0; jb < NT; jb++) {
+        o << "        { T er = Sr, ei = Si;";
+        for (int j2 = 0; j2 < NT; j2++)
+          if (j2 != jb) o << " qj::cmul(er, ei, gr[" << j2 << "], gi[" << j2 << "]);";
+        o << "\n          const bool hi = ((tid >> " << jb << ") & 1u) != 0u;\n"
+          << "          qj::prefix_put<T, " << NTHR << ", S_SELF::CTA>(hi ? T(0) : er, hi ? T(0) : ei, " << 2 * (int)Ph.tbit[jb]
+          << ", ws, " << NS << ", tid);\n"
+          << "          qj::prefix_put<T, " << NTHR << ", S_SELF::CTA>(hi ? er : T(0), hi ? ei : T(0), " << 2 * (int)Ph.tbit[jb] + 1
+          << ", ws, " << NS << ", tid); }\n";
+      }
+      o << "        { T vr = Ftr, vi = Fti; qj::cmul(vr, vi, Sr, Si); qj::prefix_put<T, " << NTHR << ", S_SELF::CTA>(vr, vi, "
+        << 2 * K << ", ws, " << NS << ", tid); }\n"
+        << "        __syncthreads();\n        qj::prefix_store<T, " << NTHR << ">(c, ws, " << NS << ", c.cf[" << d.n_ops << "]);\n"
+        << "      }\n";
     }
     // ---- store
     if (last) {
@@ -458,19 +682,25 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         }
         o << "        qj::z_reduce_regs<T, " << K << ", " << R << ", " << NTHR
           << ", S_SELF>(c.tile, zt, zs, a.zpart + (c.b * a.tps + c.t) * " << K + 1 << ", tid, c.valid);\n      }\n";
+      } else if (prefix) {
+        // the first pass's backward runs last and stores neither psi nor lambda (api: out = lam_out = nullptr)
+        o << "      (void)sc;\n";
       } else {
         // psi is not stored when the previous pass restarts from a checkpoint (a.out == nullptr)
         o << fold_glob("gf", "gs");
-        o << "      if (a.out != nullptr && c.valid) {\n"
-          << "        qj::scal<" << N << ">(pr, pq, sc);\n        T* po = reinterpret_cast<T*>(a.out);\n";
+        if (pk) o << "      qj::scal_p<" << N << ">(X, Y, sc);\n";
+        o << "      if (a.out != nullptr && c.valid) {\n";
+        if (!pk) o << "        qj::scal<" << N << ">(pr, pq, sc);\n";
+        o << "        T* po = reinterpret_cast<T*>(a.out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(po + 2 * " << goff("gf", "gs", i) << ", pr[" << i << "], pq[" << i << "], pr[" << i + 1
-            << "], pq[" << i + 1 << "]);\n";
-        o << "      }\n      if (a.lam_out != nullptr && c.valid) {\n"
-          << "        qj::scal<" << N << ">(lr, lq, sc);\n        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
+          o << "        qj::stg_pair(po + 2 * " << goff("gf", "gs", i) << ", " << PR(i) << ", " << PQ(i) << ", " << PR(i + 1)
+            << ", " << PQ(i + 1) << ");\n";
+        o << "      }\n      if (a.lam_out != nullptr && c.valid) {\n";
+        if (!pk) o << "        qj::scal<" << N << ">(lr, lq, sc);\n";
+        o << "        T* lo = reinterpret_cast<T*>(a.lam_out);\n";
         for (int i = 0; i < N; i += 2)
-          o << "        qj::stg_pair(lo + 2 * " << goff("gf", "gs", i) << ", lr[" << i << "], lq[" << i << "], lr[" << i + 1
-            << "], lq[" << i + 1 << "]);\n";
+          o << "        qj::stg_pair(lo + 2 * " << goff("gf", "gs", i) << ", " << LR(i) << ", " << LQ(i) << ", " << LR(i + 1)
+            << ", " << LQ(i + 1) << ");\n";
         o << "      }\n";
       }
     } else {
@@ -481,6 +711,8 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         const uint32_t cc = lay_eval(Lo, K, dep_of(Ph, i));
         if (!bwd) {
           o << "      qj::stpx<" << ad << ">(c.tile, so, " << cc << "u, re[" << i << "], im[" << i << "], re[" << i + 1 << "], im[" << i + 1 << "]);\n";
+        } else if (pk) {
+          o << "      qj::stppx<" << ad << ">(c.tile, so, " << cc << "u, X[" << i << "], Y[" << i << "], X[" << i + 1 << "], Y[" << i + 1 << "]);\n";
         } else {
           o << "      qj::stpx<" << ad << ">(c.tile, so, " << cc << "u, pr[" << i << "], pq[" << i << "], pr[" << i + 1 << "], pq[" << i + 1 << "]);\n";
           o << "      qj::stpx<" << ad << ">(c.tile2, so, " << cc << "u, lr[" << i << "], lq[" << i << "], lr[" << i + 1 << "], lq[" << i + 1 << "]);\n";
@@ -526,7 +758,7 @@ static void jit_units(const Schedule& s, std::vector<std::string>& fnames, std::
       const DevPass& d = dir == 0 ? pp.dev : pp.devb;
       const bool bwd = dir == 1;
       const int K = d.k, R = d.R, NTHR = 1 << (K - R);
-      std::string body = gen_spec_body(s, d, bwd);
+      std::string body = gen_spec_body(s, d, bwd, 0, s.has_prefix && &pp == &s.passes[0]);
       // register cap: at least this many CTAs per SM (65536 registers each)
       const int minb = s.max_regs > 0 ? std::max(1, 65536 / (NTHR * s.max_regs)) : 0;
       std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" +

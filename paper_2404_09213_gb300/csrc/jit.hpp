@@ -23,6 +23,8 @@ struct JitArgs {
   double* zpart;
   double* gpart;
   const double* grad_out;
+  const void* phi;
+  double* ppart;
   int64_t tps;
   int64_t gpart_offset;
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch (tiles cover samples b0, b0+1, ...)
@@ -33,7 +35,7 @@ struct JitArgs {
   uint8_t Q[16];
   uint8_t QN[40];
 };
-static_assert(sizeof(JitArgs) == 280, "JitArgs must match qj::Args");
+static_assert(sizeof(JitArgs) == 296, "JitArgs must match qj::Args");
 
 // Layouts of a pass into its kernel arguments. The forward reads the pass's input layout and writes
 // its output layout; the backward undoes the pass, so it reads the output layout and writes the input.

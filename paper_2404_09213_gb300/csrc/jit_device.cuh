@@ -29,6 +29,8 @@ struct Args {
   double* zpart;         // forward <Z> partials [(B * tps) x (K + 1)] or nullptr
   double* gpart;         // backward gradient partials
   const double* grad_out;   // backward: dL/d<Z> (B x n)
+  const void* phi;       // product-state prefix: [B][n][4] phi_q(0), phi_q(1) (first pass only; else nullptr)
+  double* ppart;         // backward of the first pass: prefix contraction partials [(B * tps) x (2K + 1) x 2]
   i64 tps;               // tiles per sample
   i64 gpart_offset;      // first gradient slot of this pass
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch
@@ -189,6 +191,120 @@ __device__ __forceinline__ void scal(T* re, T* im, T s) {
   for (int i = 0; i < N; i++) { re[i] *= s; im[i] *= s; }
 }
 
+// ---------------------------------------------------------------- backward, psi and lambda packed (complex64)
+// X[i] = (Re psi_i, Re lambda_i), Y[i] = (Im psi_i, Im lambda_i). psi and lambda take the same update in
+// the backward, so with the tangent form only (Pauli frame) each update of both states is one packed
+// FP32x2 FMA: 2 packed FMAs per amplitude and rotation instead of 4 scalar ones.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+template <int N, int S>
+__device__ __forceinline__ void ry_p(float2* X, float2* Y, float c) {
+  const float2 cp = f2(c), cn = f2(-c);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;
+      const float2 a = X[i], u = Y[i], b = X[j], v = Y[j];
+      X[i] = pfma(cn, b, a); Y[i] = pfma(cn, v, u);
+      X[j] = pfma(cp, a, b); Y[j] = pfma(cp, u, v);
+    }
+}
+
+template <int N, int S>
+__device__ __forceinline__ void rx_p(float2* X, float2* Y, float c) {
+  const float2 cp = f2(c), cn = f2(-c);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;
+      const float2 a = X[i], u = Y[i], b = X[j], v = Y[j];
+      X[i] = pfma(cp, v, a); Y[i] = pfma(cn, b, u);
+      X[j] = pfma(cp, u, b); Y[j] = pfma(cn, a, v);
+    }
+}
+
+template <int N, int S>
+__device__ __forceinline__ void rz_p(float2* X, float2* Y, float c) {
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    const float cs = (i & S) ? -c : c;
+    const float2 r = X[i], m = Y[i];
+    X[i] = pfma(f2(cs), m, r);
+    Y[i] = pfma(f2(-cs), r, m);
+  }
+}
+
+// RZ on a thread bit: s = +1 (bit 0) or -1 (bit 1) for all of the thread's elements
+template <int N>
+__device__ __forceinline__ void rz_tp(float2* X, float2* Y, float c, float s) {
+  const float2 cp = f2(s * c), cn = f2(-s * c);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    const float2 r = X[i], m = Y[i];
+    X[i] = pfma(cp, m, r);
+    Y[i] = pfma(cn, r, m);
+  }
+}
+
+template <int N, int S>
+__device__ __forceinline__ void hd_p(float2* X, float2* Y) {
+  const float2 m1 = f2(-1.f);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;
+      const float2 a = X[i], u = Y[i], b = X[j], v = Y[j];
+      X[i] = __fadd2_rn(a, b); Y[i] = __fadd2_rn(u, v);
+      X[j] = pfma(m1, b, a); Y[j] = pfma(m1, v, u);
+    }
+}
+
+template <int N, int SA, int SB>
+__device__ __forceinline__ void swp_p(float2* X, float2* Y) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if ((i & SB) == SB && !(i & SA)) {
+      const int j = i | SA;
+      const float2 t = X[i], w = Y[i];
+      X[i] = X[j]; Y[i] = Y[j];
+      X[j] = t; Y[j] = w;
+    }
+}
+
+template <int N, int SA>
+__device__ __forceinline__ void cnot_tp(float2* X, float2* Y, bool ctl) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & SA)) {
+      const int j = i | SA;
+      const float2 a = X[i], u = Y[i], b = X[j], v = Y[j];
+      X[i] = ctl ? b : a; Y[i] = ctl ? v : u;
+      X[j] = ctl ? a : b; Y[j] = ctl ? u : v;
+    }
+}
+
+template <int N, int SA, int SB>
+__device__ __forceinline__ void cz_p(float2* X, float2* Y) {
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if ((i & SA) && (i & SB)) { X[i] = __fmul2_rn(X[i], f2(-1.f)); Y[i] = __fmul2_rn(Y[i], f2(-1.f)); }
+}
+
+template <int N, int SA>
+__device__ __forceinline__ void cz_tp(float2* X, float2* Y, bool o) {
+  const float2 sg = f2(o ? -1.f : 1.f);
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (i & SA) { X[i] = __fmul2_rn(X[i], sg); Y[i] = __fmul2_rn(Y[i], sg); }
+}
+
+template <int N>
+__device__ __forceinline__ void scal_p(float2* X, float2* Y, float s) {
+#pragma unroll
+  for (int i = 0; i < N; i++) { X[i] = __fmul2_rn(X[i], f2(s)); Y[i] = __fmul2_rn(Y[i], f2(s)); }
+}
+
 // ---------------------------------------------------------------- gradient partials (before undoing)
 template <typename T> struct Acc { typedef float t; };
 template <> struct Acc<double> { typedef double t; };
@@ -259,6 +375,86 @@ __device__ __forceinline__ typename Acc<T>::t g_im(const T* pr, const T* pi, con
     h = fm(-(A)li[i], (A)pr[i], h);
   }
   return sum4(g);
+}
+
+// The same inner products on packed registers (psi = .x, lambda = .y; X real parts, Y imaginary parts).
+template <int N, int S>
+__device__ __forceinline__ float g_ry_p(const float2* X, const float2* Y) {
+  float g[4] = {0, 0, 0, 0};
+  int n = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;   // Re(l1* p0) - Re(l0* p1)
+      float& h = g[n++ & 3];
+      h = fm(X[j].y, X[i].x, h);
+      h = fm(Y[j].y, Y[i].x, h);
+      h = fm(-X[i].y, X[j].x, h);
+      h = fm(-Y[i].y, Y[j].x, h);
+    }
+  return sum4(g);
+}
+
+template <int N, int S>
+__device__ __forceinline__ float g_rx_p(const float2* X, const float2* Y) {
+  float g[4] = {0, 0, 0, 0};
+  int n = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++)
+    if (!(i & S)) {
+      const int j = i | S;   // Im(l0* p1) + Im(l1* p0)
+      float& h = g[n++ & 3];
+      h = fm(X[i].y, Y[j].x, h);
+      h = fm(-Y[i].y, X[j].x, h);
+      h = fm(X[j].y, Y[i].x, h);
+      h = fm(-Y[j].y, X[i].x, h);
+    }
+  return sum4(g);
+}
+
+template <int N, int S>
+__device__ __forceinline__ float g_rz_p(const float2* X, const float2* Y) {
+  float g[4] = {0, 0, 0, 0};   // [0], [1]: amplitudes with the bit clear; [2], [3]: set
+  int n0 = 0, n1 = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    float& h = (i & S) ? g[2 + (n1++ & 1)] : g[n0++ & 1];
+    h = fm(X[i].y, Y[i].x, h);
+    h = fm(-Y[i].y, X[i].x, h);
+  }
+  return (g[0] + g[1]) - (g[2] + g[3]);
+}
+
+template <int N>
+__device__ __forceinline__ float g_im_p(const float2* X, const float2* Y) {
+  float g[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    float& h = g[i & 3];
+    h = fm(X[i].y, Y[i].x, h);
+    h = fm(-Y[i].y, X[i].x, h);
+  }
+  return sum4(g);
+}
+
+// Shared memory of the packed backward: one 16-byte word (Re psi, Re lambda, Im psi, Im lambda) per
+// amplitude; a register pair (elements e, e ^ 1) is two words.
+__device__ __forceinline__ void ldpp(const void* tile, u32 w, float2& x0, float2& y0, float2& x1, float2& y1) {
+  const float4 a = reinterpret_cast<const float4*>(tile)[w], b = reinterpret_cast<const float4*>(tile)[w ^ 1u];
+  x0 = make_float2(a.x, a.y); y0 = make_float2(a.z, a.w);
+  x1 = make_float2(b.x, b.y); y1 = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void stpp(void* tile, u32 w, float2 x0, float2 y0, float2 x1, float2 y1) {
+  reinterpret_cast<float4*>(tile)[w] = make_float4(x0.x, x0.y, y0.x, y0.y);
+  reinterpret_cast<float4*>(tile)[w ^ 1u] = make_float4(x1.x, x1.y, y1.x, y1.y);
+}
+template <bool ADD>
+__device__ __forceinline__ void ldppx(const void* tile, u32 s, u32 c, float2& x0, float2& y0, float2& x1, float2& y1) {
+  ldpp(tile, ADD ? s + c : s ^ c, x0, y0, x1, y1);
+}
+template <bool ADD>
+__device__ __forceinline__ void stppx(void* tile, u32 s, u32 c, float2 x0, float2 y0, float2 x1, float2 y1) {
+  stpp(tile, ADD ? s + c : s ^ c, x0, y0, x1, y1);
 }
 
 // Sum over the NTHR threads of a tile group. Groups are aligned blocks of NTHR lanes; when several
@@ -356,6 +552,96 @@ struct Ctx {
   u32 tid;
   bool valid;
 };
+
+// ---------------------------------------------------------------- product-state prefix
+// The qubits' prefix states phi_q (per sample: phi_q(0), phi_q(1) as four reals) multiply into the first
+// pass's starting state psi(x) = prod_q phi_q(x_q). In the backward of that pass, with lambda the
+// adjoint state at the same point, the prefix gradients need
+//   mu_q(b) = sum_{x: x_q = b} conj(lambda(x)) prod_{q' != q} phi_q'(x_q'),
+// which each tile contributes to through 2K + 1 complex partials: for tile bit j and b, the sum over
+// the tile's elements with bit j = b of conj(lambda) times the product of the other tile qubits' phi
+// (slot 2j + b), and the full contraction over the tile (slot 2K); the qubits outside the tile enter on
+// the host side of the reduction (prefix_grad_kernel).
+template <typename T>
+__device__ __forceinline__ void cmul(T& ar, T& ai, T br, T bi) {
+  const T r = ar * br - ai * bi;
+  ai = ar * bi + ai * br;
+  ar = r;
+}
+
+// product of phi over the tile-index bits of tile t (the qubits outside the tile)
+template <typename T>
+__device__ __forceinline__ void phi_nonlocal(const Args& a, const T* ph, i64 t, T& re, T& im) {
+  re = T(1);
+  im = T(0);
+  for (int i = 0; i < a.n_nonlocal; i++) {
+    const T* f = ph + 4 * a.QN[i] + 2 * ((t >> i) & 1);
+    cmul(re, im, f[0], f[1]);
+  }
+}
+
+// Contraction of the thread's N = 2^R register elements w_i = conj(lambda_i) with the register qubits'
+// factors f_r(bit r of i): S = full contraction; nu[r][b] = the same over elements with bit r = b,
+// leaving factor r out (prefix and suffix products over r).
+template <typename T, int N, int R>
+__device__ __forceinline__ void prefix_contract(const T* wr, const T* wi, const T (*fr)[2], const T (*fi)[2],
+                                                T& Sr, T& Si, T (*nr)[2], T (*ni)[2]) {
+  Sr = T(0);
+  Si = T(0);
+#pragma unroll
+  for (int r = 0; r < R; r++) nr[r][0] = nr[r][1] = ni[r][0] = ni[r][1] = T(0);
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    T pr[R + 1], pi[R + 1], sr[R + 1], si[R + 1];
+    pr[0] = T(1); pi[0] = T(0);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      pr[r + 1] = pr[r]; pi[r + 1] = pi[r];
+      cmul(pr[r + 1], pi[r + 1], fr[r][(i >> r) & 1], fi[r][(i >> r) & 1]);
+    }
+    sr[R] = T(1); si[R] = T(0);
+#pragma unroll
+    for (int r = R - 1; r >= 0; r--) {
+      sr[r] = sr[r + 1]; si[r] = si[r + 1];
+      cmul(sr[r], si[r], fr[r][(i >> r) & 1], fi[r][(i >> r) & 1]);
+    }
+    Sr += wr[i] * pr[R] - wi[i] * pi[R];
+    Si += wr[i] * pi[R] + wi[i] * pr[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      T xr = pr[r], xi = pi[r];
+      cmul(xr, xi, sr[r + 1], si[r + 1]);
+      const int b = (i >> r) & 1;
+      nr[r][b] += wr[i] * xr - wi[i] * xi;
+      ni[r][b] += wr[i] * xi + wi[i] * xr;
+    }
+  }
+}
+
+// One prefix partial slot (re, im) of this thread into the per-warp sums in shared memory (ws, one row
+// of 2 * NS values per warp); the caller synchronises before the first and after the last slot.
+template <typename T, int NTHR, int CTA>
+__device__ __forceinline__ void prefix_put(T vr, T vi, int slot, T* ws, int NS, u32 tid) {
+  vr = warp_sum<NTHR, T, CTA>(vr);
+  vi = warp_sum<NTHR, T, CTA>(vi);
+  if ((tid & 31u) == 0u) {
+    ws[(tid >> 5) * 2 * NS + 2 * slot] = vr;
+    ws[(tid >> 5) * 2 * NS + 2 * slot + 1] = vi;
+  }
+}
+
+// The tile's NS slots: warps summed in a fixed order (FP64), times the pass's backward scale sc
+// (lambda_true = sc * lambda in the kernel), into ppart.
+template <typename T, int NTHR>
+__device__ __forceinline__ void prefix_store(const Ctx<T>& c, const T* ws, int NS, T sc) {
+  constexpr int NW = NTHR >= 32 ? NTHR / 32 : 1;
+  const Args& a = *c.a;
+  for (int v = (int)c.tid; v < 2 * NS; v += NTHR) {
+    double s = 0.0;
+    for (int w = 0; w < NW; w++) s += (double)ws[w * 2 * NS + v];
+    if (c.valid) a.ppart[(c.b * a.tps + c.t) * (2 * NS) + v] = s * (double)sc;
+  }
+}
 
 // Block reduction of the <Z> partials of the last forward phase into zrow[0..K]: row[j] is the
 // signed sum over tile bit j, row[K] the tile total. zmap[j] >= 0: register bit; else thread bit -1-zmap[j].
@@ -599,8 +885,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 __device__ __forceinline__ bool wait_dependency(const MultiArgs& m, const Item& it) {
   if (it.wait < 0) return true;
   const unsigned long long t0 = gtimer();
-  while (ld_acquire(m.counters + it.wait) < it.wait_target) {
-    if (ld_acquire(m.status) != 0) return false;
+  for (unsigned polls = 0; ld_acquire(m.counters + it.wait) < it.wait_target; polls++) {
+    if ((polls & 31u) == 31u && *reinterpret_cast<const volatile int*>(m.status) != 0) return false;
     if ((long long)(gtimer() - t0) > m.timeout_ns) {
       atomicExch(m.status, -8);
       return false;

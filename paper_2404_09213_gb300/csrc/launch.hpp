@@ -85,6 +85,33 @@ struct GradReduceArgs {
   int weight_remap, dtype;
 };
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st);
+// the two halves of launch_grad_reduce: per-occurrence sums (occurrences with occ_slot < 0 are skipped),
+// then the sums over occurrences and samples
+cudaError_t launch_grad_gather(const GradReduceArgs& a, cudaStream_t st);
+cudaError_t launch_grad_scatter(const GradReduceArgs& a, cudaStream_t st);
+
+// ---- product-state prefix (single-circuit fused plans)
+struct PrefixArgs {
+  const int32_t* gate_type;     // [G]
+  const int32_t* gate_param;    // [G]
+  const int32_t* pfx_begin;     // [n + 1] CSR over qubits into pfx_gate / pfx_occ
+  const int32_t* pfx_gate;      // prefix gates of every qubit, in circuit order
+  const int32_t* pfx_occ;       // gradient occurrence of each prefix gate (-1: not a rotation)
+  const void* params;
+  const void* inputs;
+  int n_inputs, weight_remap;
+  int n, B;
+  void* phi;                    // [B][n][4] phi_q(0), phi_q(1) in the state's precision
+  const double* ppart;          // [B][tps][2K + 1][2] backward partials of the first pass
+  const uint8_t* Qnl;           // first pass: logical qubit of every tile bit, then of every tile-index bit
+  int K, n_nonlocal;
+  int64_t tps;
+  double* G;                    // [n_occ][B]: dL/dtheta of every occurrence and sample
+};
+// phi_q = G_m ... G_1 |0> in FP64 for every (sample, qubit), stored in the state's precision
+cudaError_t launch_prefix_phi(const PrefixArgs& a, int dtype, cudaStream_t st);
+// mu_q from the partials, then dL/dtheta of every prefix rotation into G
+cudaError_t launch_prefix_grad(const PrefixArgs& a, int dtype, cudaStream_t st);
 
 // ---- several circuits
 struct ZCirc {

@@ -396,9 +396,10 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
   if (o.mode != QSIM_FUSED) return mfail(QSIM_ERR_ARG, "multi-circuit plans use the fused mode");
   if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return mfail(QSIM_ERR_ARG, "bad dtype");
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
-      (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs != 0 || o.pauli_frame != 0 || o.reserved != 0)
+      (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs != 0 || o.pauli_frame != 0 || o.scalar_bwd != 0 ||
+      o.product_prefix != 0 || o.split_diagonal != 0)
     return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], weight_remap 0 or 1, max_regs 0 "
-                               "(multi-circuit kernels size their own CTAs), pauli_frame 0, reserved 0");
+                               "(multi-circuit kernels size their own CTAs), pauli_frame 0, scalar_bwd 0, product_prefix 0, split_diagonal 0");
   if (o.k == 0 || o.k > multi_max_k(o.dtype)) o.k = multi_max_k(o.dtype);
   auto* m = new qsim_multi_s();
   m->opts = o;

@@ -336,6 +336,8 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
   s.mode = o.mode;
   s.max_regs = o.max_regs;
   s.pauli_frame = o.pauli_frame == 1 && o.mode == QSIM_FUSED;
+  s.packed_bwd = s.pauli_frame && o.dtype == QSIM_C64 && o.scalar_bwd == 0;
+  s.merge_diag = s.pauli_frame && o.split_diagonal == 0;
   int k = o.k > 0 ? o.k : 12;
   int c = o.contiguous_bits > 0 ? o.contiguous_bits : 4;
   if (k > kMaxTileBits) {
@@ -390,6 +392,26 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
   // the store addressing). The last pass writes the canonical layout.
   std::vector<char> done(G, 0);
   int n_done = 0;
+  if (o.product_prefix == 1) {
+    // a single-qubit gate on a qubit that no two-qubit gate has touched yet acts on that qubit's |0>
+    // factor alone: it joins the qubit's prefix and leaves the fused passes
+    s.prefix.assign(n, {});
+    std::vector<char> entangled(n, 0);
+    for (int i = 0; i < G; i++) {
+      const Gate& g = gates[i];
+      if (is_1q(g.type)) {
+        if (!entangled[g.t0]) {
+          s.prefix[g.t0].push_back(i);
+          done[i] = 1;
+          n_done++;
+        }
+      } else {
+        entangled[g.t0] = entangled[g.c0] = 1;
+      }
+    }
+    s.has_prefix = n_done > 0;
+    if (!s.has_prefix) s.prefix.clear();
+  }
   std::vector<int> phys(n), at(n);   // current layout: logical qubit -> physical bit, and inverse
   for (int q = 0; q < n; q++) {
     phys[q] = n - 1 - q;
@@ -475,7 +497,7 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
         S = greedy(S1, dn, took);
       }
     }
-    if (took.empty() && G > 0) {
+    if (took.empty() && n_done < G) {   // (a circuit whose gates all went to the prefix gets one empty pass)
       err = "internal: fusion made no progress";
       return QSIM_ERR_ARG;
     }
@@ -526,12 +548,21 @@ int build_schedule(const std::vector<Gate>& gates, int n, const qsim_plan_opts& 
     pp.devb.R = Rb;
     int rc = build_phases(s, pp, pp.dev, false, w0, rng, err);
     if (rc) return rc;
-    rc = build_phases(s, pp, pp.devb, true, w0, rng, err);
+    // packed backward: one 16-byte word per amplitude (psi and lambda), like complex128
+    rc = build_phases(s, pp, pp.devb, true, s.packed_bwd ? 0 : w0, rng, err);
     if (rc) return rc;
     pp.dev.gpart_offset = s.total_gslots;
     pp.devb.gpart_offset = s.total_gslots;
     s.total_gslots += pp.devb.n_gslots;
   }
+  // prefix rotations are gradient occurrences too, computed from the prefix contraction (no pass, no slot)
+  for (int q = 0; q < (int)s.prefix.size(); q++)
+    for (int gi : s.prefix[q])
+      if (is_rot(gates[gi].type)) {
+        s.grad_gate.push_back(gi);
+        s.grad_pass.push_back(-1);
+        s.grad_slot.push_back(-1);
+      }
   return QSIM_OK;
 }
 
@@ -540,7 +571,13 @@ std::string describe_schedule(const Schedule& s) {
   std::ostringstream o;
   o << "{\"n\":" << s.n << ",\"k\":" << s.k << ",\"R\":" << s.R << ",\"Rb\":" << s.Rb << ",\"c\":" << s.c
     << ",\"mode\":" << s.mode << ",\"n_params\":" << s.n_params << ",\"n_inputs\":" << s.n_inputs
-    << ",\"passes\":[";
+    << ",\"prefix\":[";
+  for (size_t q = 0; q < s.prefix.size(); q++) {
+    o << (q ? "," : "") << "[";
+    for (size_t i = 0; i < s.prefix[q].size(); i++) o << (i ? "," : "") << s.prefix[q][i];
+    o << "]";
+  }
+  o << "],\"passes\":[";
   for (size_t p = 0; p < s.passes.size(); p++) {
     const auto& pp = s.passes[p];
     const auto& d = pp.dev;

@@ -28,6 +28,12 @@ struct Schedule {
   int n = 0, k = 0, R = 0, Rb = 0, c = 0, dtype = 0, mode = 0;
   int max_regs = 0;                  // register cap of the pass kernels (0: none)
   bool pauli_frame = false;          // rotations run the tangent form only (cotangent Paulis in a frame)
+  bool packed_bwd = false;           // backward holds (psi, lambda) register pairs, packed FP32x2 updates
+  bool merge_diag = false;           // runs of diagonal ops become one factor per amplitude (tangent form only)
+  // product-state prefix: per qubit, the single-qubit gates before its first two-qubit gate (in order),
+  // merged into phi_q and taken out of the fused passes
+  bool has_prefix = false;
+  std::vector<std::vector<int>> prefix;
   int n_params = 0, n_inputs = 0;
   std::vector<Gate> gates;
   std::vector<PassPlan> passes;

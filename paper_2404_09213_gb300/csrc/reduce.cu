@@ -230,23 +230,41 @@ __host__ __device__ inline int frame_step(Frame& f, int ty, int q, int c, int co
   return sigma;
 }
 
-// one thread per sample over every op of every pass in execution order
+// One thread per sample over every op of every pass in execution order. The ops' gate, kind and qubits
+// are the same for every sample: each block stages them in shared memory a chunk at a time, so a step of
+// the walk reads shared memory plus one byte of the sample's form (coalesced across the warp).
 __global__ void frame_walk_kernel(CoefArgs a) {
+  constexpr int CH = 512;
+  __shared__ int s_g[CH];
+  __shared__ int s_meta[CH];   // kind | q0 << 8 | (q1 + 1) << 16
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.B) return;
   Frame f;
-  for (int e = a.exec_begin[0]; e < a.exec_begin[a.P]; e++) {
-    const int g = a.exec_gates[e];
-    if (g < 0) continue;   // rescale op
-    const int ty = a.gate_type[g];
-    const int64_t gi = (int64_t)g * a.B + b;
-    const int cot = ty <= QSIM_RZ ? a.form[gi] : 0;
-    const int sg = frame_step(f, ty, a.gate_q0[g], a.gate_q1[g], cot);
-    if (ty <= QSIM_RZ) a.sigma[gi] = (int8_t)sg;
+  const int e0 = a.exec_begin[0], e1 = a.exec_begin[a.P];
+  for (int base = e0; base < e1; base += CH) {
+    const int m = min(CH, e1 - base);
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int g = a.exec_gates[base + i];
+      s_g[i] = g;
+      s_meta[i] = g < 0 ? 0 : (a.gate_type[g] | (a.gate_q0[g] << 8) | ((a.gate_q1[g] + 1) << 16));
+    }
+    __syncthreads();
+    if (b < a.B)
+      for (int i = 0; i < m; i++) {
+        const int g = s_g[i];
+        if (g < 0) continue;   // rescale op
+        const int meta = s_meta[i], ty = meta & 255;
+        const int64_t gi = (int64_t)g * a.B + b;
+        const int cot = ty <= QSIM_RZ ? a.form[gi] : 0;
+        const int sg = frame_step(f, ty, (meta >> 8) & 255, ((meta >> 16) & 255) - 1, cot);
+        if (ty <= QSIM_RZ) a.sigma[gi] = (int8_t)sg;
+      }
   }
-  a.frame_x[b] = f.x;
-  a.frame_z[b] = f.z;
-  a.frame_k[b] = f.k;
+  if (b < a.B) {
+    a.frame_x[b] = f.x;
+    a.frame_z[b] = f.z;
+    a.frame_k[b] = f.k;
+  }
 }
 
 cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
@@ -385,6 +403,7 @@ cudaError_t launch_frame_gsign(const double* grad_out, const uint64_t* fx, int n
 __global__ void grad_gather_kernel(GradReduceArgs a) {
   __shared__ double sh[32];
   const int j = blockIdx.x / a.B, b = blockIdx.x - (blockIdx.x / a.B) * a.B;
+  if (a.occ_slot[j] < 0) return;   // a prefix rotation: no pass partials (launch_prefix_grad writes G)
   const double* src = a.gpart + (a.occ_slot[j] * a.B + b) * a.tiles_per_sample;
   double acc = 0.0;
   for (int64_t t = threadIdx.x; t < a.tiles_per_sample; t += blockDim.x) acc += src[t];
@@ -414,17 +433,177 @@ __global__ void grad_scatter_kernel(GradReduceArgs a) {
 }
 
 cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_grad_gather(a, st);
+  if (e != cudaSuccess) return e;
+  return launch_grad_scatter(a, st);
+}
+
+cudaError_t launch_grad_gather(const GradReduceArgs& a, cudaStream_t st) {
   if (a.n_occ > 0 && a.B > 0) {
     grad_gather_kernel<<<(unsigned)(a.n_occ * a.B), a.tiles_per_sample >= 256 ? 256 : 32, 0, st>>>(a);
     g_kernel_launches++;
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_scatter(const GradReduceArgs& a, cudaStream_t st) {
   const int64_t total = (a.dparams ? a.n_params : 0) + (a.dinputs ? (int64_t)a.B * a.n_inputs : 0);
   if (total > 0) {
     grad_scatter_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(a);
     g_kernel_launches++;
   }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ product-state prefix
+// A single-qubit gate that acts on a qubit before any two-qubit gate touches it acts on that qubit's |0>
+// factor alone, so the state after all of them is the product of phi_q = G_m ... G_1 |0> (the per-qubit
+// embedding matrices of Sec. "Gate Matrix Caching", applied to |0> and merged). Complex 2x2 matrices in
+// FP64, m[row][col] = (re, im).
+struct C2 {
+  double r, i;
+};
+__device__ __forceinline__ C2 cm(C2 a, C2 b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ C2 ca(C2 a, C2 b) { return {a.r + b.r, a.i + b.i}; }
+
+template <typename T>
+__device__ double prefix_angle(const PrefixArgs& a, int g, int b) {
+  const int pr = a.gate_param[g];
+  const T* params = reinterpret_cast<const T*>(a.params);
+  const T* inputs = reinterpret_cast<const T*>(a.inputs);
+  return pr >= 0 ? weight(params[pr], a.weight_remap)
+                 : weight(inputs[(int64_t)b * a.n_inputs + (-2 - pr)], a.weight_remap == 2);
+}
+
+// matrix of gate type ty at angle th (rotations exp(-i th P / 2))
+__device__ void gate_m(int ty, double th, C2 m[2][2]) {
+  const double kH = 0.70710678118654752440;
+  double s = 0.0, c = 1.0;
+  if (ty <= QSIM_RZ) sincos(0.5 * th, &s, &c);
+  switch (ty) {
+    case QSIM_RX: m[0][0] = {c, 0}; m[0][1] = {0, -s}; m[1][0] = {0, -s}; m[1][1] = {c, 0}; break;
+    case QSIM_RY: m[0][0] = {c, 0}; m[0][1] = {-s, 0}; m[1][0] = {s, 0}; m[1][1] = {c, 0}; break;
+    case QSIM_RZ: m[0][0] = {c, -s}; m[0][1] = {0, 0}; m[1][0] = {0, 0}; m[1][1] = {c, s}; break;
+    case QSIM_H: m[0][0] = {kH, 0}; m[0][1] = {kH, 0}; m[1][0] = {kH, 0}; m[1][1] = {-kH, 0}; break;
+    default: m[0][0] = {0, 0}; m[0][1] = {1, 0}; m[1][0] = {1, 0}; m[1][1] = {0, 0}; break;   // X
+  }
+}
+
+// thread per (sample, qubit)
+template <typename T>
+__global__ void prefix_phi_kernel(PrefixArgs a) {
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (int64_t)a.B * a.n) return;
+  const int b = (int)(id / a.n), q = (int)(id - (int64_t)b * a.n);
+  C2 v0 = {1, 0}, v1 = {0, 0};
+  for (int e = a.pfx_begin[q]; e < a.pfx_begin[q + 1]; e++) {
+    const int g = a.pfx_gate[e], ty = a.gate_type[g];
+    C2 m[2][2];
+    gate_m(ty, ty <= QSIM_RZ ? prefix_angle<T>(a, g, b) : 0.0, m);
+    const C2 w0 = ca(cm(m[0][0], v0), cm(m[0][1], v1)), w1 = ca(cm(m[1][0], v0), cm(m[1][1], v1));
+    v0 = w0;
+    v1 = w1;
+  }
+  T* out = reinterpret_cast<T*>(a.phi) + id * 4;
+  out[0] = (T)v0.r; out[1] = (T)v0.i; out[2] = (T)v1.r; out[3] = (T)v1.i;
+}
+
+// Warp per (sample, qubit). mu_q(beta) = sum over the first pass's tiles of the tile's partial for q
+// (tile qubit: slot 2j + beta; qubit outside the tile: slot 2K where the tile has bit beta) times the
+// phi of the tile's other outside qubits. Then the adjoint of the short prefix chain: with r the row
+// vector mu^T G_m ... G_{j+1} and v_j = G_j ... G_1 |0>,
+//   dL/dtheta_j = 2 Re[ r (-i/2) P_j v_j ],
+// walking j down from m (r <- r G_j, v <- G_j^dag v).
+template <typename T>
+__global__ void prefix_grad_kernel(PrefixArgs a) {
+  const int b = blockIdx.x / a.n, q = blockIdx.x - (blockIdx.x / a.n) * a.n;
+  const unsigned lane = threadIdx.x;
+  int jq = -1, iq = -1;   // q as tile bit jq or tile-index bit iq of the first pass
+  for (int j = 0; j < a.K; j++)
+    if (a.Qnl[j] == q) jq = j;
+  for (int i = 0; i < a.n_nonlocal; i++)
+    if (a.Qnl[a.K + i] == q) iq = i;
+  const T* ph = reinterpret_cast<const T*>(a.phi) + (int64_t)b * a.n * 4;
+  const int NS = 2 * a.K + 1;
+  C2 mu0 = {0, 0}, mu1 = {0, 0};
+  for (int64_t t = lane; t < a.tps; t += 32) {
+    C2 F = {1, 0};
+    for (int i = 0; i < a.n_nonlocal; i++) {
+      if (i == iq) continue;
+      const T* f = ph + 4 * a.Qnl[a.K + i] + 2 * ((t >> i) & 1);
+      F = cm(F, C2{(double)f[0], (double)f[1]});
+    }
+    const double* row = a.ppart + ((int64_t)b * a.tps + t) * NS * 2;
+    if (jq >= 0) {
+      mu0 = ca(mu0, cm(C2{row[4 * jq], row[4 * jq + 1]}, F));
+      mu1 = ca(mu1, cm(C2{row[4 * jq + 2], row[4 * jq + 3]}, F));
+    } else {
+      const C2 v = cm(C2{row[4 * a.K], row[4 * a.K + 1]}, F);
+      if ((t >> iq) & 1) mu1 = ca(mu1, v);
+      else mu0 = ca(mu0, v);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {   // fixed tree: the same order every run
+    mu0.r += __shfl_xor_sync(0xffffffffu, mu0.r, off);
+    mu0.i += __shfl_xor_sync(0xffffffffu, mu0.i, off);
+    mu1.r += __shfl_xor_sync(0xffffffffu, mu1.r, off);
+    mu1.i += __shfl_xor_sync(0xffffffffu, mu1.i, off);
+  }
+  if (lane != 0) return;
+  // v = phi_q in FP64, then the chain backwards
+  C2 v0 = {1, 0}, v1 = {0, 0};
+  const int e0 = a.pfx_begin[q], e1 = a.pfx_begin[q + 1];
+  for (int e = e0; e < e1; e++) {
+    const int g = a.pfx_gate[e], ty = a.gate_type[g];
+    C2 m[2][2];
+    gate_m(ty, ty <= QSIM_RZ ? prefix_angle<T>(a, g, b) : 0.0, m);
+    const C2 w0 = ca(cm(m[0][0], v0), cm(m[0][1], v1)), w1 = ca(cm(m[1][0], v0), cm(m[1][1], v1));
+    v0 = w0;
+    v1 = w1;
+  }
+  C2 r0 = mu0, r1 = mu1;
+  for (int e = e1 - 1; e >= e0; e--) {
+    const int g = a.pfx_gate[e], ty = a.gate_type[g];
+    C2 m[2][2];
+    gate_m(ty, ty <= QSIM_RZ ? prefix_angle<T>(a, g, b) : 0.0, m);
+    if (ty <= QSIM_RZ && a.pfx_occ[e] >= 0) {
+      // P v with P = X, Y or Z, then times -i/2
+      C2 p0, p1;
+      if (ty == QSIM_RX) { p0 = v1; p1 = v0; }
+      else if (ty == QSIM_RY) { p0 = {v1.i, -v1.r}; p1 = {-v0.i, v0.r}; }   // Y = [[0, -i], [i, 0]]
+      else { p0 = v0; p1 = {-v1.r, -v1.i}; }
+      const C2 d0 = {0.5 * p0.i, -0.5 * p0.r}, d1 = {0.5 * p1.i, -0.5 * p1.r};   // (-i/2) P v
+      const C2 s = ca(cm(r0, d0), cm(r1, d1));
+      a.G[(int64_t)a.pfx_occ[e] * a.B + b] = 2.0 * s.r;
+    }
+    // r <- r G_j ; v <- G_j^dag v
+    const C2 n0 = ca(cm(r0, m[0][0]), cm(r1, m[1][0])), n1 = ca(cm(r0, m[0][1]), cm(r1, m[1][1]));
+    r0 = n0;
+    r1 = n1;
+    const C2 c00 = {m[0][0].r, -m[0][0].i}, c01 = {m[1][0].r, -m[1][0].i};   // rows of G^dag
+    const C2 c10 = {m[0][1].r, -m[0][1].i}, c11 = {m[1][1].r, -m[1][1].i};
+    const C2 u0 = ca(cm(c00, v0), cm(c01, v1)), u1 = ca(cm(c10, v0), cm(c11, v1));
+    v0 = u0;
+    v1 = u1;
+  }
+}
+
+cudaError_t launch_prefix_phi(const PrefixArgs& a, int dtype, cudaStream_t st) {
+  const int64_t tot = (int64_t)a.B * a.n;
+  if (tot == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((tot + 127) / 128);
+  if (dtype == QSIM_C128) prefix_phi_kernel<double><<<blocks, 128, 0, st>>>(a);
+  else prefix_phi_kernel<float><<<blocks, 128, 0, st>>>(a);
+  g_kernel_launches++;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefix_grad(const PrefixArgs& a, int dtype, cudaStream_t st) {
+  const int64_t tot = (int64_t)a.B * a.n;
+  if (tot == 0) return cudaSuccess;
+  if (dtype == QSIM_C128) prefix_grad_kernel<double><<<(unsigned)tot, 32, 0, st>>>(a);
+  else prefix_grad_kernel<float><<<(unsigned)tot, 32, 0, st>>>(a);
+  g_kernel_launches++;
   return cudaGetLastError();
 }
 

@@ -96,6 +96,149 @@ def test_random_circuits_both_forms(q, seed, n, dtype, k, c, ckpt):
     _random_case(q, seed, n, dtype, "fused", k, c, pauli_frame=False, checkpoint_passes=ckpt)
 
 
+# complex64 Pauli-frame plans update psi and lambda together with packed FP32x2 FMAs in the backward by
+# default; the scalar variant against the oracle on the same random circuits (every gate kind)
+@pytest.mark.parametrize("seed,n,k,c,ckpt", [(40, 6, 5, 2, 0), (41, 10, 8, 4, 1), (42, 12, 12, 4, 0)])
+def test_random_circuits_frame_scalar_backward(q, seed, n, k, c, ckpt):
+    _random_case(q, seed, n, "c64", "fused", k, c, pauli_frame=True, scalar_bwd=True, checkpoint_passes=ckpt)
+
+
+# product-state prefix (on by default): every qubit's single-qubit gates before its first two-qubit gate
+# become phi_q, the first pass starts from their product and their gradients come from one contraction
+def _prefix_circuit(rng, n, g, n_params=6, n_inputs=3):
+    """A random circuit whose qubits start with runs of every single-qubit gate kind (rotations on shared
+    parameters and on input columns, H and X) before the entanglers begin."""
+    head = []
+    for qb in range(n):
+        for _ in range(int(rng.integers(0, 4))):
+            k = int(rng.choice([W.RX, W.RY, W.RZ, W.H, W.X]))
+            if k in (W.RX, W.RY, W.RZ):
+                p = W.input_param(int(rng.integers(0, n_inputs))) if rng.uniform() < 0.4 else int(rng.integers(0, n_params))
+                head.append(W.gate(k, (qb,), param=p))
+            else:
+                head.append(W.gate(k, (qb,)))
+    return head + random_circuit(rng, n, g, n_params, n_inputs)
+
+
+@pytest.mark.parametrize("seed,n,dtype,k,c,ckpt", [(50, 3, "c64", 3, 1, 0), (51, 7, "c128", 5, 2, 1),
+                                                   (52, 10, "c64", 8, 4, 1), (53, 12, "c64", 12, 4, 0),
+                                                   (54, 13, "c128", 11, 4, 1), (55, 9, "c64", 6, 2, 2)])
+def test_product_prefix_against_oracle(q, seed, n, dtype, k, c, ckpt):
+    rng = np.random.default_rng(200 + seed)
+    n_par, n_in, B = 6, 3, 3
+    gates = _prefix_circuit(rng, n, 6 * n, n_par, n_in)
+    params = rng.uniform(0, 2 * math.pi, n_par)
+    inputs = rng.uniform(0, math.pi, (B, n_in))
+    g = rng.uniform(-1, 1, (B, n))
+    wl = W.Workload("pfx", n, B, dtype, gates, params, inputs, g)
+    r = run(q, wl, dtype, "fused", k=k, contiguous_bits=c, checkpoint_passes=ckpt, product_prefix=True)
+    assert any(r["plan"].describe()["prefix"])
+    pr, ir = rounded(wl, dtype)
+    psi = oracle.simulate_strided(gates, n, pr, ir)
+    t = TOL[dtype]
+    np.testing.assert_allclose(r["states"], psi, atol=t["state"], rtol=0)
+    np.testing.assert_allclose(r["z"], oracle.expval_z(psi, n), atol=t["z"], rtol=0)
+    dp, di = oracle.grad_adjoint(gates, n, pr, ir, g)
+    check_grad(r["dp"], dp, dtype, "dparams")
+    check_grad(r["di"], di, dtype, "dinputs")
+
+
+def test_product_prefix_whole_circuit_and_initial_state(q):
+    # no entangler at all: every gate is in a prefix and the single pass only writes the product state;
+    # then an initial state, which the prefix cannot use (an internal plan without it runs instead)
+    rng = np.random.default_rng(9)
+    n, B = 8, 2
+    gates = [W.gate(W.RX, (qb,), param=W.input_param(qb)) for qb in range(n)]
+    gates += [W.gate(W.RY, (qb,), param=qb) for qb in range(n)] + [W.gate(W.H, (3,))]
+    wl = W.Workload("prod", n, B, "c64", gates, rng.uniform(0, 2 * math.pi, n), rng.uniform(0, math.pi, (B, n)),
+                    rng.uniform(-1, 1, (B, n)))
+    r = run(q, wl, "c64", "fused", k=6)
+    pr, ir = rounded(wl, "c64")
+    psi = oracle.simulate_strided(gates, n, pr, ir)
+    np.testing.assert_allclose(r["states"], psi, atol=1e-5, rtol=0)
+    dp, di = oracle.grad_adjoint(gates, n, pr, ir, wl.grad_out)
+    check_grad(r["dp"], dp, "c64", "dparams (product circuit)")
+    check_grad(r["di"], di, "c64", "dinputs (product circuit)")
+    init = rng.normal(size=(B, 2 ** n)) + 1j * rng.normal(size=(B, 2 ** n))
+    init /= np.linalg.norm(init, axis=1, keepdims=True)
+    r2 = run(q, wl, "c64", "fused", k=6, init=torch.tensor(init, dtype=torch.complex64, device="cuda"))
+    i64 = init.astype(np.complex64).astype(complex)
+    psi2 = oracle.simulate_strided(gates, n, pr, ir, init=i64)
+    np.testing.assert_allclose(r2["states"], psi2, atol=1e-5, rtol=0)
+    dp2, di2 = oracle.grad_adjoint(gates, n, pr, ir, wl.grad_out, init=i64)
+    check_grad(r2["dp"], dp2, "c64", "dparams (initial state)")
+    check_grad(r2["di"], di2, "c64", "dinputs (initial state)")
+
+
+def test_product_prefix_equals_plain_plan_on_c3_ansatz(q):
+    # the 14-qubit version of the 20-qubit workload: the prefix holds the RX encoding and the first layer
+    wl = W.config(3, n=14, batch=4)
+    a = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1, product_prefix=False)
+    b = run(q, wl, "c64", "fused", k=10, checkpoint_passes=1, product_prefix=True)
+    assert [len(x) for x in b["plan"].describe()["prefix"]] == [3] * 14
+    assert b["plan"].info()["n_passes"] <= a["plan"].info()["n_passes"]
+    np.testing.assert_allclose(b["states"], a["states"], atol=2e-5, rtol=0)
+    np.testing.assert_allclose(b["z"], a["z"], atol=2e-5, rtol=0)
+    check_grad(b["dp"], a["dp"], "c64", "dparams, prefix vs none")
+    check_grad(b["di"], a["di"], "c64", "dinputs, prefix vs none")
+
+
+# runs of consecutive diagonal ops (RZ, CZ) are merged into one factor per amplitude, and their backward
+# gradients come from one pass (default with the Pauli frame): circuits dense in such runs, vs the oracle
+def _diagonal_heavy_circuit(rng, n, g, n_params=6, n_inputs=2):
+    out = []
+    while len(out) < g:
+        if rng.uniform() < 0.25:
+            out += random_circuit(rng, n, 2, n_params, n_inputs)
+            continue
+        for _ in range(int(rng.integers(2, 9))):
+            if n >= 2 and rng.uniform() < 0.3:
+                c, t = rng.choice(n, 2, replace=False)
+                out.append(W.gate(W.CZ, (int(t),), (int(c),)))
+            else:
+                p = W.input_param(int(rng.integers(0, n_inputs))) if rng.uniform() < 0.3 else int(rng.integers(0, n_params))
+                out.append(W.gate(W.RZ, (int(rng.integers(0, n)),), param=p))
+    return out
+
+
+@pytest.mark.parametrize("seed,n,dtype,k,c,ckpt", [(60, 5, "c64", 4, 1, 0), (61, 8, "c128", 6, 2, 1),
+                                                   (62, 11, "c64", 9, 3, 1), (63, 12, "c64", 12, 4, 0),
+                                                   (64, 13, "c128", 11, 4, 0)])
+def test_diagonal_runs_against_oracle(q, seed, n, dtype, k, c, ckpt):
+    rng = np.random.default_rng(300 + seed)
+    n_par, n_in, B = 6, 2, 3
+    gates = [W.gate(W.H, (qb,)) for qb in range(n)] + _diagonal_heavy_circuit(rng, n, 10 * n, n_par, n_in)
+    params = rng.uniform(0, 2 * math.pi, n_par)
+    inputs = rng.uniform(0, math.pi, (B, n_in))
+    g = rng.uniform(-1, 1, (B, n))
+    wl = W.Workload("diag", n, B, dtype, gates, params, inputs, g)
+    r = run(q, wl, dtype, "fused", k=k, contiguous_bits=c, checkpoint_passes=ckpt)
+    assert "diagonal run" in r["plan"].kernel_source()
+    pr, ir = rounded(wl, dtype)
+    psi = oracle.simulate_strided(gates, n, pr, ir)
+    t = TOL[dtype]
+    np.testing.assert_allclose(r["states"], psi, atol=t["state"], rtol=0)
+    np.testing.assert_allclose(r["z"], oracle.expval_z(psi, n), atol=t["z"], rtol=0)
+    dp, di = oracle.grad_adjoint(gates, n, pr, ir, g)
+    check_grad(r["dp"], dp, dtype, "dparams")
+    check_grad(r["di"], di, dtype, "dinputs")
+
+
+@pytest.mark.parametrize("which,dtype", [("c3", "c64"), ("hea", "c64"), ("hea", "c128")])
+def test_merged_diagonal_runs_equal_split(q, which, dtype):
+    wl = W.config(3, n=14, batch=4, dtype=dtype) if which == "c3" else W.Workload(
+        "hea", 12, 3, dtype, W.hea_cz_ansatz(12, 4), *[np.random.default_rng(5).uniform(0, 3, s)
+                                                       for s in ((96,), (3, 12), (3, 12))])
+    k = 10 if dtype == "c64" else 9
+    a = run(q, wl, dtype, "fused", k=k, checkpoint_passes=1, split_diagonal=True)
+    b = run(q, wl, dtype, "fused", k=k, checkpoint_passes=1)
+    t = 2e-5 if dtype == "c64" else 1e-12
+    np.testing.assert_allclose(b["states"], a["states"], atol=t, rtol=0)
+    np.testing.assert_allclose(b["z"], a["z"], atol=t, rtol=0)
+    check_grad(b["dp"], a["dp"], dtype, "dparams, merged vs split")
+    check_grad(b["di"], a["di"], dtype, "dinputs, merged vs split")
+
+
 def test_pauli_frame_agrees_with_both_forms(q):
     # the same 14-qubit checkpointed workload both ways: results within the complex64 tolerances
     wl = W.config(3, n=14, batch=4)

@@ -57,7 +57,9 @@ def test_schedule_invariants(q, name, gates, n, kw):
     p = q.Plan(gates, n, **kw)
     d = p.describe()
     k, R = d["k"], d["R"]
-    order = [g for ps in d["passes"] for g in ps["gates"]]
+    # the product-state prefix (each qubit's single-qubit gates before its first two-qubit gate) runs
+    # before every pass; the per-wire order check below also proves no prefix gate follows an entangler
+    order = [g for pq in d["prefix"] for g in pq] + [g for ps in d["passes"] for g in ps["gates"]]
     # every gate exactly once
     assert sorted(order) == list(range(len(gates)))
     # per-wire order preserved across passes
@@ -216,8 +218,12 @@ def test_per_gate_schedule(q):
 def test_empty_circuit_and_single_qubit(q):
     d = q.Plan([], 3).describe()
     assert len(d["passes"]) == 1 and d["passes"][0]["gates"] == []
-    d1 = q.Plan([W.gate(W.RX, (0,), param=0), W.gate(W.H, (0,))], 1).describe()
+    one = [W.gate(W.RX, (0,), param=0), W.gate(W.H, (0,))]
+    d1 = q.Plan(one, 1, product_prefix=False).describe()
     assert d1["k"] == 1 and [ps["gates"] for ps in d1["passes"]] == [[0, 1]]
+    # with the product prefix both gates become the qubit's prefix state and the one pass has no ops
+    d2 = q.Plan(one, 1).describe()
+    assert d2["prefix"] == [[0, 1]] and [ps["gates"] for ps in d2["passes"]] == [[]]
 
 
 @pytest.mark.parametrize("n,kw", [(20, {}), (16, {"dtype": "c128"}), (14, {"k": 10}), (13, {"k": 12}),
@@ -245,4 +251,25 @@ def test_rotating_low_bits_cut_the_passes():
     wl = W.config(3)
     assert qq.Plan(wl.gates, wl.n, k=12, rotate_low_bits=True).info()["n_passes"] <= 20
     assert qq.Plan(wl.gates, wl.n, k=11, rotate_low_bits=True).info()["n_passes"] <= 25
-    assert qq.Plan(wl.gates, wl.n, k=12).info()["n_passes"] == 24
+    assert qq.Plan(wl.gates, wl.n, k=12, product_prefix=False).info()["n_passes"] == 24
+    # the product prefix takes the encoding and the first layer out of the passes: one pass fewer
+    assert qq.Plan(wl.gates, wl.n, k=12).info()["n_passes"] == 23
+
+
+def test_product_prefix_collects_single_qubit_gates_before_first_entangler():
+    import paper_2404_09213_gb300 as q
+    RX, RY, RZ, H, X, CX, CZ = range(7)
+    g = W.gate
+    gates = [g(RX, (0,), param=W.input_param(0)), g(RY, (0,), param=0), g(H, (2,)), g(CX, (1,), (0,)),
+             g(RZ, (1,), param=1), g(RY, (0,), param=2), g(X, (2,)), g(RZ, (3,), param=3), g(CZ, (3,), (2,)),
+             g(RY, (3,), param=4)]
+    d = q.Plan(gates, 4, k=3, contiguous_bits=1).describe()
+    # qubit 0: RX, RY before CX(0 -> 1); qubit 1: nothing before the CX; qubit 2: H, X before the CZ;
+    # qubit 3: RZ before the CZ; the rest stay in the passes
+    assert d["prefix"] == [[0, 1], [], [2, 6], [7]]
+    in_passes = sorted(i for ps in d["passes"] for i in ps["gates"])
+    assert in_passes == [3, 4, 5, 8, 9]
+    off = q.Plan(gates, 4, k=3, contiguous_bits=1, product_prefix=False).describe()
+    assert off["prefix"] == [] and sorted(i for ps in off["passes"] for i in ps["gates"]) == list(range(10))
+    with pytest.raises(q.QsimError):
+        q.Plan(gates, 4, mode="per_gate", product_prefix=True)
