@@ -143,6 +143,9 @@ int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n
   qsim_plan_opts base;
   qsim_default_opts(&base);
   if (opts) base = *opts;
+  // time single-circuit plans with the register bits the queue kernels use (their own default differs)
+  if (base.bwd_reg_bits == 0) base.bwd_reg_bits = qsim::bwd_R_for(16, base.dtype);
+  if (base.fwd_reg_bits == 0) base.fwd_reg_bits = qsim::fwd_R_for(16, base.dtype);
   // one representative (the first circuit) per qubit count
   std::map<int, int> rep_of;
   for (int c = 0; c < n_circuits; c++)

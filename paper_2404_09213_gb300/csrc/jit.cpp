@@ -615,7 +615,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       int n_rz = 0;
       if (s.merge_diag)
         while (y < order.size() && is_diag(order[y])) n_rz += s.ops[order[y++]].rot;
-      if (n_rz >= 2) {
+      // the merged run costs a complex multiply per amplitude (two in the backward, where it also saves
+      // two FMAs of gradient and four of updates per RZ): worth it from 2 RZs backward, 4 forward
+      if (n_rz >= (bwd ? 2 : 4)) {
         emit_diag_run(std::vector<int>(order.begin() + x, order.begin() + y));
         x = y;
       } else {

@@ -277,7 +277,9 @@ cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
     else coef_gate_kernel<float><<<bg, tg, 0, st>>>(a);
     g_kernel_launches++;
   }
-  if (a.sigma) {   // the frame's signs must exist before the coefficients are packed
+  // the frame's signs must exist before the coefficients are packed; the walk also writes the final frame
+  // (the identity for a gate list without rotations, which has no sign array)
+  if (a.frame_x) {
     frame_walk_kernel<<<(unsigned)((a.B + 63) / 64), 64, 0, st>>>(a);
     g_kernel_launches++;
   }

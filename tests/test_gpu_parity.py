@@ -186,11 +186,11 @@ def test_product_prefix_equals_plain_plan_on_c3_ansatz(q):
 # runs of consecutive diagonal ops (RZ, CZ) are merged into one factor per amplitude, and their backward
 # gradients come from one pass (default with the Pauli frame): circuits dense in such runs, vs the oracle
 def _diagonal_heavy_circuit(rng, n, g, n_params=6, n_inputs=2):
+    """Runs of 2..8 diagonal ops (RZ on parameters and input columns, CZ), each followed by a few
+    non-diagonal gates (H, RX, RY, CNOT) so that the phases the runs put in reach <Z> (a circuit of H
+    layers and diagonal gates alone has <Z_i> = 0 and zero gradients for every angle)."""
     out = []
     while len(out) < g:
-        if rng.uniform() < 0.25:
-            out += random_circuit(rng, n, 2, n_params, n_inputs)
-            continue
         for _ in range(int(rng.integers(2, 9))):
             if n >= 2 and rng.uniform() < 0.3:
                 c, t = rng.choice(n, 2, replace=False)
@@ -198,7 +198,16 @@ def _diagonal_heavy_circuit(rng, n, g, n_params=6, n_inputs=2):
             else:
                 p = W.input_param(int(rng.integers(0, n_inputs))) if rng.uniform() < 0.3 else int(rng.integers(0, n_params))
                 out.append(W.gate(W.RZ, (int(rng.integers(0, n)),), param=p))
-    return out
+        for _ in range(int(rng.integers(1, 4))):
+            k = int(rng.choice([W.H, W.RX, W.RY, W.CNOT])) if n >= 2 else W.H
+            if k == W.CNOT:
+                c, t = rng.choice(n, 2, replace=False)
+                out.append(W.gate(k, (int(t),), (int(c),)))
+            elif k == W.H:
+                out.append(W.gate(k, (int(rng.integers(0, n)),)))
+            else:
+                out.append(W.gate(k, (int(rng.integers(0, n)),), param=int(rng.integers(0, n_params))))
+    return out + [W.gate(W.H, (qb,)) for qb in range(n)]
 
 
 @pytest.mark.parametrize("seed,n,dtype,k,c,ckpt", [(60, 5, "c64", 4, 1, 0), (61, 8, "c128", 6, 2, 1),
