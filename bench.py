@@ -62,8 +62,13 @@ def parse():
                          "two-qubit gate are merged into its prefix state and the first pass starts from the product)")
     ap.add_argument("--split-diagonal", action="store_true",
                     help="apply runs of diagonal ops one op at a time (default: one factor per amplitude per run)")
+    ap.add_argument("--max-regs", type=int, default=0,
+                    help="cap the pass kernels' registers per thread (0: the compiler's choice)")
     ap.add_argument("--bwd-reg-bits", type=int, default=0, help="amplitudes per thread in backward phases = 2^bits (0: default)")
     ap.add_argument("--fwd-reg-bits", type=int, default=0, help="amplitudes per thread in forward phases = 2^bits (0: default)")
+    ap.add_argument("--large-qubits", type=int, default=0,
+                    help="c4: circuits of at least this many qubits run as their own single-circuit plan "
+                         "(0: the library default, -1: every circuit in the persistent queue)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true", help="skip timing the per-gate path next to the fused one")
     ap.add_argument("--per-gate-steps", type=int, default=5)
@@ -386,13 +391,14 @@ def run_ours(args, world, rank, local):
                            checkpoint_passes=args.checkpoint_passes, pauli_frame=int((not args.no_pauli_frame)),
                            scalar_bwd=int(args.scalar_bwd), product_prefix=int(not args.no_product_prefix),
                            bwd_reg_bits=args.bwd_reg_bits, fwd_reg_bits=args.fwd_reg_bits,
-                           split_diagonal=int(args.split_diagonal))
+                           split_diagonal=int(args.split_diagonal), max_regs=args.max_regs)
         autotune = {"k_candidates": [10, 11, 12], "ms_per_fwd_bwd": ms, "chosen_k": k}
     ckpt = args.checkpoint_passes if args.mode == "fused" else 0
     plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits,
                   checkpoint_passes=ckpt, pauli_frame=(not args.no_pauli_frame) and args.mode == "fused",
                   scalar_bwd=args.scalar_bwd, product_prefix=args.mode == "fused" and not args.no_product_prefix,
-                  bwd_reg_bits=args.bwd_reg_bits, fwd_reg_bits=args.fwd_reg_bits, split_diagonal=args.split_diagonal)
+                  bwd_reg_bits=args.bwd_reg_bits, fwd_reg_bits=args.fwd_reg_bits, split_diagonal=args.split_diagonal,
+                  max_regs=args.max_regs)
     desc = plan.describe()
     p = torch.tensor(wl.params, dtype=torch.float32, device=dev)
     x = torch.tensor(wl.inputs, dtype=torch.float32, device=dev)
@@ -513,7 +519,7 @@ def run_ours(args, world, rank, local):
                     "product_prefix": bool(args.mode == "fused" and not args.no_product_prefix),
                     "merged_diagonal_runs": bool((not args.no_pauli_frame) and args.mode == "fused" and not args.split_diagonal),
                     "prefix_gates": sum(len(x) for x in desc.get("prefix", [])),
-                    "reg_bits": {"fwd": desc.get("R"), "bwd": desc.get("Rb")},
+                    "reg_bits": {"fwd": desc.get("R"), "bwd": desc.get("Rb")}, "max_regs": args.max_regs,
                     "workspace_bytes": plan.info()["workspace_bytes"], "contiguous_bits": desc["c"]},
            "roofline": roofline, "vs_per_gate": per_gate, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     return out, wl
@@ -535,7 +541,7 @@ def run_other(args, world, rank, local):
         B = 4
         circuits = [(w.gates, w.n) for w in wls]
         ks = q.multi_autotune(circuits, B, reps=2)   # per qubit count (untimed setup)
-        mp = q.MultiPlan(circuits, graph=True, ks=ks)
+        mp = q.MultiPlan(circuits, graph=True, ks=ks, large_qubits=args.large_qubits)
         p = torch.tensor(np.concatenate([w.params for w in wls]), dtype=torch.float32, device=dev)
         x = torch.tensor(np.concatenate([w.inputs.ravel() for w in wls]), dtype=torch.float32, device=dev)
         g = torch.tensor(np.concatenate([w.grad_out.ravel() for w in wls]), dtype=torch.float64, device=dev)
@@ -558,7 +564,7 @@ def run_other(args, world, rank, local):
             tot += amps * (8 + 16 * (P - 1))
             tot += amps * (8 if P == 1 else 24 + 16 + 32 * (P - 2))
         name = "C4: 256 circuits, 8..22 qubits (log-uniform), depth 4..16, HEA (RY,RZ + CZ ladder), batch 4, c64, fwd+bwd"
-        extra = {"circuits": len(wls), "batch_per_circuit": B, "graph": True,
+        extra = {"circuits": len(wls), "batch_per_circuit": B, "graph": True, "large_qubits": args.large_qubits,
                  "k_by_qubits": {str(w.n): kc for w, kc in sorted(zip(wls, ks), key=lambda t: t[0].n)}}
     elif args.workload == "c5":
         wl = W.config(5)

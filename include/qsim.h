@@ -117,6 +117,12 @@ typedef struct {
                                 and in the backward all of the run's RZ gradients come from one pass over the
                                 amplitudes (Im(conj(lambda) psi) is unchanged through diagonal ops up to a known
                                 real factor); 1: every op on its own. 0 or 1 */
+  int32_t large_circuit_qubits; /* multi-circuit plans: a circuit of at least this many qubits runs as its own
+                                single-circuit fused plan (Pauli frame, product prefix, merged diagonal runs) on its
+                                slices of the caller's buffers, right after the queue launch; the queue keeps the
+                                smaller circuits. 0 = default (20); < 0: every circuit in the queue. Single-circuit
+                                plans ignore it */
+  int32_t reserved;          /* must be 0 */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
 } qsim_plan_opts;
 

@@ -222,7 +222,7 @@ class MultiPlan:
     in circuit order; :meth:`offsets` gives the element offsets of every block for a batch size.
     """
 
-    def __init__(self, circuits, *, dtype="c64", k=0, graph=False, ks=None, weight_remap=False):
+    def __init__(self, circuits, *, dtype="c64", k=0, graph=False, ks=None, weight_remap=False, large_qubits=0):
         L = _lib.lib()
         self.circuits = [(list(g), int(n)) for g, n in circuits]
         self.dtype = dtype
@@ -238,6 +238,7 @@ class MultiPlan:
         opts.dtype = self._code
         opts.graph = 1 if graph else 0
         opts.weight_remap = 1 if weight_remap else 0
+        opts.large_circuit_qubits = int(large_qubits)   # 0: library default; < 0: every circuit in the queue
         h = ctypes.c_void_p()
         kv = None if ks is None else (ctypes.c_int32 * C)(*[int(x) for x in ks])
         _lib.check(L.qsim_multi_plan(lists, ng, nq, C, ctypes.byref(opts), kv, ctypes.byref(h)))

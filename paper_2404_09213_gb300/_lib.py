@@ -32,6 +32,7 @@ class QsimPlanOpts(ctypes.Structure):
                 ("graph", ctypes.c_int32), ("max_regs", ctypes.c_int32), ("rotate_low_bits", ctypes.c_int32),
                 ("pauli_frame", ctypes.c_int32), ("scalar_bwd", ctypes.c_int32),
                 ("product_prefix", ctypes.c_int32), ("split_diagonal", ctypes.c_int32),
+                ("large_circuit_qubits", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("mem_budget_bytes", ctypes.c_int64)]
 
 

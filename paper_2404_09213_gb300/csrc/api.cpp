@@ -289,7 +289,8 @@ struct qsim_plan_s {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       for (auto& pp : s.passes)
-        if ((int64_t)jit_smem_bytes(pp.dev, s.dtype, false) > optin || (int64_t)jit_smem_bytes(pp.devb, s.dtype, true) > optin)
+        if ((int64_t)jit_smem_bytes(pp.dev, s.dtype, false, 0, s.max_regs) > optin ||
+            (int64_t)jit_smem_bytes(pp.devb, s.dtype, true, 0, s.max_regs) > optin)
           return fail(QSIM_ERR_UNSUPPORTED, "tile does not fit in shared memory: lower k");
       std::string err;
       int rc = jit_build(s, jit, err);
@@ -477,11 +478,12 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
       (o.max_regs > 0 && o.max_regs < 32) || (o.rotate_low_bits != 0 && o.rotate_low_bits != 1) ||
       (o.pauli_frame != 0 && o.pauli_frame != 1) || (o.pauli_frame == 1 && o.mode != QSIM_FUSED) ||
       (o.scalar_bwd != 0 && o.scalar_bwd != 1) || (o.product_prefix != 0 && o.product_prefix != 1) ||
-      (o.product_prefix == 1 && o.mode != QSIM_FUSED) || (o.split_diagonal != 0 && o.split_diagonal != 1)) {
+      (o.product_prefix == 1 && o.mode != QSIM_FUSED) || (o.split_diagonal != 0 && o.split_diagonal != 1) ||
+      o.reserved != 0) {
     delete p;
     return fail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], sample_block >= 0, weight_remap 0..2, "
                               "max_regs 0 or >= 32, rotate_low_bits 0 or 1, pauli_frame 0 or 1 (fused mode), "
-                              "scalar_bwd 0 or 1, product_prefix 0 or 1 (fused mode), split_diagonal 0 or 1");
+                              "scalar_bwd 0 or 1, product_prefix 0 or 1 (fused mode), split_diagonal 0 or 1, reserved 0");
   }
   const int Rf = o.fwd_reg_bits > 0 ? o.fwd_reg_bits : fwd_R_for(16, o.dtype);
   // single-circuit complex64 backward kernels hold 2^5 amplitudes of psi and lambda per thread: fewer

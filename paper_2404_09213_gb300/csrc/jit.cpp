@@ -201,20 +201,26 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 // which they fit in 32 KiB per CTA; deep passes, or many small tile groups in one CTA of a
 // multi-circuit queue kernel, take GS up to a whole warp. cta: threads of the queue kernel's CTA
 // (0: one tile per CTA).
-static int grad_level(const DevPass& d, int dtype, int cta) {
+static int grad_level(const DevPass& d, int dtype, int cta, int max_regs = 0) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4;
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const int lt = d.k - d.R;                      // log2 threads per tile
   const size_t groups = cta > 0 ? std::max<size_t>(1, (size_t)cta >> lt) : 1;
-  const size_t budget = cta > 0 ? 16 * 1024 : 32 * 1024;   // queue kernels: keep CTAs small (see multi.cpp)
+  size_t budget = cta > 0 ? 16 * 1024 : 32 * 1024;   // queue kernels: keep CTAs small (see multi.cpp)
+  if (cta == 0 && max_regs > 0) {
+    // a register cap asks for as many CTAs per SM as the registers allow: keep the shared memory of
+    // one CTA (plus the 1 KiB the SM reserves per CTA) within 228 KiB divided by that count
+    const size_t ctas = std::max<size_t>(1, 65536 / (((size_t)1 << lt) * (size_t)max_regs));
+    const size_t per_cta = 228 * 1024 / ctas - 1024;
+    const size_t fixed = 2 * ((2 * sc) << d.k) + (d.k + 2) * 8 + (size_t)(d.n_ops + 1) * (sc + 1) + 32;
+    budget = std::min(budget, per_cta > fixed ? per_cta - fixed : 0);
+  }
   const int cap = std::min(lt, 5);
   for (int gs = 0; gs < cap; gs++)
     if (ng * ((size_t)1 << (lt - gs)) * sc * groups <= budget) return gs;
   return cap;
 }
 
-// prefix: this is the first pass of a product-prefix plan (its forward starts from the product state, its
-// backward writes the prefix partials)
 static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, int cta = 0, bool prefix = false) {
   const int K = d.k, R = d.R, N = 1 << R, NTHR = 1 << (K - R);
   const int P = d.n_phases;
@@ -222,7 +228,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   o << "  static constexpr int CTA = " << (cta > 0 ? cta : NTHR) << ";\n";
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
-  const int gs = bwd ? grad_level(d, s.dtype, cta) : 0;
+  const int gs = bwd ? grad_level(d, s.dtype, cta, s.max_regs) : 0;
   o << "  static constexpr int GS = " << gs << ";\n";
   for (int i = 0; i <= P; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
   auto dep_of = [&](const DevPhase& ph, int i) {
@@ -735,14 +741,14 @@ int bwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 3 : 4; retu
 int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
 
 // Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
-size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta) {
+size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta, int max_regs) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
   const size_t no = (size_t)d.n_ops + 1;   // op coefficients + the pass scale
   if (!bwd) return (tile + no * sc + no + 15) & ~(size_t)15;
   const size_t nthr = (size_t)1 << (d.k - d.R);
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const size_t red = 2 * tile;
-  const size_t parts = ng * (nthr >> grad_level(d, dtype, cta));
+  const size_t parts = ng * (nthr >> grad_level(d, dtype, cta, max_regs));
   const size_t gq = (red + parts * sc + 15) & ~(size_t)15;
   const size_t cf = gq + (d.k + 2) * 8;
   const size_t fm = cf + no * sc;
@@ -899,7 +905,7 @@ int jit_build(const Schedule& s, JitPlan& jp, std::string& err) {
       const DevPass& d = dir == 0 ? s.passes[p].dev : s.passes[p].devb;
       cudaKernel_t k = loaded[names[p]];
       ks[p].fn = reinterpret_cast<void*>(k);
-      ks[p].smem = jit_smem_bytes(d, s.dtype, dir == 1);
+      ks[p].smem = jit_smem_bytes(d, s.dtype, dir == 1, 0, s.max_regs);
       ks[p].nthr = 1 << (d.k - d.R);
       if (ks[p].smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
@@ -1001,6 +1007,7 @@ int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int c
   jm.smem_group[1].clear();
   size_t max_smem[2] = {0, 0};
   for (size_t c = 0; c < scheds.size(); c++) {
+    if (!scheds[c]) continue;   // a circuit the queue does not run
     const Schedule& s = *scheds[c];
     jm.kind[c].resize(2 * s.passes.size());
     for (size_t p = 0; p < s.passes.size(); p++) {

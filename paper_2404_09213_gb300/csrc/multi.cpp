@@ -77,6 +77,10 @@ int32_t op_gate(const DevOp& op, int64_t goff) { return op.gate < 0 ? -1 : (int3
 
 struct qsim_multi_s {
   std::vector<Schedule> sch;
+  // circuits run by their own single-circuit plan (at least large_circuit_qubits qubits): no queue
+  // items, no queue-kernel code, no queue gradient occurrences, no <Z> rows
+  std::vector<char> ext;
+  std::vector<qsim_plan_t> ext_plan;
   qsim_plan_opts opts{};
   int C = 0, el = 8, sc = 4, dtype = QSIM_C64;
   const void* params = nullptr;   // of the last forward (weight remapping needs them in the backward)
@@ -201,7 +205,7 @@ struct qsim_multi_s {
         for (int j = 0; j < pp.dev.n_nonlocal; j++) bits.push_back(pp.dev.QN[j]);
         bits.push_back(0);
       }
-      for (size_t j = 0; j < s.grad_gate.size(); j++) {
+      for (size_t j = 0; j < (ext[c] ? 0 : s.grad_gate.size()); j++) {
         const int g = s.grad_gate[j];
         const int occ = (int)occ_gate.size();
         occ_gate.push_back((int32_t)(goff[c] + g));
@@ -245,7 +249,7 @@ struct qsim_multi_s {
 #undef QSIM_UP
     if (e != cudaSuccess) return mcuda(e, "uploading the multi-circuit plan");
     std::vector<const Schedule*> ptrs;
-    for (auto& s : sch) ptrs.push_back(&s);
+    for (int c = 0; c < C; c++) ptrs.push_back(ext[c] ? nullptr : &sch[c]);
     std::string err;
     int rc = jit_build_multi(ptrs, kCtaF, kCtaB, jm, err);
     if (rc) return mfail(rc, err);
@@ -271,7 +275,7 @@ struct qsim_multi_s {
     std::vector<ZCirc> zc(C);
     for (int c = 0; c < C; c++) {
       const DevPass& last = sch[c].passes.back().dev;
-      zc[c] = {zp_off[c], tps(c), off_bits[poff[c] + P(c) - 1], last.k, sch[c].n, last.n_nonlocal, 0};
+      zc[c] = {zp_off[c], tps(c), off_bits[poff[c] + P(c) - 1], ext[c] ? -1 : last.k, sch[c].n, last.n_nonlocal, 0};
     }
     // work queues: rounds of passes, items of up to CTA / NTHR tiles
     std::vector<QItem> itf, itb;
@@ -283,7 +287,7 @@ struct qsim_multi_s {
       const int cta = dir == 0 ? kCtaF : kCtaB;
       for (int r = 0; r < maxP; r++) {
         for (int c = 0; c < C; c++) {
-          if (r >= P(c)) continue;
+          if (r >= P(c) || ext[c]) continue;
           const int p = dir == 0 ? r : P(c) - 1 - r;
           const DevPass& d = dir == 0 ? sch[c].passes[p].dev : sch[c].passes[p].devb;
           const int nthr = 1 << (d.k - d.R);
@@ -397,9 +401,9 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
   if (o.dtype != QSIM_C64 && o.dtype != QSIM_C128) return mfail(QSIM_ERR_ARG, "bad dtype");
   if (o.bwd_reg_bits < 0 || o.bwd_reg_bits > kMaxR || o.fwd_reg_bits < 0 || o.fwd_reg_bits > kMaxR ||
       (o.weight_remap != 0 && o.weight_remap != 1) || o.max_regs != 0 || o.pauli_frame != 0 || o.scalar_bwd != 0 ||
-      o.product_prefix != 0 || o.split_diagonal != 0)
+      o.product_prefix != 0 || o.split_diagonal != 0 || o.reserved != 0)
     return mfail(QSIM_ERR_ARG, "fwd_reg_bits/bwd_reg_bits must be in [0, 5], weight_remap 0 or 1, max_regs 0 "
-                               "(multi-circuit kernels size their own CTAs), pauli_frame 0, scalar_bwd 0, product_prefix 0, split_diagonal 0");
+                               "(multi-circuit kernels size their own CTAs), pauli_frame 0, scalar_bwd 0, product_prefix 0, split_diagonal 0, reserved 0");
   if (o.k == 0 || o.k > multi_max_k(o.dtype)) o.k = multi_max_k(o.dtype);
   auto* m = new qsim_multi_s();
   m->opts = o;
@@ -450,6 +454,27 @@ int qsim_multi_plan(const qsim_gate* const* lists, const int32_t* n_gates, const
     m->amp_off.push_back(m->amp_off.back() + ((int64_t)1 << n_qubits[c]));
     m->zq_off.push_back(m->zq_off.back() + n_qubits[c]);
     m->sch.push_back(std::move(s));
+  }
+  // circuits large enough to fill the GPU on their own run as single-circuit plans (the queue's kernels
+  // hold every pass structure at once and so run with smaller tiles and fewer registers than theirs)
+  const int large = o.large_circuit_qubits > 0 ? o.large_circuit_qubits : o.large_circuit_qubits == 0 ? 20 : 1 << 30;
+  m->ext.assign(n_circ, 0);
+  m->ext_plan.assign(n_circ, nullptr);
+  for (int c = 0; c < n_circ; c++) {
+    if (n_qubits[c] < large) continue;
+    qsim_plan_opts so;
+    qsim_default_opts(&so);
+    so.dtype = o.dtype;
+    so.weight_remap = o.weight_remap;
+    so.pauli_frame = 1;
+    so.product_prefix = 1;
+    const int rc = qsim_plan(lists[c], n_gates[c], n_qubits[c], &so, &m->ext_plan[c]);
+    if (rc) {
+      const std::string why = qsim_last_error();
+      qsim_multi_destroy(m);
+      return mfail(rc, "circuit " + std::to_string(c) + " (own plan): " + why);
+    }
+    m->ext[c] = 1;
   }
   m->G_tot = m->goff.back();
   m->P_tot = m->poff.back();
@@ -593,6 +618,15 @@ int qsim_multi_forward(qsim_multi_t m, const void* d_params, const void* d_input
     e = multi_enqueue_fwd(m, d_params, d_inputs, d_states, d_z, st);
   }
   if (e != cudaSuccess) return mcuda(e, "multi-circuit forward");
+  for (int c = 0; c < m->C; c++) {   // the large circuits, each on its slices of the buffers
+    if (!m->ext[c]) continue;
+    const Schedule& s = m->sch[c];
+    const void* pc = s.n_params ? static_cast<const char*>(d_params) + m->param_off[c] * m->sc : nullptr;
+    const void* ic = s.n_inputs ? static_cast<const char*>(d_inputs) + (int64_t)batch * m->col_off[c] * m->sc : nullptr;
+    void* stc = static_cast<char*>(d_states) + m->amp_off[c] * batch * m->el;
+    const int r2 = qsim_forward(m->ext_plan[c], pc, ic, batch, nullptr, stc, d_z + (int64_t)batch * m->zq_off[c], stream);
+    if (r2) return r2;
+  }
   m->states = d_states;
   m->params = d_params;
   m->has_fwd = true;
@@ -685,6 +719,15 @@ int qsim_multi_backward(qsim_multi_t m, const double* d_grad_out, double* d_dpar
     e = multi_enqueue_bwd(m, d_dparams, d_dinputs, st);
   }
   if (e != cudaSuccess) return mcuda(e, "multi-circuit backward");
+  // the queue's gradient scatter wrote zeros for the large circuits' entries: their plans come after
+  for (int c = 0; c < m->C; c++) {
+    if (!m->ext[c]) continue;
+    const Schedule& s = m->sch[c];
+    double* dp = (d_dparams && s.n_params) ? d_dparams + m->param_off[c] : nullptr;
+    double* di = (d_dinputs && s.n_inputs) ? d_dinputs + (int64_t)m->B * m->col_off[c] : nullptr;
+    const int r2 = qsim_backward(m->ext_plan[c], d_grad_out + (int64_t)m->B * m->zq_off[c], dp, di, stream);
+    if (r2) return r2;
+  }
   return QSIM_OK;
 }
 
@@ -728,6 +771,8 @@ int qsim_multi_kernel_info(qsim_multi_t m, int32_t* ctas_per_sm, int32_t* regs, 
 
 void qsim_multi_destroy(qsim_multi_t m) {
   if (!m) return;
+  for (qsim_plan_t p : m->ext_plan) qsim_plan_destroy(p);
+  m->ext_plan.clear();
   if (m->uploaded || m->B >= 0) {
     cudaStreamSynchronize(m->last);
     m->free_all();

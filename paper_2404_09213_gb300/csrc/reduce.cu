@@ -230,34 +230,48 @@ __host__ __device__ inline int frame_step(Frame& f, int ty, int q, int c, int co
   return sigma;
 }
 
-// One thread per sample over every op of every pass in execution order. The ops' gate, kind and qubits
-// are the same for every sample: each block stages them in shared memory a chunk at a time, so a step of
-// the walk reads shared memory plus one byte of the sample's form (coalesced across the warp).
+// One thread per sample over every op of every pass in execution order, one warp per block. The ops'
+// gate, kind and qubits are the same for every sample, and each sample's form bytes of a chunk of ops
+// are independent of the walk: both are staged in shared memory first (the form loads pipeline, 32
+// consecutive samples per op), so the serial walk itself reads shared memory only.
 __global__ void frame_walk_kernel(CoefArgs a) {
-  constexpr int CH = 512;
+  constexpr int CH = 256;
   __shared__ int s_g[CH];
   __shared__ int s_meta[CH];   // kind | q0 << 8 | (q1 + 1) << 16
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ uint8_t s_form[CH][32];
+  const int lane = (int)threadIdx.x;
+  const int b = blockIdx.x * 32 + lane;
   Frame f;
   const int e0 = a.exec_begin[0], e1 = a.exec_begin[a.P];
   for (int base = e0; base < e1; base += CH) {
     const int m = min(CH, e1 - base);
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    __syncwarp();
+    for (int i = lane; i < m; i += 32) {
       const int g = a.exec_gates[base + i];
       s_g[i] = g;
       s_meta[i] = g < 0 ? 0 : (a.gate_type[g] | (a.gate_q0[g] << 8) | ((a.gate_q1[g] + 1) << 16));
     }
-    __syncthreads();
+    __syncwarp();
+    for (int i0 = 0; i0 < m; i0 += 16) {   // 16 independent loads in flight, then their stores
+      uint8_t v[16];
+#pragma unroll
+      for (int u = 0; u < 16; u++) {
+        const int i = i0 + u;
+        const int g = i < m ? s_g[i] : -1;
+        v[u] = (g >= 0 && (s_meta[i] & 255) <= QSIM_RZ && b < a.B) ? a.form[(int64_t)g * a.B + b] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; u++)
+        if (i0 + u < m) s_form[i0 + u][lane] = v[u];
+    }
+    __syncwarp();
     if (b < a.B)
       for (int i = 0; i < m; i++) {
         const int g = s_g[i];
         if (g < 0) continue;   // rescale op
         const int meta = s_meta[i], ty = meta & 255;
-        const int64_t gi = (int64_t)g * a.B + b;
-        const int cot = ty <= QSIM_RZ ? a.form[gi] : 0;
-        const int sg = frame_step(f, ty, (meta >> 8) & 255, ((meta >> 16) & 255) - 1, cot);
-        if (ty <= QSIM_RZ) a.sigma[gi] = (int8_t)sg;
+        const int sg = frame_step(f, ty, (meta >> 8) & 255, ((meta >> 16) & 255) - 1, s_form[i][lane]);
+        if (ty <= QSIM_RZ) a.sigma[(int64_t)g * a.B + b] = (int8_t)sg;
       }
   }
   if (b < a.B) {
@@ -280,7 +294,7 @@ cudaError_t launch_coef(const CoefArgs& a, int dtype, cudaStream_t st) {
   // the frame's signs must exist before the coefficients are packed; the walk also writes the final frame
   // (the identity for a gate list without rotations, which has no sign array)
   if (a.frame_x) {
-    frame_walk_kernel<<<(unsigned)((a.B + 63) / 64), 64, 0, st>>>(a);
+    frame_walk_kernel<<<(unsigned)((a.B + 31) / 32), 32, 0, st>>>(a);
     g_kernel_launches++;
   }
   if (dtype == QSIM_C128) coef_pass_kernel<double><<<bp, tp, 0, st>>>(a);
@@ -622,6 +636,7 @@ __global__ void z_final_multi_kernel(ZMultiArgs a) {
   }
   const int c = lo;
   const ZCirc d = a.circ[c];
+  if (d.k < 0) return;   // a circuit run by its own single-circuit plan writes its <Z> itself
   const int64_t r = gz - (int64_t)a.B * a.zq_off[c];
   const int b = (int)(r / d.n), q = (int)(r - (int64_t)b * d.n);
   const uint8_t* Qnl = a.bits + d.bits_off;   // logical qubits of the last pass's tile and tile-index bits
@@ -778,7 +793,7 @@ struct NoAllocSlot {
 };
 NoAllocSlot g_noalloc[256];   // per device
 
-// The driver's cuCtxGetCurrent, reached through the runtime (no link against the driver library):
+// The CUDA driver API's cuCtxGetCurrent, reached through the runtime (no link against libcuda):
 // the current context identifies the module instance that holds the array.
 typedef int (*CtxGetCurrentFn)(void**);
 CtxGetCurrentFn ctx_get_current() {

@@ -8,7 +8,7 @@
 #include "qsim.h"
 
 _Static_assert(sizeof(qsim_gate) == 24, "qsim_gate layout");
-_Static_assert(sizeof(qsim_plan_opts) == 72, "qsim_plan_opts layout");
+_Static_assert(sizeof(qsim_plan_opts) == 80, "qsim_plan_opts layout");
 _Static_assert(sizeof(qsim_plan_info) == 48, "qsim_plan_info layout");
 
 int main(void) {

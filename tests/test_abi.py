@@ -45,7 +45,7 @@ def test_library_exports_every_declared_symbol(q):
 def test_struct_sizes_match_header(q):
     from paper_2404_09213_gb300 import _lib
     assert ctypes.sizeof(_lib.QsimGate) == 24
-    assert ctypes.sizeof(_lib.QsimPlanOpts) == 72
+    assert ctypes.sizeof(_lib.QsimPlanOpts) == 80
     assert ctypes.sizeof(_lib.QsimPlanInfo) == 48
 
 

@@ -35,8 +35,8 @@ def split(t, off, c):
     return t[int(off[c]):int(off[c + 1])]
 
 
-def run_multi(q, wls, B, dtype="c64", graph=False, reps=1):
-    mp = q.MultiPlan([(w.gates, w.n) for w in wls], dtype=dtype, graph=graph)
+def run_multi(q, wls, B, dtype="c64", graph=False, reps=1, **kw):
+    mp = q.MultiPlan([(w.gates, w.n) for w in wls], dtype=dtype, graph=graph, **kw)
     p, x, g = concat(wls, B, dtype)
     outs = []
     for _ in range(reps):
@@ -52,11 +52,13 @@ def small_set(n_circ=10, seed=11):
     return W.multi_circuit_config(n_circuits=n_circ, n_min=3, n_max=14, d_min=1, d_max=3, seed=seed)
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
-def test_multi_against_oracle(q, dtype):
+# large: circuits of at least this many qubits run as their own single-circuit plans (-1: none), so
+# the same launch mixes queue circuits and own-plan circuits on one set of buffers
+@pytest.mark.parametrize("dtype,large", [("c64", -1), ("c128", -1), ("c64", 9), ("c128", 12)])
+def test_multi_against_oracle(q, dtype, large):
     wls = small_set()
     B = 4
-    mp, [(states, z, dp, di)] = run_multi(q, wls, B, dtype)
+    mp, [(states, z, dp, di)] = run_multi(q, wls, B, dtype, large_qubits=large)
     off = mp.offsets(B)
     tol = 1e-5 if dtype == "c64" else 1e-12
     for c, w in enumerate(wls):
@@ -140,9 +142,10 @@ def test_c4_full_against_oracle_above_12_qubits(q):
             assert abs(got - ref) <= 1e-4 * np.abs(adp).max() + 1e-7, (c, i, got, ref)
 
 
-def test_multi_graph_replay_is_identical(q):
+@pytest.mark.parametrize("large", [-1, 8])
+def test_multi_graph_replay_is_identical(q, large):
     wls = small_set(6, seed=3)
-    mp, outs = run_multi(q, wls, 4, graph=True, reps=3)
+    mp, outs = run_multi(q, wls, 4, graph=True, reps=3, large_qubits=large)
     for o in outs[1:]:
         for a, b in zip(outs[0], o):
             assert torch.equal(a, b)
