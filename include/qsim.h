@@ -67,7 +67,9 @@ enum { QSIM_C64 = 0, QSIM_C128 = 1 };
 enum { QSIM_FUSED = 0, QSIM_PER_GATE = 1 };
 
 typedef struct {
-  int32_t k;                 /* max qubits local to one fused pass (tile = 2^k amplitudes); 0 = default (12) */
+  int32_t k;                 /* max qubits local to one fused pass (tile = 2^k amplitudes); 0 = default (12);
+                                at most 13 for complex64, 11 for complex128, and at most 8 more than the
+                                register bits of either direction (256 threads per tile) */
   int32_t dtype;             /* QSIM_C64 or QSIM_C128 */
   int32_t mode;              /* QSIM_FUSED (default) or QSIM_PER_GATE (one kernel per gate: the plain baseline) */
   int32_t contiguous_bits;   /* low index bits local in every pass (runs of 2^c amplitudes); 0 = default (4) */
@@ -120,7 +122,7 @@ typedef struct {
   int32_t large_circuit_qubits; /* multi-circuit plans: a circuit of at least this many qubits runs as its own
                                 single-circuit fused plan (Pauli frame, product prefix, merged diagonal runs) on its
                                 slices of the caller's buffers, right after the queue launch; the queue keeps the
-                                smaller circuits. 0 = default (20); < 0: every circuit in the queue. Single-circuit
+                                smaller circuits. 0 = default (18); < 0: every circuit in the queue. Single-circuit
                                 plans ignore it */
   int32_t reserved;          /* must be 0 */
   int64_t mem_budget_bytes;  /* workspace limit used when checkpoint_passes == -1 (0 = unlimited) */
@@ -340,13 +342,17 @@ int qsim_landscape(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, 
 void qsim_landscape_clear_cache(void);
 
 /* Tile-size autotuner (the fused pass's k). Plans the circuit with *opts for each candidate k in
- * {max_k - 2, max_k - 1, max_k} (max_k = 12 complex64, 11 complex128), runs one untimed forward
+ * {max_k - 2, max_k - 1, max_k} (max_k = 13 complex64, 11 complex128), runs one untimed forward
  * (+ backward when with_backward != 0; this also compiles the kernels) and then `reps` timed calls
  * on zero-filled scratch buffers of `batch` samples that it allocates and frees itself (run time
  * does not depend on the values), and writes to opts->k the largest candidate whose time is within
- * 2 % of the fastest. n_qubits <= max_k: opts->k =
- * n_qubits (one pass), nothing is run. h_ms: NULL or 3 floats, mean ms per call of each candidate
- * (-1 when not run). Synchronises `stream`. Errors: those of qsim_plan / qsim_forward /
+ * 2 % of the fastest. n_qubits <= max_k: opts->k = n_qubits (one pass), and when opts leaves
+ * fwd_reg_bits and bwd_reg_bits at 0 the candidates are the amplitudes per thread in the register phases
+ * and the Pauli frame: 2^5 and 2^4 (2^4 and 2^3 for complex128) with opts->pauli_frame as given, and the
+ * larger with the frame off when it was on (the smaller minus one when it was off); the backward's
+ * phases follow the forward's when with_backward != 0. The fastest is written to opts->fwd_reg_bits
+ * (/ bwd_reg_bits; left at 0 when the largest count wins) and opts->pauli_frame. h_ms: NULL or 3 floats,
+ * mean ms per call of each candidate (-1 when not run). Synchronises `stream`. Errors: those of qsim_plan / qsim_forward /
  * qsim_backward, QSIM_ERR_OOM for scratch. In the paper the maximum group width is a fixed
  * argument of the greedy splitter (Sec. "Circuit Splitting", typically 3 to 6 qubits); here the
  * width is measured per circuit and batch. */

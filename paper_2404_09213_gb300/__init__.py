@@ -314,7 +314,8 @@ def _opts(dtype, **kw):
     return opts
 
 
-def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64", stream=None, **opts):
+def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64", stream=None, return_opts=False,
+             **opts):
     """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate]).
     Plans are timed with the Pauli frame on unless ``pauli_frame=0`` is passed (as :class:`Plan`)."""
     opts.setdefault("pauli_frame", 1)
@@ -325,6 +326,10 @@ def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64",
     arr = gate_structs(gates)
     _lib.check(_lib.lib().qsim_autotune(arr, len(gates), int(n_qubits), int(batch), int(bool(with_backward)),
                                         int(reps), ctypes.byref(o), ms, _stream(stream)))
+    if return_opts:   # everything the autotuner chose, as Plan keyword arguments
+        return int(o.k), [float(x) for x in ms], {"k": int(o.k), "fwd_reg_bits": int(o.fwd_reg_bits),
+                                                  "bwd_reg_bits": int(o.bwd_reg_bits),
+                                                  "pauli_frame": bool(o.pauli_frame)}
     return int(o.k), [float(x) for x in ms]
 
 

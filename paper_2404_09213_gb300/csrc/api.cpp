@@ -469,7 +469,7 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   p->el = o.dtype == QSIM_C128 ? 16 : 8;
   p->sc = o.dtype == QSIM_C128 ? 8 : 4;
   if (o.mode == QSIM_FUSED) {
-    if (o.k == 0) o.k = max_k_for(o.dtype);
+    if (o.k == 0) o.k = default_k_for(o.dtype);
     if (o.k > max_k_for(o.dtype)) o.k = max_k_for(o.dtype);
   }
   p->opts = o;
@@ -491,6 +491,10 @@ int qsim_plan(const qsim_gate* gates, int32_t n_gates, int32_t n_qubits, const q
   // (measured faster on the 20-qubit workload); the multi-circuit queue kernels, capped at 128
   // registers, keep 2^4
   const int Rb = o.bwd_reg_bits > 0 ? o.bwd_reg_bits : (o.dtype == QSIM_C64 ? 5 : bwd_R_for(16, o.dtype));
+  // at most 256 threads per tile in either direction: a larger k with fewer amplitudes per thread is cut
+  if (o.mode == QSIM_FUSED)
+    while (o.k > 1 && (o.k - std::min(Rf, o.k) > 8 || o.k - std::min(Rb, o.k) > 8)) o.k--;
+  p->opts = o;
   rc = build_schedule(gv, n_qubits, o, Rf, Rb, p->s, err, o.rotate_low_bits == 1);
   if (rc) {
     delete p;

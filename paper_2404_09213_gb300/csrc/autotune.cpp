@@ -4,7 +4,8 @@
 // Candidates are the largest tiles that still fit the register/shared-memory budget of one CTA
 // (max_k - 2 .. max_k). A larger k means fewer passes (fewer HBM round trips); a smaller one means
 // smaller CTAs with cheaper barriers and more of them resident per SM. Which wins depends on the
-// circuit and the batch, so it is measured. Circuits with n <= max_k run in one pass at k = n.
+// circuit and the batch, so it is measured. Circuits with n <= max_k run in one pass at k = n; for
+// them the candidates are the amplitudes per thread of the register phases instead.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -101,11 +102,38 @@ int autotune_upto(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, i
   if (opts->dtype != QSIM_C64 && opts->dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "autotune: bad dtype");
   if (h_ms)
     for (int i = 0; i < 3; i++) h_ms[i] = -1.f;
-  if (n_qubits <= kmax) {   // one pass holds the whole state
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (n_qubits <= kmax) {
+    // One pass holds the whole state, so k is n; what remains to choose is the amplitudes per thread of
+    // the register phases and the Pauli frame. Candidates: 2^5 and 2^4 (the frame as requested), and 2^5
+    // with the frame off when it was on (2^3 otherwise). Fewer amplitudes mean shorter unrolled code and
+    // more resident warps, more mean fewer shared-memory exchanges; the frame halves the code but adds
+    // a walk per sample and a fix-up of the returned states, which a single short pass may not repay.
+    // Single-circuit plans only.
     opts->k = n_qubits;
+    if (kmax != qsim::max_k_for(opts->dtype) || opts->fwd_reg_bits != 0 || opts->bwd_reg_bits != 0) return QSIM_OK;
+    const int top = qsim::fwd_R_for(16, opts->dtype);
+    const bool frame = opts->pauli_frame == 1;
+    const int rb[3] = {top, top - 1, frame ? top : top - 2};
+    float ms[3];
+    int best = 0;
+    for (int i = 0; i < 3; i++) {
+      qsim_plan_opts o = *opts;
+      o.fwd_reg_bits = std::min(rb[i], n_qubits);
+      if (with_backward) o.bwd_reg_bits = std::min(rb[i], n_qubits);
+      if (i == 2 && frame) o.pauli_frame = 0;
+      const int rc = time_candidate(h_gates, n_gates, n_qubits, batch, with_backward, reps, o, st, ms[i]);
+      if (rc) return rc;
+      if (h_ms) h_ms[i] = ms[i];
+      if (ms[i] < ms[best]) best = i;
+    }
+    if (best == 2 && frame) opts->pauli_frame = 0;
+    if (rb[best] != top) {   // keep the library defaults (0) when the largest register count wins
+      opts->fwd_reg_bits = std::min(rb[best], n_qubits);
+      if (with_backward) opts->bwd_reg_bits = std::min(rb[best], n_qubits);
+    }
     return QSIM_OK;
   }
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   float ms[3];
   for (int i = 0; i < 3; i++) {
     qsim_plan_opts o = *opts;
@@ -156,7 +184,7 @@ int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n
     const int c = kv.second;
     // multi-circuit plans take tiles of at most max_k - 1 qubits (see multi.cpp)
     const int rc = autotune_upto(h_gate_lists[c], h_n_gates[c], h_n_qubits[c], batch, with_backward, reps, &o,
-                                 nullptr, stream, qsim::max_k_for(o.dtype) - 1);
+                                 nullptr, stream, qsim::multi_max_k_for(o.dtype));
     if (rc) return rc;
     k_of[kv.first] = o.k;
   }

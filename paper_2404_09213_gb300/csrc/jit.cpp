@@ -734,11 +734,17 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   return o.str();
 }
 
-// Register bits per phase: complex64 forward 5 (32 amplitudes per thread), backward 4 (psi and
-// lambda); complex128 one less each. Threads per CTA = 2^(k - R) <= 256, so k <= 12 (11 for c128).
+// Default register bits per phase when a caller gives none: complex64 forward 5 (32 amplitudes per
+// thread), backward 4 (psi and lambda); complex128 one less each. Threads per CTA = 2^(k - R) <= 256.
 int fwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 4 : 5; return k < r ? k : r; }
 int bwd_R_for(int k, int dtype) { const int r = dtype == QSIM_C128 ? 3 : 4; return k < r ? k : r; }
-int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
+// Largest tile of a single-circuit plan: 2^13 complex64 amplitudes (256 threads of 2^5 each; the
+// backward's psi and lambda tiles take 128 KiB of shared memory, one CTA per SM), 2^11 complex128.
+// The default is one less for complex64 (the autotuner measures 11, 12 and 13); multi-circuit queue
+// kernels take at most 2^11 / 2^10 (every pass structure of a direction shares their CTA size).
+int max_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 13; }
+int default_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
+int multi_max_k_for(int dtype) { return dtype == QSIM_C128 ? 10 : 11; }
 
 // Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
 size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta, int max_regs) {

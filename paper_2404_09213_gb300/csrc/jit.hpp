@@ -68,6 +68,8 @@ struct JitPlan {
 int fwd_R_for(int k, int dtype);
 int bwd_R_for(int k, int dtype);
 int max_k_for(int dtype);
+int default_k_for(int dtype);
+int multi_max_k_for(int dtype);
 
 // Persistent multi-circuit queue kernels (one per direction) linked from relocatable pass functions.
 struct JitMulti {

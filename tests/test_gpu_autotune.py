@@ -23,17 +23,37 @@ def q():
 def test_autotune_times_three_candidates(q):
     wl = W.config(3, n=15, batch=4, layers=3)
     k, ms = q.autotune(wl.gates, wl.n, 4, reps=1)
-    assert k in (10, 11, 12)
+    assert k in (11, 12, 13)
     assert all(m > 0 for m in ms)
     # the largest k within 2 % of the fastest candidate
-    assert ms[k - 10] <= 1.02 * min(ms)
-    assert all(m > 1.02 * min(ms) for m in ms[k - 10 + 1:])
+    assert ms[k - 11] <= 1.02 * min(ms)
+    assert all(m > 1.02 * min(ms) for m in ms[k - 11 + 1:])
 
 
 def test_autotune_single_pass_when_the_state_fits(q):
+    # one pass holds the whole state: k = n, and the three candidates are the register bits per thread;
+    # the tuned plan gives the default plan's results
     wl = W.config(2, batch=8)
-    k, ms = q.autotune(wl.gates, wl.n, 8)
-    assert k == wl.n and ms == [-1.0, -1.0, -1.0]
+    k, ms, tuned = q.autotune(wl.gates, wl.n, 8, reps=1, return_opts=True)
+    assert k == wl.n and all(m > 0 for m in ms)
+    assert tuned["fwd_reg_bits"] in (0, 4) and tuned["bwd_reg_bits"] == tuned["fwd_reg_bits"]
+    assert tuned["pauli_frame"] or tuned["fwd_reg_bits"] == 0   # the frame-off candidate is 2^5
+    p, x, g = tensors(wl)
+    a = q.Plan(wl.gates, wl.n)
+    b = q.Plan(wl.gates, wl.n, **tuned)
+    for fr, frame in ((4, True), (5, False)):   # every candidate, not only the one that won
+        c = q.Plan(wl.gates, wl.n, fwd_reg_bits=fr, bwd_reg_bits=fr, pauli_frame=frame)
+        _, zc = c.forward(p, x)
+        _, za = a.forward(p, x)
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(zc.cpu().numpy(), za.cpu().numpy(), atol=1e-5)
+        np.testing.assert_allclose(c.backward(g)[0].cpu().numpy(), a.backward(g)[0].cpu().numpy(), atol=1e-4)
+    _, zb = b.forward(p, x)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(zb.cpu().numpy(), a.forward(p, x)[1].cpu().numpy(), atol=1e-5)
+    # an explicit register choice is kept: nothing is timed
+    k2, ms2 = q.autotune(wl.gates, wl.n, 8, fwd_reg_bits=4)
+    assert k2 == wl.n and ms2 == [-1.0, -1.0, -1.0]
 
 
 def test_autotuned_plan_matches_default_plan(q):
