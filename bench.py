@@ -312,6 +312,7 @@ def pass_roofline(desc, B, wl, ckpt, mode, fwd_ms, bwd_ms, nf, nb, kernel_source
     achieved = (tot_b / n_l) / ((tot_ms / n_l) / 1e3) / 1e9 if tot_ms > 0 else None
     return {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if achieved else None, "traffic": traffic_record(kern, kernel_source),
+            "kernel_source_sha256": hashlib.sha256(kernel_source.encode()).hexdigest(),
             "algorithmic_bytes_per_launch": tot_b / n_l if n_l else None,
             "avg_launch_ms": tot_ms / n_l if n_l else None, "launches_timed": n_l,
             "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})",

@@ -289,8 +289,7 @@ struct qsim_plan_s {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       for (auto& pp : s.passes)
-        if ((int64_t)jit_smem_bytes(pp.dev, s.dtype, false, 0, s.max_regs) > optin ||
-            (int64_t)jit_smem_bytes(pp.devb, s.dtype, true, 0, s.max_regs) > optin)
+        if ((int64_t)jit_smem_bytes(s, pp.dev, false, 0) > optin || (int64_t)jit_smem_bytes(s, pp.devb, true, 0) > optin)
           return fail(QSIM_ERR_UNSUPPORTED, "tile does not fit in shared memory: lower k");
       std::string err;
       int rc = jit_build(s, jit, err);

@@ -196,12 +196,105 @@ uint32_t lay_eval(const DevLayout& L, int k, uint32_t e) {
 }  // namespace
 
 // ------------------------------------------------------------------ generation
+// Ops of a phase in the order a pass runs them (backward: reversed), without the CNOTs that open the
+// phase (forward order) with the control on a thread bit and the target on a register bit >= 1: those
+// fold into the thread's addresses instead.
+static std::vector<int> phase_order(const Schedule& s, const DevPhase& Ph, bool bwd, size_t* n_fold = nullptr) {
+  size_t nf = 0;
+  for (int oi = Ph.op_begin; oi < Ph.op_end; oi++) {
+    const DevOp& op = s.ops[oi];
+    if (op.kind != K_CNOT_RT || op.a < 1) break;
+    nf++;
+  }
+  std::vector<int> order;
+  for (int oi = Ph.op_begin + (int)nf; oi < Ph.op_end; oi++) order.push_back(oi);
+  if (bwd) std::reverse(order.begin(), order.end());
+  if (n_fold) *n_fold = nf;
+  return order;
+}
+
+static bool is_diag_op(const DevOp& op) {
+  return op.kind == K_RZ_R || op.kind == K_RZ_T || op.kind == K_CZ_RR || op.kind == K_CZ_RT || op.kind == K_CZ_TT;
+}
+
+// [x, y) ranges of a phase's op order that run as one merged diagonal factor per amplitude. The merged
+// run costs a complex multiply per amplitude (two in the backward, where it also saves two FMAs of
+// gradient and four of updates per RZ): worth it from 2 RZs backward, 4 forward.
+static std::vector<std::pair<size_t, size_t>> diag_ranges(const Schedule& s, const std::vector<int>& order, bool bwd) {
+  std::vector<std::pair<size_t, size_t>> r;
+  if (!s.merge_diag) return r;
+  for (size_t x = 0; x < order.size();) {
+    size_t y = x;
+    int n_rz = 0;
+    while (y < order.size() && is_diag_op(s.ops[order[y]])) n_rz += s.ops[order[y++]].rot;
+    if (n_rz >= (bwd ? 2 : 4)) {
+      r.push_back({x, y});
+      x = y;
+    } else {
+      x++;
+    }
+  }
+  return r;
+}
+
+// Register bits of a merged run with a per-bit factor (an RZ or a register-thread CZ on them), sorted.
+static std::vector<int> diag_used_bits(const Schedule& s, const std::vector<int>& run) {
+  std::vector<int> used;
+  for (int oi : run) {
+    const DevOp& op = s.ops[oi];
+    const int rb = op.kind == K_RZ_R ? op.a : op.kind == K_CZ_RT ? op.a : -1;
+    if (rb >= 0 && std::find(used.begin(), used.end(), rb) == used.end()) used.push_back(rb);
+  }
+  std::sort(used.begin(), used.end());
+  return used;
+}
+
+// One merged diagonal run of a pass with its factor table: for every value of the used register bits
+// the product of the run's register-bit RZ factors, per sample, built in shared memory while a tile's
+// loads are in flight. off: first element (in units of T); es: T values per entry (2: (re, im); 4:
+// (re, re, im, im), the packed backward's FP32x2 operands).
+struct DiagRun {
+  std::vector<int> ops;
+  std::vector<int> used;
+  int off = 0, es = 2;
+};
+
+// The merged runs of a pass in the order the generated code meets them (phase steps, then op order).
+static std::vector<DiagRun> pass_diag_runs(const Schedule& s, const DevPass& d, bool bwd, int* units = nullptr) {
+  std::vector<DiagRun> runs;
+  const int P = d.n_phases;
+  const int es = bwd && s.packed_bwd ? 4 : 2;
+  int off = 0;
+  for (int step = 0; step < P; step++) {
+    const int ph = bwd ? P - 1 - step : step;
+    const DevPhase& Ph = s.phases[d.phase0 + ph];
+    const std::vector<int> order = phase_order(s, Ph, bwd);
+    for (auto& xy : diag_ranges(s, order, bwd)) {
+      DiagRun r;
+      r.ops.assign(order.begin() + xy.first, order.begin() + xy.second);
+      r.used = diag_used_bits(s, r.ops);
+      r.es = es;
+      r.off = off;
+      off += es << r.used.size();
+      runs.push_back(r);
+    }
+  }
+  if (units) *units = off;
+  return runs;
+}
+
+static int diag_table_units(const Schedule& s, const DevPass& d, bool bwd) {
+  int u = 0;
+  pass_diag_runs(s, d, bwd, &u);
+  return u;
+}
+
 // Backward gradient partials live in shared memory until the end of the tile: one per gradient slot
 // and group of 2^GS neighbouring threads, GS the smallest level (no shuffles at all for GS = 0) for
 // which they fit in 32 KiB per CTA; deep passes, or many small tile groups in one CTA of a
 // multi-circuit queue kernel, take GS up to a whole warp. cta: threads of the queue kernel's CTA
 // (0: one tile per CTA).
-static int grad_level(const DevPass& d, int dtype, int cta, int max_regs = 0) {
+static int grad_level(const DevPass& d, int dtype, int cta, int max_regs = 0, size_t tab_bytes = 0) {
   const size_t sc = dtype == QSIM_C128 ? 8 : 4;
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const int lt = d.k - d.R;                      // log2 threads per tile
@@ -212,7 +305,7 @@ static int grad_level(const DevPass& d, int dtype, int cta, int max_regs = 0) {
     // one CTA (plus the 1 KiB the SM reserves per CTA) within 228 KiB divided by that count
     const size_t ctas = std::max<size_t>(1, 65536 / (((size_t)1 << lt) * (size_t)max_regs));
     const size_t per_cta = 228 * 1024 / ctas - 1024;
-    const size_t fixed = 2 * ((2 * sc) << d.k) + (d.k + 2) * 8 + (size_t)(d.n_ops + 1) * (sc + 1) + 32;
+    const size_t fixed = 2 * ((2 * sc) << d.k) + (d.k + 2) * 8 + tab_bytes + (size_t)(d.n_ops + 1) * (sc + 1) + 48;
     budget = std::min(budget, per_cta > fixed ? per_cta - fixed : 0);
   }
   const int cap = std::min(lt, 5);
@@ -228,8 +321,36 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   o << "  static constexpr int CTA = " << (cta > 0 ? cta : NTHR) << ";\n";
   o << "  static constexpr int NOPS = " << d.n_ops << ";\n";
   o << "  static constexpr int NGS = " << (bwd ? d.n_gslots : 0) << ";\n";
-  const int gs = bwd ? grad_level(d, s.dtype, cta, s.max_regs) : 0;
+  int ntab = 0;
+  const std::vector<DiagRun> druns = pass_diag_runs(s, d, bwd, &ntab);
+  const size_t sc_bytes = s.dtype == QSIM_C128 ? 8 : 4;
+  const int gs = bwd ? grad_level(d, s.dtype, cta, s.max_regs, (size_t)ntab * sc_bytes) : 0;
   o << "  static constexpr int GS = " << gs << ";\n";
+  o << "  static constexpr int NTAB = " << ntab << ";\n";
+  // factor tables of the merged diagonal runs (see DiagRun), from the sample's coefficients in global
+  // memory; the barrier after the staging publishes them
+  o << "  template <typename T> static __device__ __forceinline__ void build_tables(qj::Ctx<T>& c, const T* src) {\n"
+    << "    (void)c; (void)src;\n";
+  for (const DiagRun& r : druns) {
+    const int nu = (int)r.used.size();
+    o << "    for (qj::u32 e = c.tid; e < " << (1u << nu) << "u; e += " << NTHR << "u) {\n"
+      << "      T dr = T(1), di = T(0);\n";
+    for (int k2 = 0; k2 < nu; k2++) {
+      std::vector<int> lis;
+      for (int oi : r.ops)
+        if (s.ops[oi].kind == K_RZ_R && s.ops[oi].a == r.used[k2]) lis.push_back(oi - d.op0);
+      if (lis.empty()) continue;
+      o << "      { T ur = T(1), ui = T(0); const T sg = ((e >> " << k2 << ") & 1u) ? T(1) : T(-1);";
+      for (int li : lis) o << " qj::cmul(ur, ui, T(1), sg * src[" << li << "]);";
+      o << " qj::cmul(dr, di, ur, ui); }\n";
+    }
+    if (r.es == 4)
+      o << "      T* t = c.tab + " << r.off << " + 4 * e; t[0] = dr; t[1] = dr; t[2] = di; t[3] = di;\n";
+    else
+      o << "      T* t = c.tab + " << r.off << " + 2 * e; t[0] = dr; t[1] = di;\n";
+    o << "    }\n";
+  }
+  o << "  }\n";
   for (int i = 0; i <= P; i++) o << lay_fn("L" + std::to_string(i), s.layouts[d.lay0 + i], K);
   auto dep_of = [&](const DevPhase& ph, int i) {
     uint32_t e = 0;
@@ -292,6 +413,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       o << "    T pr[" << N << "], pq[" << N << "], lr[" << N << "], lq[" << N << "];\n";
     o << "    const qj::u32 lane = tid & 31u, warp = tid >> 5;\n    (void)lane; (void)warp;\n";
   }
+  size_t run_i = 0;   // next entry of druns
   for (int step = 0; step < P; step++) {
     const int ph = bwd ? P - 1 - step : step;
     const DevPhase& Ph = s.phases[d.phase0 + ph];
@@ -303,12 +425,10 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
     // CNOTs that open the phase (forward order) with the control on a thread bit and the target on a
     // register bit >= 1 are conditional register swaps; they become an XOR of the thread's base
     // address instead: at the load in the forward, at the store in the backward (applied last there).
+    size_t n_fold = 0;
+    const std::vector<int> order = phase_order(s, Ph, bwd, &n_fold);
     std::vector<const DevOp*> fold;
-    for (int oi = Ph.op_begin; oi < Ph.op_end; oi++) {
-      const DevOp& op = s.ops[oi];
-      if (op.kind != K_CNOT_RT || op.a < 1) break;
-      fold.push_back(&op);
-    }
+    for (size_t f = 0; f < n_fold; f++) fold.push_back(&s.ops[Ph.op_begin + (int)f]);
     auto fold_smem = [&](const DevLayout& Lx) {
       std::string t;
       for (const DevOp* op : fold)
@@ -377,16 +497,16 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
             << ", " << LQ(i + 1) << ");\n";
         // lambda = d(e) psi, d(e) = gq[K] + sum_j (bit_j(e) ? -g_j : g_j)
         o << "      }\n      qj::stage_bwd<T, " << K << ", " << NTHR << ", S_SELF>(c);\n      __syncthreads();\n";
-        o << "      if (a.lam_in == nullptr) {\n        double dt = c.gq[" << K << "];\n";
+        o << "      if (a.lam_in == nullptr) {\n        T dt = c.gq[" << K << "];\n";
         for (int jb = 0; jb < Ph.n_tbits; jb++)
           o << "        dt += ((tid >> " << jb << ") & 1u) ? -c.gq[" << (int)Ph.tbit[jb] << "] : c.gq[" << (int)Ph.tbit[jb] << "];\n";
-        // d(i) = dt + sum_r (bit r of i ? -g_r : g_r): the all-plus value in double, then a butterfly in T
-        // (subtract 2 g_r for every set register bit), then lambda = d * psi in T
+        // d(i) = dt + sum_r (bit r of i ? -g_r : g_r): the all-plus value, then a butterfly (subtract 2 g_r
+        // for every set register bit), then lambda = d * psi, all in T
         o << "        T dd[" << N << "];\n        dd[0] = (T)(dt";
         for (int r = 0; r < R; r++) o << " + c.gq[" << (int)Ph.rbit[r] << "]";
         o << ");\n";
         for (int r = 0; r < R; r++)
-          o << "        { const T m = (T)(2.0 * c.gq[" << (int)Ph.rbit[r] << "]); for (int i = 0; i < " << (1 << r)
+          o << "        { const T m = T(2) * c.gq[" << (int)Ph.rbit[r] << "]; for (int i = 0; i < " << (1 << r)
             << "; i++) dd[i + " << (1 << r) << "] = dd[i] - m; }\n";
         for (int i = 0; i < N; i++)
           o << "        " << LR(i) << " = dd[" << i << "] * " << PR(i) << "; " << LQ(i) << " = dd[" << i << "] * " << PQ(i) << ";\n";
@@ -409,9 +529,6 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       }
     }
     // ---- ops
-    std::vector<int> order;
-    for (int oi = Ph.op_begin + (int)fold.size(); oi < Ph.op_end; oi++) order.push_back(oi);
-    if (bwd) std::reverse(order.begin(), order.end());
     // gradient partial of a rotation op (backward): one per thread, or summed over 2^gs lanes first
     auto emit_grad = [&](const DevOp& op, const std::string& expr) {
       if (gs == 0)
@@ -513,29 +630,28 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       }
     };
     // A run of diagonal ops (tangent-form RZ: amplitude times 1 - i cs, cs = +-c by the qubit's bit; CZ:
-    // sign flips) is one diagonal factor D per amplitude: a thread-uniform part (RZ and CZ on thread bits)
-    // times one factor per register bit that an RZ or a register-thread CZ touches, combined by a
-    // butterfly over those bits; register-register CZs commute with the rest and are applied after.
+    // sign flips) is one diagonal factor D per amplitude: the product of the run's register-bit RZ
+    // factors for the amplitude's values of the used register bits (a table entry, per sample: see
+    // DiagRun), times a thread-uniform part (RZ and CZ on thread bits) and the signs of register-thread
+    // CZs; register-register CZs commute with the rest and are applied after.
     // Backward: conj(lambda) psi of every amplitude only gains the real factor 1 + c^2 from each RZ
     // undone, so all of the run's RZ gradients come from sums of w = Im(conj(lambda) psi) taken once at
     // the start, each times the product rho of 1 + c^2 of the run's RZs undone before it.
-    auto emit_diag_run = [&](const std::vector<int>& run) {
-      std::vector<int> used;   // register bits with a per-bit factor
+    auto emit_diag_run = [&](const DiagRun& dr) {
+      const std::vector<int>& run = dr.ops;
+      const std::vector<int>& used = dr.used;
       std::vector<int> wused;  // register bits with an RZ gradient (backward)
+      bool has_t = false;      // a thread-uniform factor
+      std::vector<std::pair<int, int>> czrt;   // (index in used, thread bit) of register-thread CZs
       for (int oi : run) {
         const DevOp& op = s.ops[oi];
-        const int rb = op.kind == K_RZ_R ? op.a : op.kind == K_CZ_RT ? op.a : -1;
-        if (rb >= 0 && std::find(used.begin(), used.end(), rb) == used.end()) used.push_back(rb);
         if (op.kind == K_RZ_R && std::find(wused.begin(), wused.end(), (int)op.a) == wused.end()) wused.push_back(op.a);
+        if (op.kind == K_RZ_T || op.kind == K_CZ_TT) has_t = true;
+        if (op.kind == K_CZ_RT)
+          czrt.push_back({(int)(std::find(used.begin(), used.end(), (int)op.a) - used.begin()), (int)op.b});
       }
-      std::sort(used.begin(), used.end());
-      auto uname = [&](int r, int b, char part) {
-        return "u" + std::to_string(r) + "_" + std::to_string(b) + part;
-      };
-      o << "      { // diagonal run of " << run.size() << " ops\n        T tr = T(1), ti = T(0);\n";
-      for (int r : used)
-        o << "        T " << uname(r, 0, 'r') << " = T(1), " << uname(r, 0, 'i') << " = T(0), " << uname(r, 1, 'r')
-          << " = T(1), " << uname(r, 1, 'i') << " = T(0);\n";
+      o << "      { // diagonal run of " << run.size() << " ops\n";
+      if (has_t) o << "        T tr = T(1), ti = T(0);\n";
       if (bwd) {
         o << "        A wt = A(0);";
         for (size_t k2 = 0; k2 < wused.size(); k2++) o << " A w" << wused[k2] << " = A(0);";
@@ -557,8 +673,6 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
               emit_grad(op, "(A)w" + std::to_string(op.a) + " * (A)rho");
               o << "        rho *= T(1) + " << cf << " * " << cf << ";\n";
             }
-            o << "        { const T cc = " << cf << "; qj::cmul(" << uname(op.a, 0, 'r') << ", " << uname(op.a, 0, 'i')
-              << ", T(1), -cc); qj::cmul(" << uname(op.a, 1, 'r') << ", " << uname(op.a, 1, 'i') << ", T(1), cc); }\n";
             break;
           case K_RZ_T: {
             const std::string sg = "(((tb >> " + std::to_string(op.a) + ") & 1u) ? T(-1) : T(1))";
@@ -573,36 +687,46 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
             o << "        if (((tb >> " << (int)op.a << ") & 1u) && ((tb >> " << (int)op.b << ") & 1u)) { tr = -tr; ti = -ti; }\n";
             break;
           case K_CZ_RT:
-            o << "        if ((tb >> " << (int)op.b << ") & 1u) { " << uname(op.a, 1, 'r') << " = -" << uname(op.a, 1, 'r')
-              << "; " << uname(op.a, 1, 'i') << " = -" << uname(op.a, 1, 'i') << "; }\n";
             break;
           default:   // K_CZ_RR
             czrr.push_back(&op);
             break;
         }
       }
-      // D over the used register bits (compressed index), then every amplitude times its D
+      // every amplitude times its D: one table entry per value of the used bits (compressed index)
       const int nu = (int)used.size();
-      o << "        T dr[" << (1 << nu) << "], di[" << (1 << nu) << "];\n        dr[0] = tr; di[0] = ti;\n";
-      for (int k2 = 0; k2 < nu; k2++)
-        o << "        for (int j = 0; j < " << (1 << k2) << "; j++) { dr[j + " << (1 << k2) << "] = dr[j]; di[j + " << (1 << k2)
-          << "] = di[j]; qj::cmul(dr[j + " << (1 << k2) << "], di[j + " << (1 << k2) << "], " << uname(used[k2], 1, 'r') << ", "
-          << uname(used[k2], 1, 'i') << "); qj::cmul(dr[j], di[j], " << uname(used[k2], 0, 'r') << ", " << uname(used[k2], 0, 'i')
-          << "); }\n";
-      for (int i = 0; i < N; i++) {
-        int idx = 0;
-        for (int k2 = 0; k2 < nu; k2++)
-          if ((i >> used[k2]) & 1) idx |= 1 << k2;
-        const std::string D = "dr[" + std::to_string(idx) + "], di[" + std::to_string(idx) + "]";
-        if (!bwd) {
-          o << "        qj::cmul(re[" << i << "], im[" << i << "], " << D << ");\n";
-        } else if (pk) {
-          o << "        { const float2 x = X[" << i << "], y = Y[" << i << "]; X[" << i << "] = qj::pfma(qj::f2(-di[" << idx
-            << "]), y, __fmul2_rn(qj::f2(dr[" << idx << "]), x)); Y[" << i << "] = qj::pfma(qj::f2(di[" << idx
-            << "]), x, __fmul2_rn(qj::f2(dr[" << idx << "]), y)); }\n";
+      for (int idx = 0; idx < (1 << nu); idx++) {
+        std::string flip;   // register-thread CZs whose register bit is set in this entry
+        for (auto& zc : czrt)
+          if ((idx >> zc.first) & 1) flip += std::string(flip.empty() ? "" : " ^ ") + "((tb >> " + std::to_string(zc.second) + ") & 1u)";
+        const bool plain = !has_t && flip.empty();
+        const int e0 = dr.off + dr.es * idx;
+        o << "        {";
+        if (pk && plain) {
+          o << " const float4 f = *reinterpret_cast<const float4*>(c.tab + " << e0 << ");"
+            << " const float2 fr2 = make_float2(f.x, f.y), fi2 = make_float2(f.z, f.w), fn2 = make_float2(-f.z, -f.w);\n";
         } else {
-          o << "        qj::cmul(pr[" << i << "], pq[" << i << "], " << D << "); qj::cmul(lr[" << i << "], lq[" << i << "], " << D << ");\n";
+          o << " T fr, fi; qj::ldtab(c.tab + " << e0 << ", " << (dr.es == 4 ? 2 : 1) << ", fr, fi);";
+          if (has_t) o << " qj::cmul(fr, fi, tr, ti);";
+          if (!flip.empty()) o << " if (" << flip << ") { fr = -fr; fi = -fi; }";
+          if (pk) o << " const float2 fr2 = qj::f2(fr), fi2 = qj::f2(fi), fn2 = qj::f2(-fi);";
+          o << "\n";
         }
+        for (int i = 0; i < N; i++) {
+          int ci = 0;
+          for (int k2 = 0; k2 < nu; k2++)
+            if ((i >> used[k2]) & 1) ci |= 1 << k2;
+          if (ci != idx) continue;
+          if (!bwd) {
+            o << "          qj::cmul(re[" << i << "], im[" << i << "], fr, fi);\n";
+          } else if (pk) {
+            o << "          { const float2 x = X[" << i << "], y = Y[" << i << "]; X[" << i << "] = qj::pfma(fn2, y, __fmul2_rn(fr2, x)); Y["
+              << i << "] = qj::pfma(fi2, x, __fmul2_rn(fr2, y)); }\n";
+          } else {
+            o << "          qj::cmul(pr[" << i << "], pq[" << i << "], fr, fi); qj::cmul(lr[" << i << "], lq[" << i << "], fr, fi);\n";
+          }
+        }
+        o << "        }\n";
       }
       for (const DevOp* op : czrr) {
         const std::string t = std::to_string(N) + ", " + std::to_string(1 << op->a) + ", " + std::to_string(1 << op->b);
@@ -612,23 +736,20 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       }
       o << "      }\n";
     };
-    auto is_diag = [&](int oi) {
-      const int kd = s.ops[oi].kind;
-      return kd == K_RZ_R || kd == K_RZ_T || kd == K_CZ_RR || kd == K_CZ_RT || kd == K_CZ_TT;
-    };
-    for (size_t x = 0; x < order.size();) {
-      size_t y = x;
-      int n_rz = 0;
-      if (s.merge_diag)
-        while (y < order.size() && is_diag(order[y])) n_rz += s.ops[order[y++]].rot;
-      // the merged run costs a complex multiply per amplitude (two in the backward, where it also saves
-      // two FMAs of gradient and four of updates per RZ): worth it from 2 RZs backward, 4 forward
-      if (n_rz >= (bwd ? 2 : 4)) {
-        emit_diag_run(std::vector<int>(order.begin() + x, order.begin() + y));
-        x = y;
-      } else {
-        emit_op(order[x++]);
+    {
+      const std::vector<std::pair<size_t, size_t>> rng = diag_ranges(s, order, bwd);
+      size_t x = 0;
+      for (auto& xy : rng) {
+        for (; x < xy.first; x++) emit_op(order[x]);
+        const DiagRun& dr = druns[run_i++];
+        if (dr.ops != std::vector<int>(order.begin() + xy.first, order.begin() + xy.second)) {
+          fprintf(stderr, "qsim: diagonal run tables out of step with the generated code\n");
+          abort();
+        }
+        emit_diag_run(dr);
+        x = xy.second;
       }
+      for (; x < order.size(); x++) emit_op(order[x]);
     }
     // ---- prefix partials (backward of the first pass of a product-prefix plan; a.ppart set only there)
     if (bwd && last && prefix) {
@@ -654,8 +775,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       o << "        T* ws = reinterpret_cast<T*>(c.tile);\n        __syncthreads();\n";
       for (int r = 0; r < R; r++)
         for (int b = 0; b < 2; b++)
-          o << "        { T vr = Ftr, vi = Fti; qj::cmul(vr, vi, nr[" << r << "][" << b << " ^ swr[" << r << "]], ni[" << r
-            << "][" << b << " ^ swr[" << r << "]]); qj::prefix_put<T, " << NTHR << ", S_SELF::CTA>(vr, vi, "
+          o << "        { T vr = Ftr, vi = Fti; qj::cmul(vr, vi, qj::sel(swr[" << r << "], nr[" << r << "][" << (b ^ 1) << "], nr["
+            << r << "][" << b << "]), qj::sel(swr[" << r << "], ni[" << r << "][" << (b ^ 1) << "], ni[" << r << "][" << b
+            << "])); qj::prefix_put<T, " << NTHR << ", S_SELF::CTA>(vr, vi, "
             << 2 * (int)Ph.rbit[r] + b << ", ws, " << NS << ", tid); }\n";
       for (int jb = 0; jb < NT; jb++) {
         o << "        { T er = Sr, ei = Si;";
@@ -747,16 +869,19 @@ int default_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
 int multi_max_k_for(int dtype) { return dtype == QSIM_C128 ? 10 : 11; }
 
 // Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
-size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta, int max_regs) {
+size_t jit_smem_bytes(const Schedule& s, const DevPass& d, bool bwd, int cta) {
+  const int dtype = s.dtype;
   const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
   const size_t no = (size_t)d.n_ops + 1;   // op coefficients + the pass scale
-  if (!bwd) return (tile + no * sc + no + 15) & ~(size_t)15;
+  const size_t tab = (size_t)diag_table_units(s, d, bwd) * sc;
+  if (!bwd) return (tile + tab + no * sc + no + 15) & ~(size_t)15;
   const size_t nthr = (size_t)1 << (d.k - d.R);
   const size_t ng = d.n_gslots > 0 ? d.n_gslots : 1;
   const size_t red = 2 * tile;
-  const size_t parts = ng * (nthr >> grad_level(d, dtype, cta, max_regs));
+  const size_t parts = ng * (nthr >> grad_level(d, dtype, cta, s.max_regs, tab));
   const size_t gq = (red + parts * sc + 15) & ~(size_t)15;
-  const size_t cf = gq + (d.k + 2) * 8;
+  const size_t tb = (gq + (d.k + 2) * 8 + 15) & ~(size_t)15;
+  const size_t cf = tb + tab;
   const size_t fm = cf + no * sc;
   return (fm + no + 15) & ~(size_t)15;
 }
@@ -911,7 +1036,7 @@ int jit_build(const Schedule& s, JitPlan& jp, std::string& err) {
       const DevPass& d = dir == 0 ? s.passes[p].dev : s.passes[p].devb;
       cudaKernel_t k = loaded[names[p]];
       ks[p].fn = reinterpret_cast<void*>(k);
-      ks[p].smem = jit_smem_bytes(d, s.dtype, dir == 1, 0, s.max_regs);
+      ks[p].smem = jit_smem_bytes(s, d, dir == 1, 0);
       ks[p].nthr = 1 << (d.k - d.R);
       if (ks[p].smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
@@ -943,12 +1068,12 @@ static std::string multi_unit(const Schedule& s, const DevPass& d, bool bwd, int
     << "  const long long ti = tile0 + g;\n"
     << "  const bool valid = ti < ntiles;\n";
   if (!bwd)
-    u << "  constexpr int GB = qj::FwdGroupSmem<" << T << ", " << K << ", S_" << name << "::NOPS>::BYTES;\n"
+    u << "  constexpr int GB = qj::FwdGroupSmem<" << T << ", " << K << ", S_" << name << "::NOPS, S_" << name << "::NTAB>::BYTES;\n"
       << "  qj::fwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
       << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
   else
     u << "  constexpr int GB = qj::BwdGroupSmem<" << T << ", " << K << ", " << R << ", NTHR, S_" << name << "::NOPS, S_"
-      << name << "::NGS, S_" << name << "::GS>::BYTES;\n"
+      << name << "::NGS, S_" << name << "::GS, S_" << name << "::NTAB>::BYTES;\n"
       << "  qj::bwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
       << ">(*a, valid ? ti : tile0, valid, tid, smem + (size_t)g * GB);\n";
   u << "}\n";
@@ -1030,7 +1155,7 @@ int jit_build_multi(const std::vector<const Schedule*>& scheds, int cta_f, int c
         jm.kind[c][2 * p + dir] = kind_id[dir][name];
         const int nthr = 1 << (d.k - d.R);
         const size_t groups = (size_t)cta / nthr;
-        max_smem[dir] = std::max(max_smem[dir], groups * jit_smem_bytes(d, s.dtype, dir == 1, cta));
+        max_smem[dir] = std::max(max_smem[dir], groups * jit_smem_bytes(s, d, dir == 1, cta));
       }
     }
   }

@@ -84,10 +84,10 @@ void jit_free_multi(JitMulti& jm);
 
 // Full NVRTC program text and the kernel name of every pass (forward, backward).
 std::string jit_generate(const Schedule& s, std::vector<std::string>& fwd_names, std::vector<std::string>& bwd_names);
-// Shared-memory bytes of one tile group; cta: the queue kernel's CTA size (0: single-circuit kernel);
-// max_regs: the plan's register cap (a single-circuit backward then sizes its gradient partials so that
-// as many CTAs fit in shared memory as in the registers).
-size_t jit_smem_bytes(const DevPass& d, int dtype, bool bwd, int cta = 0, int max_regs = 0);
+// Shared-memory bytes of one tile group; cta: the queue kernel's CTA size (0: single-circuit kernel).
+// With a register cap in the plan (s.max_regs) a single-circuit backward sizes its gradient partials so
+// that as many CTAs fit in shared memory as in the registers.
+size_t jit_smem_bytes(const Schedule& s, const DevPass& d, bool bwd, int cta = 0);
 // NVRTC-compile (or fetch from the on-disk cache) the plan's kernels; host only, no CUDA calls.
 int jit_compile(const Schedule& s, std::map<std::string, std::string>& cubins, std::vector<std::string>& fwd_names,
                 std::vector<std::string>& bwd_names, std::string& err);

@@ -158,15 +158,30 @@ __device__ __forceinline__ void swp(T* re, T* im) {
     }
 }
 
+// p != 0 ? a : b as a predicated select. Written as C++ conditionals, the register swaps of a CNOT
+// whose control is a thread bit were compiled as branches that kept both register assignments live.
+__device__ __forceinline__ float sel(u32 p, float a, float b) {
+  float r;
+  asm("{ .reg .pred q; setp.ne.u32 q, %1, 0; selp.f32 %0, %2, %3, q; }" : "=f"(r) : "r"(p), "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ double sel(u32 p, double a, double b) {
+  double r;
+  asm("{ .reg .pred q; setp.ne.u32 q, %1, 0; selp.f64 %0, %2, %3, q; }" : "=d"(r) : "r"(p), "d"(a), "d"(b));
+  return r;
+}
+__device__ __forceinline__ float2 sel2(u32 p, float2 a, float2 b) { return make_float2(sel(p, a.x, b.x), sel(p, a.y, b.y)); }
+
 template <int N, int SA, typename T>
 __device__ __forceinline__ void cnot_t(T* re, T* im, bool ctl) {
+  const u32 p = ctl ? 1u : 0u;
 #pragma unroll
   for (int i = 0; i < N; i++)
     if (!(i & SA)) {
       const int j = i | SA;
       const T ar = re[i], ai = im[i], br = re[j], bi = im[j];
-      re[i] = ctl ? br : ar; im[i] = ctl ? bi : ai;
-      re[j] = ctl ? ar : br; im[j] = ctl ? ai : bi;
+      re[i] = sel(p, br, ar); im[i] = sel(p, bi, ai);
+      re[j] = sel(p, ar, br); im[j] = sel(p, ai, bi);
     }
 }
 
@@ -274,13 +289,14 @@ __device__ __forceinline__ void swp_p(float2* X, float2* Y) {
 
 template <int N, int SA>
 __device__ __forceinline__ void cnot_tp(float2* X, float2* Y, bool ctl) {
+  const u32 p = ctl ? 1u : 0u;
 #pragma unroll
   for (int i = 0; i < N; i++)
     if (!(i & SA)) {
       const int j = i | SA;
       const float2 a = X[i], u = Y[i], b = X[j], v = Y[j];
-      X[i] = ctl ? b : a; Y[i] = ctl ? v : u;
-      X[j] = ctl ? a : b; Y[j] = ctl ? u : v;
+      X[i] = sel2(p, b, a); Y[i] = sel2(p, v, u);
+      X[j] = sel2(p, a, b); Y[j] = sel2(p, u, v);
     }
 }
 
@@ -544,8 +560,9 @@ struct Ctx {
   void* tile;            // forward: the tile; backward: psi
   void* tile2;           // backward: lambda
   T* cf;                 // op coefficients of this tile's sample, [NOPS] = pass scale (shared memory)
+  T* tab;                // factor tables of the merged diagonal runs (shared memory, 16-byte aligned)
   u8* fm;                // op forms (shared memory)
-  double* gq;            // backward, lambda init: g of every tile bit, [K] = fixed-bit part
+  T* gq;                 // backward, lambda init: g of every tile bit, [K] = fixed-bit part
   i64 base;              // element offset of the tile (bits outside the tile) in the batched state, read layout
   i64 base_out;          // the same in the layout the pass writes
   i64 b, t;              // sample, tile within the sample
@@ -569,6 +586,16 @@ __device__ __forceinline__ void cmul(T& ar, T& ai, T br, T bi) {
   ar = r;
 }
 
+// A diagonal-run table entry (re at p[0], im at p[di]); with di = 1 one vector load.
+__device__ __forceinline__ void ldtab(const float* p, int di, float& r, float& i) {
+  if (di == 1) { const float2 v = *reinterpret_cast<const float2*>(p); r = v.x; i = v.y; }
+  else { r = p[0]; i = p[di]; }
+}
+__device__ __forceinline__ void ldtab(const double* p, int di, double& r, double& i) {
+  if (di == 1) { const double2 v = *reinterpret_cast<const double2*>(p); r = v.x; i = v.y; }
+  else { r = p[0]; i = p[di]; }
+}
+
 // product of phi over the tile-index bits of tile t (the qubits outside the tile)
 template <typename T>
 __device__ __forceinline__ void phi_nonlocal(const Args& a, const T* ph, i64 t, T& re, T& im) {
@@ -582,40 +609,58 @@ __device__ __forceinline__ void phi_nonlocal(const Args& a, const T* ph, i64 t, 
 
 // Contraction of the thread's N = 2^R register elements w_i = conj(lambda_i) with the register qubits'
 // factors f_r(bit r of i): S = full contraction; nu[r][b] = the same over elements with bit r = b,
-// leaving factor r out (prefix and suffix products over r).
+// leaving factor r out. The high bits are contracted one at a time (C_r: w contracted over bits
+// r..R-1, 2^r values); nu[r][b] pairs the half of C_(r+1) with bit r = b with the product state P_r of
+// the factors of bits 0..r-1. About 5N complex multiply-adds instead of 3RN for per-element prefix and
+// suffix products.
+template <typename T, int R, int r>
+struct PrefixStep {   // bit r of the contraction (compile-time r: every register index is a constant)
+  static __device__ __forceinline__ void run(T* cr, T* ci, const T (*fr)[2], const T (*fi)[2], T (*nr)[2], T (*ni)[2]) {
+    constexpr int H = 1 << r;
+    T pr[H], pi[H];   // P_r
+    pr[0] = T(1); pi[0] = T(0);
+#pragma unroll
+    for (int q = 0; q < r; q++)
+#pragma unroll
+      for (int j = 0; j < (1 << q); j++) {
+        pr[j + (1 << q)] = pr[j]; pi[j + (1 << q)] = pi[j];
+        cmul(pr[j + (1 << q)], pi[j + (1 << q)], fr[q][1], fi[q][1]);
+        cmul(pr[j], pi[j], fr[q][0], fi[q][0]);
+      }
+#pragma unroll
+    for (int b = 0; b < 2; b++) {
+      T ar = T(0), ai = T(0);
+#pragma unroll
+      for (int j = 0; j < H; j++) {
+        const T xr = cr[j + b * H], xi = ci[j + b * H];
+        ar += xr * pr[j] - xi * pi[j];
+        ai += xr * pi[j] + xi * pr[j];
+      }
+      nr[r][b] = ar; ni[r][b] = ai;
+    }
+#pragma unroll
+    for (int j = 0; j < H; j++) {
+      T ar = cr[j], ai = ci[j], br = cr[j + H], bi = ci[j + H];
+      cmul(ar, ai, fr[r][0], fi[r][0]);
+      cmul(br, bi, fr[r][1], fi[r][1]);
+      cr[j] = ar + br; ci[j] = ai + bi;
+    }
+    PrefixStep<T, R, r - 1>::run(cr, ci, fr, fi, nr, ni);
+  }
+};
+template <typename T, int R>
+struct PrefixStep<T, R, -1> {
+  static __device__ __forceinline__ void run(T*, T*, const T (*)[2], const T (*)[2], T (*)[2], T (*)[2]) {}
+};
+
 template <typename T, int N, int R>
 __device__ __forceinline__ void prefix_contract(const T* wr, const T* wi, const T (*fr)[2], const T (*fi)[2],
                                                 T& Sr, T& Si, T (*nr)[2], T (*ni)[2]) {
-  Sr = T(0);
-  Si = T(0);
+  T cr[N], ci[N];
 #pragma unroll
-  for (int r = 0; r < R; r++) nr[r][0] = nr[r][1] = ni[r][0] = ni[r][1] = T(0);
-#pragma unroll
-  for (int i = 0; i < N; i++) {
-    T pr[R + 1], pi[R + 1], sr[R + 1], si[R + 1];
-    pr[0] = T(1); pi[0] = T(0);
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-      pr[r + 1] = pr[r]; pi[r + 1] = pi[r];
-      cmul(pr[r + 1], pi[r + 1], fr[r][(i >> r) & 1], fi[r][(i >> r) & 1]);
-    }
-    sr[R] = T(1); si[R] = T(0);
-#pragma unroll
-    for (int r = R - 1; r >= 0; r--) {
-      sr[r] = sr[r + 1]; si[r] = si[r + 1];
-      cmul(sr[r], si[r], fr[r][(i >> r) & 1], fi[r][(i >> r) & 1]);
-    }
-    Sr += wr[i] * pr[R] - wi[i] * pi[R];
-    Si += wr[i] * pi[R] + wi[i] * pr[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-      T xr = pr[r], xi = pi[r];
-      cmul(xr, xi, sr[r + 1], si[r + 1]);
-      const int b = (i >> r) & 1;
-      nr[r][b] += wr[i] * xr - wi[i] * xi;
-      ni[r][b] += wr[i] * xi + wi[i] * xr;
-    }
-  }
+  for (int i = 0; i < N; i++) { cr[i] = wr[i]; ci[i] = wi[i]; }
+  PrefixStep<T, R, R - 1>::run(cr, ci, fr, fi, nr, ni);
+  Sr = cr[0]; Si = ci[0];
 }
 
 // One prefix partial slot (re, im) of this thread into the per-warp sums in shared memory (ws, one row
@@ -699,11 +744,13 @@ __device__ __forceinline__ void tile_coords(const Args& a, i64 tile, i64& b, i64
 // ---------------------------------------------------------------- forward pass
 // Shared-memory bytes of one tile group (forward): tile (also the <Z> reduction area), coefficients and
 // the pass scale (NOPS + 1 values), forms.
-template <typename T, int K, int NOPS>
+template <typename T, int K, int NOPS, int NTAB>
 struct FwdGroupSmem {
   static constexpr int NO = NOPS + 1;
   static constexpr int TILE = (2 * (int)sizeof(T)) << K;
-  static constexpr int BYTES = (TILE + NO * (int)sizeof(T) + NO + 15) & ~15;
+  static constexpr int TB = TILE;                               // diagonal-run factor tables
+  static constexpr int CF = TB + NTAB * (int)sizeof(T);
+  static constexpr int BYTES = (CF + NO * (int)sizeof(T) + NO + 15) & ~15;
 };
 
 // One tile (sample b0 + tile / tps) processed by the NTHR threads `tid` of a group owning `smem`.
@@ -711,13 +758,14 @@ struct FwdGroupSmem {
 // computes on another tile's data but writes nothing to global memory.
 template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void fwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
-  typedef FwdGroupSmem<T, K, Spec::NOPS> SM;
-  T* cf = reinterpret_cast<T*>(smem + SM::TILE);
+  typedef FwdGroupSmem<T, K, Spec::NOPS, Spec::NTAB> SM;
+  T* cf = reinterpret_cast<T*>(smem + SM::CF);
   Ctx<T> c;
   c.a = &a;
   c.tile = smem;
   c.tile2 = nullptr;
   c.cf = cf;
+  c.tab = reinterpret_cast<T*>(smem + SM::TB);
   c.fm = reinterpret_cast<u8*>(cf + SM::NO);
   c.gq = nullptr;
   c.tid = tid;
@@ -741,6 +789,7 @@ __device__ __forceinline__ void stage_fwd(Ctx<T>& c) {
     fm[i] = fsrc[i];
   }
   if (c.tid == (u32)(NTHR - 1)) cf[Spec::NOPS] = reinterpret_cast<const T*>(a.scale)[c.b];
+  Spec::template build_tables<T>(c, src);
 }
 
 template <typename T, int K, int R, int NTHR, class Spec>
@@ -752,7 +801,7 @@ __device__ __forceinline__ void fwd_pass(const Args& a) {
 // ---------------------------------------------------------------- backward pass
 // Shared-memory bytes of one tile group (backward): psi, lambda, gradient warp partials, g per tile
 // bit, coefficients and forms.
-template <typename T, int K, int R, int NTHR, int NOPS, int NGS, int GS>
+template <typename T, int K, int R, int NTHR, int NOPS, int NGS, int GS, int NTAB>
 struct BwdGroupSmem {
   typedef typename Acc<T>::t A;
   static constexpr int NW = (NTHR + 31) / 32;
@@ -762,7 +811,8 @@ struct BwdGroupSmem {
   // gradient partials [NG][NTHR >> GS]: one per slot and group of 2^GS neighbouring threads
   static constexpr int RED = 2 * TILE;
   static constexpr int GQ = (RED + NG * (NTHR >> GS) * (int)sizeof(A) + 15) & ~15;
-  static constexpr int CF = GQ + (K + 2) * 8;
+  static constexpr int TB = (GQ + (K + 2) * 8 + 15) & ~15;     // diagonal-run factor tables
+  static constexpr int CF = TB + NTAB * (int)sizeof(T);
   static constexpr int FM = CF + NO * (int)sizeof(T);
   static constexpr int BYTES = (FM + NO + 15) & ~15;
 };
@@ -781,19 +831,30 @@ __device__ __forceinline__ void stage_bwd(Ctx<T>& c) {
     fm[i] = fsrc[i];
   }
   if (c.tid == (u32)(NTHR - 1)) cf[Spec::NOPS] = reinterpret_cast<const T*>(a.scale)[c.b];
+  Spec::template build_tables<T>(c, src);
   if (a.lam_in == nullptr) {
-    double* gq = c.gq;
-    for (int j = c.tid; j <= K; j += NTHR) {
-      if (j < K) {
-        gq[j] = a.grad_out[c.b * a.n + a.Q[j]];
-      } else {
+    // g in T: lambda = d psi is formed in T, and T sums keep the FP64 pipe (a small fraction of the
+    // FP32 rate) out of the per-thread work; the fixed-bit part is summed in FP64 by one warp
+    T* gq = c.gq;
+    for (int j = c.tid; j < K; j += NTHR) gq[j] = (T)a.grad_out[c.b * a.n + a.Q[j]];
+    if constexpr (NTHR >= 32) {
+      if (c.tid < 32u) {
         double dc = 0.0;
-        for (int q = 0; q < a.n_nonlocal; q++) {
+        for (int q = (int)c.tid; q < a.n_nonlocal; q += 32) {
           const double g = a.grad_out[c.b * a.n + a.QN[q]];
           dc += ((c.t >> q) & 1) ? -g : g;
         }
-        gq[K] = dc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dc += __shfl_xor_sync(0xffffffffu, dc, o);
+        if (c.tid == 0u) gq[K] = (T)dc;
       }
+    } else if (c.tid == 0u) {
+      double dc = 0.0;
+      for (int q = 0; q < a.n_nonlocal; q++) {
+        const double g = a.grad_out[c.b * a.n + a.QN[q]];
+        dc += ((c.t >> q) & 1) ? -g : g;
+      }
+      gq[K] = (T)dc;
     }
   }
 }
@@ -801,15 +862,16 @@ __device__ __forceinline__ void stage_bwd(Ctx<T>& c) {
 template <typename T, int K, int R, int NTHR, class Spec>
 __device__ __forceinline__ void bwd_tile(const Args& a, i64 tile, bool valid, u32 tid, unsigned char* smem) {
   typedef typename Acc<T>::t A;
-  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS, Spec::GS> SM;
+  typedef BwdGroupSmem<T, K, R, NTHR, Spec::NOPS, Spec::NGS, Spec::GS, Spec::NTAB> SM;
   A* red = reinterpret_cast<A*>(smem + SM::RED);
   Ctx<T> c;
   c.a = &a;
   c.tile = smem;
   c.tile2 = smem + SM::TILE;
   c.cf = reinterpret_cast<T*>(smem + SM::CF);
+  c.tab = reinterpret_cast<T*>(smem + SM::TB);
   c.fm = smem + SM::FM;
-  c.gq = reinterpret_cast<double*>(smem + SM::GQ);        // [K + 1]
+  c.gq = reinterpret_cast<T*>(smem + SM::GQ);             // [K + 1]
   c.tid = tid;
   c.valid = valid;
   tile_coords(a, tile, c.b, c.t, c.base, c.base_out);
