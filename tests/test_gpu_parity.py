@@ -372,6 +372,29 @@ def test_c3_full_size_against_oracle(q, k):
     assert ep <= 1e-4 and ei <= 1e-4, (ep, ei)
 
 
+# ---------------------------------------------------------------- many tiles, every sample weighted
+@pytest.mark.parametrize("k,ckpt", [(10, 1), (9, 0)])
+def test_backward_many_tiles_all_samples(q, k, ckpt):
+    """Far more tiles than resident CTAs (4096 and 8192) and every sample weighted, so every tile's
+    gradient partials count: complex64 against the complex128 plan on every sample, and both against
+    the FP64 oracle's adjoint sweep on the first and last sample."""
+    wl = W.ring_workload("many-tiles", 14, 256, 4, "c64", 7)
+    r = run(q, wl, "c64", "fused", k=k, checkpoint_passes=ckpt)
+    assert r["plan"].info()["n_passes"] >= 2
+    pr, ir = rounded(wl, "c64")   # the complex128 plan takes the angles complex64 saw
+    wl2 = W.Workload("many-tiles", wl.n, wl.batch, "c128", wl.gates, pr, ir, wl.grad_out)
+    r2 = run(q, wl2, "c128", "fused", k=k, checkpoint_passes=ckpt)
+    check_grad(r["dp"], r2["dp"], "c64", "dparams vs complex128")
+    for b in (0, 1, 77, 128, 254, 255):
+        check_grad(r["di"][b], r2["di"][b], "c64", f"dinputs sample {b} vs complex128")
+    np.testing.assert_allclose(r["di"], r2["di"], atol=1e-4 * np.abs(r2["di"]).max())
+    sel = [0, wl.batch - 1]
+    adp, adi = oracle.grad_adjoint(wl.gates, wl.n, pr, ir[sel], wl.grad_out[sel])
+    for j, b in enumerate(sel):
+        check_grad(r["di"][b], adi[j], "c64", f"dinputs sample {b} vs oracle")
+        check_grad(r2["di"][b], adi[j], "c128", f"complex128 dinputs sample {b} vs oracle")
+
+
 # ---------------------------------------------------------------- backward vs central finite differences
 @pytest.mark.parametrize("dtype,tol", [("c64", 1e-4), ("c128", 1e-7)])
 def test_backward_against_central_finite_differences(q, dtype, tol):
