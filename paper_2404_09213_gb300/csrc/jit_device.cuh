@@ -460,9 +460,23 @@ __device__ __forceinline__ void ldpp(const void* tile, u32 w, float2& x0, float2
   x0 = make_float2(a.x, a.y); y0 = make_float2(a.z, a.w);
   x1 = make_float2(b.x, b.y); y1 = make_float2(b.z, b.w);
 }
+__device__ __forceinline__ u32 smem_u32(const void* p) {
+  u32 r;
+  asm("{ .reg .u64 t; cvta.to.shared.u64 t, %1; cvt.u32.u64 %0, t; }" : "=r"(r) : "l"(p));
+  return r;
+}
+// The stores go out as two 8-byte halves per word, each straight from its register pair: written as
+// one 16-byte store, the compiler first copied X and Y into four adjacent registers (about 3 MOVs per
+// amplitude and exchange).
+template <int OFF>
+__device__ __forceinline__ void sts2o(u32 a, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0+%3], {%1, %2};" ::"r"(a), "f"(v.x), "f"(v.y), "n"(OFF) : "memory");
+}
 __device__ __forceinline__ void stpp(void* tile, u32 w, float2 x0, float2 y0, float2 x1, float2 y1) {
-  reinterpret_cast<float4*>(tile)[w] = make_float4(x0.x, x0.y, y0.x, y0.y);
-  reinterpret_cast<float4*>(tile)[w ^ 1u] = make_float4(x1.x, x1.y, y1.x, y1.y);
+  const u32 base = smem_u32(tile);
+  const u32 a0 = base + 16u * w, a1 = base + 16u * (w ^ 1u);
+  sts2o<0>(a0, x0); sts2o<8>(a0, y0);
+  sts2o<0>(a1, x1); sts2o<8>(a1, y1);
 }
 template <bool ADD>
 __device__ __forceinline__ void ldppx(const void* tile, u32 s, u32 c, float2& x0, float2& y0, float2& x1, float2& y1) {

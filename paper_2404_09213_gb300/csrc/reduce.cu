@@ -353,34 +353,75 @@ cudaError_t launch_z_final(const double* zpart, int k, const uint8_t* d_Qnl, int
 
 // ------------------------------------------------------------------ Pauli frame: returned states, loss signs
 // out[b][i] = i^k (-1)^popc(zi & (i ^ xi)) S[b][i ^ xi], with xi, zi the frame's masks in index bits (qubit q
-// at index bit n - 1 - q)
-template <typename T>
+// at index bit n - 1 - q). A thread takes E consecutive elements i0..i0+E-1 (i0 a multiple of E): their
+// sources are the aligned block at (i0 ^ xi) with E - 1 cleared, element e coming from position
+// e ^ (xi & (E - 1)), so both sides move as 16-byte vectors.
+template <typename T, int E>
+__device__ __forceinline__ void ld_block(const T* p, T* re, T* im) {
+  if constexpr (E == 4 && sizeof(T) == 4) {
+    const float4 u = reinterpret_cast<const float4*>(p)[0], v = reinterpret_cast<const float4*>(p)[1];
+    re[0] = u.x; im[0] = u.y; re[1] = u.z; im[1] = u.w; re[2] = v.x; im[2] = v.y; re[3] = v.z; im[3] = v.w;
+  } else if constexpr (E == 4) {
+#pragma unroll
+    for (int e = 0; e < 4; e++) { const double2 u = reinterpret_cast<const double2*>(p)[e]; re[e] = u.x; im[e] = u.y; }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; e++) { re[e] = p[2 * e]; im[e] = p[2 * e + 1]; }
+  }
+}
+template <typename T, int E>
+__device__ __forceinline__ void st_block(T* p, const T* re, const T* im) {
+  if constexpr (E == 4 && sizeof(T) == 4) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(re[0], im[0], re[1], im[1]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(re[2], im[2], re[3], im[3]);
+  } else if constexpr (E == 4) {
+#pragma unroll
+    for (int e = 0; e < 4; e++) reinterpret_cast<double2*>(p)[e] = make_double2(re[e], im[e]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; e++) { p[2 * e] = re[e]; p[2 * e + 1] = im[e]; }
+  }
+}
+
+template <typename T, int E>
 __global__ void frame_fixup_kernel(const T* S, T* out, const uint64_t* fx, const uint64_t* fz, const int32_t* fk,
                                    int n, int B) {
   const int64_t per = (int64_t)1 << n;
-  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= per * B) return;
-  const int64_t b = id >> n, i = id & (per - 1);
+  const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * E;
+  if (i0 >= per * B) return;
+  const int64_t b = i0 >> n, i = i0 & (per - 1);
   // qubit q sits at index bit n - 1 - q: a 64-bit reversal, then a shift
   const uint64_t xi = (uint64_t)__brevll((unsigned long long)fx[b]) >> (64 - n);
   const uint64_t zi = (uint64_t)__brevll((unsigned long long)fz[b]) >> (64 - n);
-  const int64_t j = (int64_t)((uint64_t)i ^ xi);
-  const T* src = S + 2 * (b * per + j);
-  T re = src[0], im = src[1];
-  if (__popcll((unsigned long long)(zi & (uint64_t)j)) & 1) {
-    re = -re;
-    im = -im;
+  const int64_t j0 = (int64_t)(((uint64_t)i ^ xi) & ~(uint64_t)(E - 1));
+  T re[E], im[E];
+  ld_block<T, E>(S + 2 * (b * per + j0), re, im);
+  // permute by the low bits of xi (conditional swaps: no dynamic register index)
+#pragma unroll
+  for (int m = 1; m < E; m <<= 1)
+    if (xi & (uint64_t)m) {
+#pragma unroll
+      for (int e = 0; e < E; e++)
+        if (!(e & m)) {
+          const T r = re[e], v = im[e];
+          re[e] = re[e | m]; im[e] = im[e | m];
+          re[e | m] = r; im[e | m] = v;
+        }
+    }
+  const int k = fk[b] & 3;
+  T ro[E], io[E];
+#pragma unroll
+  for (int e = 0; e < E; e++) {
+    T r = re[e], v = im[e];
+    if (__popcll((unsigned long long)(zi & ((uint64_t)(i + e) ^ xi))) & 1) { r = -r; v = -v; }
+    T r2 = r, i2 = v;   // times i^k
+    if (k == 1) { r2 = -v; i2 = r; }
+    else if (k == 2) { r2 = -r; i2 = -v; }
+    else if (k == 3) { r2 = v; i2 = -r; }
+    ro[e] = r2;
+    io[e] = i2;
   }
-  T r2 = re, i2 = im;   // times i^k
-  switch (fk[b] & 3) {
-    case 1: r2 = -im; i2 = re; break;
-    case 2: r2 = -re; i2 = -im; break;
-    case 3: r2 = im; i2 = -re; break;
-    default: break;
-  }
-  T* dst = out + 2 * (b * per + i);
-  dst[0] = r2;
-  dst[1] = i2;
+  st_block<T, E>(out + 2 * (b * per + i), ro, io);
 }
 
 cudaError_t launch_frame_fixup(const void* S, void* out, const uint64_t* fx, const uint64_t* fz, const int32_t* fk,
@@ -388,11 +429,19 @@ cudaError_t launch_frame_fixup(const void* S, void* out, const uint64_t* fx, con
   const int64_t tot = ((int64_t)1 << n) * B;
   if (tot == 0) return cudaSuccess;
   const int thr = 256;
-  const unsigned blocks = (unsigned)((tot + thr - 1) / thr);
-  if (dtype == QSIM_C128)
-    frame_fixup_kernel<double><<<blocks, thr, 0, st>>>((const double*)S, (double*)out, fx, fz, fk, n, B);
-  else
-    frame_fixup_kernel<float><<<blocks, thr, 0, st>>>((const float*)S, (float*)out, fx, fz, fk, n, B);
+  if (n >= 2) {   // 4 elements per thread: whole vectors on both sides
+    const unsigned blocks = (unsigned)((tot / 4 + thr - 1) / thr);
+    if (dtype == QSIM_C128)
+      frame_fixup_kernel<double, 4><<<blocks, thr, 0, st>>>((const double*)S, (double*)out, fx, fz, fk, n, B);
+    else
+      frame_fixup_kernel<float, 4><<<blocks, thr, 0, st>>>((const float*)S, (float*)out, fx, fz, fk, n, B);
+  } else {
+    const unsigned blocks = (unsigned)((tot + thr - 1) / thr);
+    if (dtype == QSIM_C128)
+      frame_fixup_kernel<double, 1><<<blocks, thr, 0, st>>>((const double*)S, (double*)out, fx, fz, fk, n, B);
+    else
+      frame_fixup_kernel<float, 1><<<blocks, thr, 0, st>>>((const float*)S, (float*)out, fx, fz, fk, n, B);
+  }
   g_kernel_launches++;
   return cudaGetLastError();
 }
@@ -415,16 +464,20 @@ cudaError_t launch_frame_gsign(const double* grad_out, const uint64_t* fx, int n
 }
 
 // ------------------------------------------------------------------ gradients
-// G[j][b] = gm[g_j][b] * sum over the sample's tiles of the slot's partials (block per (j, b)).
+// G[j][b] = gm[g_j][b] * sum over the sample's tiles of the slot's partials (a warp per (j, b): strided
+// lane sums, then a butterfly, in a fixed order).
 __global__ void grad_gather_kernel(GradReduceArgs a) {
-  __shared__ double sh[32];
-  const int j = blockIdx.x / a.B, b = blockIdx.x - (blockIdx.x / a.B) * a.B;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)a.n_occ * a.B) return;
+  const int j = (int)(w / a.B), b = (int)(w - (w / a.B) * a.B);
   if (a.occ_slot[j] < 0) return;   // a prefix rotation: no pass partials (launch_prefix_grad writes G)
-  const double* src = a.gpart + (a.occ_slot[j] * a.B + b) * a.tiles_per_sample;
+  const double* src = a.gpart + ((int64_t)a.occ_slot[j] * a.B + b) * a.tiles_per_sample;
   double acc = 0.0;
-  for (int64_t t = threadIdx.x; t < a.tiles_per_sample; t += blockDim.x) acc += src[t];
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) a.G[(int64_t)j * a.B + b] = acc * a.gm[(int64_t)a.occ_gate[j] * a.B + b];
+  for (int64_t t = lane; t < a.tiles_per_sample; t += 32) acc += src[t];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) a.G[(int64_t)j * a.B + b] = acc * a.gm[(int64_t)a.occ_gate[j] * a.B + b];
 }
 
 // dparams[p] = sum over occurrences (fixed order) of sum_b G[j][b]; dinputs[b][c] likewise per sample.
@@ -456,7 +509,8 @@ cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st) {
 
 cudaError_t launch_grad_gather(const GradReduceArgs& a, cudaStream_t st) {
   if (a.n_occ > 0 && a.B > 0) {
-    grad_gather_kernel<<<(unsigned)(a.n_occ * a.B), a.tiles_per_sample >= 256 ? 256 : 32, 0, st>>>(a);
+    const int64_t warps = (int64_t)a.n_occ * a.B;
+    grad_gather_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
     g_kernel_launches++;
   }
   return cudaGetLastError();
