@@ -253,10 +253,13 @@ static std::vector<int> diag_used_bits(const Schedule& s, const std::vector<int>
 // the product of the run's register-bit RZ factors, per sample, built in shared memory while a tile's
 // loads are in flight. off: first element (in units of T); es: T values per entry (2: (re, im); 4:
 // (re, re, im, im), the packed backward's FP32x2 operands).
+// Runs whose table has more entries than the tile has threads (tiny tiles: a 5-qubit circuit's tile
+// is one thread) form their factors in registers instead, by a butterfly over the used bits (tab false).
 struct DiagRun {
   std::vector<int> ops;
   std::vector<int> used;
   int off = 0, es = 2;
+  bool tab = true;
 };
 
 // The merged runs of a pass in the order the generated code meets them (phase steps, then op order).
@@ -264,6 +267,7 @@ static std::vector<DiagRun> pass_diag_runs(const Schedule& s, const DevPass& d, 
   std::vector<DiagRun> runs;
   const int P = d.n_phases;
   const int es = bwd && s.packed_bwd ? 4 : 2;
+  const int nthr = 1 << (d.k - d.R);
   int off = 0;
   for (int step = 0; step < P; step++) {
     const int ph = bwd ? P - 1 - step : step;
@@ -274,8 +278,9 @@ static std::vector<DiagRun> pass_diag_runs(const Schedule& s, const DevPass& d, 
       r.ops.assign(order.begin() + xy.first, order.begin() + xy.second);
       r.used = diag_used_bits(s, r.ops);
       r.es = es;
-      r.off = off;
-      off += es << r.used.size();
+      r.tab = (1 << r.used.size()) <= nthr;
+      r.off = r.tab ? off : -1;
+      if (r.tab) off += es << r.used.size();
       runs.push_back(r);
     }
   }
@@ -332,6 +337,7 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
   o << "  template <typename T> static __device__ __forceinline__ void build_tables(qj::Ctx<T>& c, const T* src) {\n"
     << "    (void)c; (void)src;\n";
   for (const DiagRun& r : druns) {
+    if (!r.tab) continue;
     const int nu = (int)r.used.size();
     o << "    for (qj::u32 e = c.tid; e < " << (1u << nu) << "u; e += " << NTHR << "u) {\n"
       << "      T dr = T(1), di = T(0);\n";
@@ -650,8 +656,14 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         if (op.kind == K_CZ_RT)
           czrt.push_back({(int)(std::find(used.begin(), used.end(), (int)op.a) - used.begin()), (int)op.b});
       }
+      const bool tab = dr.tab;
+      auto uname = [&](int r, int b, char part) { return "u" + std::to_string(r) + "_" + std::to_string(b) + part; };
       o << "      { // diagonal run of " << run.size() << " ops\n";
-      if (has_t) o << "        T tr = T(1), ti = T(0);\n";
+      if (has_t || !tab) o << "        T tr = T(1), ti = T(0);\n";
+      if (!tab)
+        for (int r : used)
+          o << "        T " << uname(r, 0, 'r') << " = T(1), " << uname(r, 0, 'i') << " = T(0), " << uname(r, 1, 'r')
+            << " = T(1), " << uname(r, 1, 'i') << " = T(0);\n";
       if (bwd) {
         o << "        A wt = A(0);";
         for (size_t k2 = 0; k2 < wused.size(); k2++) o << " A w" << wused[k2] << " = A(0);";
@@ -673,6 +685,9 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
               emit_grad(op, "(A)w" + std::to_string(op.a) + " * (A)rho");
               o << "        rho *= T(1) + " << cf << " * " << cf << ";\n";
             }
+            if (!tab)
+              o << "        { const T cc = " << cf << "; qj::cmul(" << uname(op.a, 0, 'r') << ", " << uname(op.a, 0, 'i')
+                << ", T(1), -cc); qj::cmul(" << uname(op.a, 1, 'r') << ", " << uname(op.a, 1, 'i') << ", T(1), cc); }\n";
             break;
           case K_RZ_T: {
             const std::string sg = "(((tb >> " + std::to_string(op.a) + ") & 1u) ? T(-1) : T(1))";
@@ -686,7 +701,10 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
           case K_CZ_TT:
             o << "        if (((tb >> " << (int)op.a << ") & 1u) && ((tb >> " << (int)op.b << ") & 1u)) { tr = -tr; ti = -ti; }\n";
             break;
-          case K_CZ_RT:
+          case K_CZ_RT:   // with a table: the entry's sign below
+            if (!tab)
+              o << "        if ((tb >> " << (int)op.b << ") & 1u) { " << uname(op.a, 1, 'r') << " = -" << uname(op.a, 1, 'r')
+                << "; " << uname(op.a, 1, 'i') << " = -" << uname(op.a, 1, 'i') << "; }\n";
             break;
           default:   // K_CZ_RR
             czrr.push_back(&op);
@@ -695,6 +713,14 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
       }
       // every amplitude times its D: one table entry per value of the used bits (compressed index)
       const int nu = (int)used.size();
+      if (!tab) {   // D over the used bits by a butterfly from the thread-uniform part
+        o << "        T dr[" << (1 << nu) << "], di[" << (1 << nu) << "];\n        dr[0] = tr; di[0] = ti;\n";
+        for (int k2 = 0; k2 < nu; k2++)
+          o << "        for (int j = 0; j < " << (1 << k2) << "; j++) { dr[j + " << (1 << k2) << "] = dr[j]; di[j + " << (1 << k2)
+            << "] = di[j]; qj::cmul(dr[j + " << (1 << k2) << "], di[j + " << (1 << k2) << "], " << uname(used[k2], 1, 'r') << ", "
+            << uname(used[k2], 1, 'i') << "); qj::cmul(dr[j], di[j], " << uname(used[k2], 0, 'r') << ", " << uname(used[k2], 0, 'i')
+            << "); }\n";
+      }
       for (int idx = 0; idx < (1 << nu); idx++) {
         std::string flip;   // register-thread CZs whose register bit is set in this entry
         for (auto& zc : czrt)
@@ -702,7 +728,11 @@ static std::string gen_spec_body(const Schedule& s, const DevPass& d, bool bwd, 
         const bool plain = !has_t && flip.empty();
         const int e0 = dr.off + dr.es * idx;
         o << "        {";
-        if (pk && plain) {
+        if (!tab) {
+          o << " const T fr = dr[" << idx << "], fi = di[" << idx << "];";
+          if (pk) o << " const float2 fr2 = qj::f2(fr), fi2 = qj::f2(fi), fn2 = qj::f2(-fi);";
+          o << "\n";
+        } else if (pk && plain) {
           o << " const float4 f = *reinterpret_cast<const float4*>(c.tab + " << e0 << ");"
             << " const float2 fr2 = make_float2(f.x, f.y), fi2 = make_float2(f.z, f.w), fn2 = make_float2(-f.z, -f.w);\n";
         } else {
