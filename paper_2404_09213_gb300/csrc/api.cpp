@@ -289,7 +289,7 @@ struct qsim_plan_s {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
       for (auto& pp : s.passes)
-        if ((int64_t)jit_smem_bytes(s, pp.dev, false, 0) > optin || (int64_t)jit_smem_bytes(s, pp.devb, true, 0) > optin)
+        if ((int64_t)single_smem_bytes(s, pp.dev, false) > optin || (int64_t)single_smem_bytes(s, pp.devb, true) > optin)
           return fail(QSIM_ERR_UNSUPPORTED, "tile does not fit in shared memory: lower k");
       std::string err;
       int rc = jit_build(s, jit, err);

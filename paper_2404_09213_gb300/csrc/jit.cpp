@@ -899,6 +899,14 @@ int default_k_for(int dtype) { return dtype == QSIM_C128 ? 11 : 12; }
 int multi_max_k_for(int dtype) { return dtype == QSIM_C128 ? 10 : 11; }
 
 // Shared-memory bytes of one tile group; mirrors FwdGroupSmem / BwdGroupSmem in jit_device.cuh.
+int single_cta(const DevPass& d) { return d.k - d.R < 5 ? 32 : 0; }
+
+size_t single_smem_bytes(const Schedule& s, const DevPass& d, bool bwd) {
+  const int cta = single_cta(d);
+  const size_t groups = cta > 0 ? (size_t)cta >> (d.k - d.R) : 1;
+  return groups * jit_smem_bytes(s, d, bwd, cta);
+}
+
 size_t jit_smem_bytes(const Schedule& s, const DevPass& d, bool bwd, int cta) {
   const int dtype = s.dtype;
   const size_t sc = dtype == QSIM_C128 ? 8 : 4, tile = (2 * sc) << d.k;
@@ -927,9 +935,10 @@ static void jit_units(const Schedule& s, std::vector<std::string>& fnames, std::
       const DevPass& d = dir == 0 ? pp.dev : pp.devb;
       const bool bwd = dir == 1;
       const int K = d.k, R = d.R, NTHR = 1 << (K - R);
-      std::string body = gen_spec_body(s, d, bwd, 0, s.has_prefix && &pp == &s.passes[0]);
+      const int cta = single_cta(d), CTA = cta > 0 ? cta : NTHR;
+      std::string body = gen_spec_body(s, d, bwd, cta, s.has_prefix && &pp == &s.passes[0]);
       // register cap: at least this many CTAs per SM (65536 registers each)
-      const int minb = s.max_regs > 0 ? std::max(1, 65536 / (NTHR * s.max_regs)) : 0;
+      const int minb = s.max_regs > 0 ? std::max(1, 65536 / (CTA * s.max_regs)) : 0;
       std::string key = std::string(T) + "|" + std::to_string(K) + "|" + std::to_string(R) + "|" +
                         std::to_string(minb) + "|" + body;
       std::string name = std::string(bwd ? "qb_" : "qf_") + hex64(fnv1a(key));
@@ -938,11 +947,27 @@ static void jit_units(const Schedule& s, std::vector<std::string>& fnames, std::
         std::string b2 = body;
         for (size_t p; (p = b2.find("S_SELF")) != std::string::npos;) b2.replace(p, 6, "S_" + name);
         u << "struct S_" << name << " {\n" << b2 << "};\n";
-        u << "extern \"C\" __global__ void __launch_bounds__(" << NTHR;
+        u << "extern \"C\" __global__ void __launch_bounds__(" << CTA;
         if (minb > 0) u << ", " << minb;
-        u << ") " << name
-          << "(const qj::Args a) { qj::" << (bwd ? "bwd_pass" : "fwd_pass") << "<" << T << ", " << K << ", " << R
-          << ", " << NTHR << ", S_" << name << ">(a); }\n";
+        u << ") " << name << "(const qj::Args a) {";
+        if (cta == 0) {
+          u << " qj::" << (bwd ? "bwd_pass" : "fwd_pass") << "<" << T << ", " << K << ", " << R << ", " << NTHR << ", S_"
+            << name << ">(a); }\n";
+        } else {   // CTA / NTHR tiles per CTA, each group of NTHR threads on its own tile and shared memory
+          u << "\n  extern __shared__ __align__(16) unsigned char smem[];\n"
+            << "  constexpr int NTHR = " << NTHR << ", G = " << CTA / NTHR << ";\n"
+            << "  const unsigned g = threadIdx.x / NTHR, tid = threadIdx.x % NTHR;\n"
+            << "  const long long t0 = (long long)blockIdx.x * G, ti = t0 + g;\n"
+            << "  const bool valid = ti < a.ntiles;\n";
+          if (!bwd)
+            u << "  constexpr int GB = qj::FwdGroupSmem<" << T << ", " << K << ", S_" << name << "::NOPS, S_" << name
+              << "::NTAB>::BYTES;\n  qj::fwd_tile<" << T << ", " << K << ", " << R << ", NTHR, S_" << name
+              << ">(a, valid ? ti : t0, valid, tid, smem + (size_t)g * GB);\n}\n";
+          else
+            u << "  constexpr int GB = qj::BwdGroupSmem<" << T << ", " << K << ", " << R << ", NTHR, S_" << name << "::NOPS, S_"
+              << name << "::NGS, S_" << name << "::GS, S_" << name << "::NTAB>::BYTES;\n  qj::bwd_tile<" << T << ", " << K << ", "
+              << R << ", NTHR, S_" << name << ">(a, valid ? ti : t0, valid, tid, smem + (size_t)g * GB);\n}\n";
+        }
         units[name] = u.str();
       }
       (bwd ? bnames : fnames).push_back(name);
@@ -1066,8 +1091,9 @@ int jit_build(const Schedule& s, JitPlan& jp, std::string& err) {
       const DevPass& d = dir == 0 ? s.passes[p].dev : s.passes[p].devb;
       cudaKernel_t k = loaded[names[p]];
       ks[p].fn = reinterpret_cast<void*>(k);
-      ks[p].smem = jit_smem_bytes(s, d, dir == 1, 0);
-      ks[p].nthr = 1 << (d.k - d.R);
+      ks[p].smem = single_smem_bytes(s, d, dir == 1);
+      ks[p].nthr = single_cta(d) > 0 ? single_cta(d) : 1 << (d.k - d.R);
+      ks[p].groups = single_cta(d) > 0 ? single_cta(d) >> (d.k - d.R) : 1;
       if (ks[p].smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k),
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks[p].smem);
@@ -1323,8 +1349,11 @@ void jit_free(JitPlan& jp) {
 
 cudaError_t jit_launch(const JitKernel& k, int64_t blocks, const JitArgs& a, cudaStream_t st) {
   if (blocks <= 0 || blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-  void* args[] = {const_cast<JitArgs*>(&a)};
-  cudaError_t e = cudaLaunchKernel(k.fn, dim3((unsigned)blocks), dim3((unsigned)k.nthr), args, k.smem, st);
+  JitArgs la = a;
+  la.ntiles = blocks;   // tiles; a CTA takes k.groups of them
+  const int64_t grid = (blocks + k.groups - 1) / k.groups;
+  void* args[] = {&la};
+  cudaError_t e = cudaLaunchKernel(k.fn, dim3((unsigned)grid), dim3((unsigned)k.nthr), args, k.smem, st);
   if (e == cudaSuccess) g_kernel_launches++;
   return e;
 }

@@ -27,6 +27,7 @@ struct JitArgs {
   double* ppart;
   int64_t tps;
   int64_t gpart_offset;
+  int64_t ntiles;             // tiles of the launch (set by jit_launch)
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch (tiles cover samples b0, b0+1, ...)
   uint8_t L[16];
   uint8_t nonlocal[40];
@@ -35,7 +36,7 @@ struct JitArgs {
   uint8_t Q[16];
   uint8_t QN[40];
 };
-static_assert(sizeof(JitArgs) == 296, "JitArgs must match qj::Args");
+static_assert(sizeof(JitArgs) == 304, "JitArgs must match qj::Args");
 
 // Layouts of a pass into its kernel arguments. The forward reads the pass's input layout and writes
 // its output layout; the backward undoes the pass, so it reads the output layout and writes the input.
@@ -58,6 +59,7 @@ struct JitKernel {
   int nthr = 0;
   int64_t max_blocks = 0;   // resident blocks (persistent queue kernels only)
   int per_sm = 0, regs = 0; // resident blocks per SM and registers per thread (queue kernels only)
+  int groups = 1;           // tiles per CTA (single-circuit kernels of tiles with fewer than 32 threads)
 };
 
 struct JitPlan {
@@ -88,6 +90,10 @@ std::string jit_generate(const Schedule& s, std::vector<std::string>& fwd_names,
 // With a register cap in the plan (s.max_regs) a single-circuit backward sizes its gradient partials so
 // that as many CTAs fit in shared memory as in the registers.
 size_t jit_smem_bytes(const Schedule& s, const DevPass& d, bool bwd, int cta = 0);
+// A single-circuit pass kernel whose tile has fewer than 32 threads runs several tiles per CTA: the
+// CTA's threads (0: one tile per CTA), and the shared memory of such a launch's CTA.
+int single_cta(const DevPass& d);
+size_t single_smem_bytes(const Schedule& s, const DevPass& d, bool bwd);
 // NVRTC-compile (or fetch from the on-disk cache) the plan's kernels; host only, no CUDA calls.
 int jit_compile(const Schedule& s, std::map<std::string, std::string>& cubins, std::vector<std::string>& fwd_names,
                 std::vector<std::string>& bwd_names, std::string& err);

@@ -33,6 +33,7 @@ struct Args {
   double* ppart;         // backward of the first pass: prefix contraction partials [(B * tps) x (2K + 1) x 2]
   i64 tps;               // tiles per sample
   i64 gpart_offset;      // first gradient slot of this pass
+  i64 ntiles;            // tiles of the launch
   int n_nonlocal, n, B, b0;   // b0: first sample of this launch
   u8 L[16];              // tile bit j: physical bit in the layout the pass reads
   u8 nonlocal[40];       // tile-index bit i: physical bit in the layout the pass reads

@@ -252,16 +252,16 @@ __global__ void frame_walk_kernel(CoefArgs a) {
       s_meta[i] = g < 0 ? 0 : (a.gate_type[g] | (a.gate_q0[g] << 8) | ((a.gate_q1[g] + 1) << 16));
     }
     __syncwarp();
-    for (int i0 = 0; i0 < m; i0 += 16) {   // 16 independent loads in flight, then their stores
-      uint8_t v[16];
+    for (int i0 = 0; i0 < m; i0 += 64) {   // 64 independent loads in flight, then their stores
+      uint8_t v[64];
 #pragma unroll
-      for (int u = 0; u < 16; u++) {
+      for (int u = 0; u < 64; u++) {
         const int i = i0 + u;
         const int g = i < m ? s_g[i] : -1;
         v[u] = (g >= 0 && (s_meta[i] & 255) <= QSIM_RZ && b < a.B) ? a.form[(int64_t)g * a.B + b] : 0;
       }
 #pragma unroll
-      for (int u = 0; u < 16; u++)
+      for (int u = 0; u < 64; u++)
         if (i0 + u < m) s_form[i0 + u][lane] = v[u];
     }
     __syncwarp();
@@ -464,8 +464,19 @@ cudaError_t launch_frame_gsign(const double* grad_out, const uint64_t* fx, int n
 }
 
 // ------------------------------------------------------------------ gradients
-// G[j][b] = gm[g_j][b] * sum over the sample's tiles of the slot's partials (a warp per (j, b): strided
-// lane sums, then a butterfly, in a fixed order).
+// G[j][b] = gm[g_j][b] * sum over the sample's tiles of the slot's partials, in a fixed order: a thread
+// per (j, b) when a sample has few tiles, else a warp (strided lane sums, then a butterfly).
+__global__ void grad_gather_small_kernel(GradReduceArgs a) {
+  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= (int64_t)a.n_occ * a.B) return;
+  const int j = (int)(w / a.B), b = (int)(w - (w / a.B) * a.B);
+  if (a.occ_slot[j] < 0) return;
+  const double* src = a.gpart + ((int64_t)a.occ_slot[j] * a.B + b) * a.tiles_per_sample;
+  double acc = 0.0;
+  for (int64_t t = 0; t < a.tiles_per_sample; t++) acc += src[t];
+  a.G[(int64_t)j * a.B + b] = acc * a.gm[(int64_t)a.occ_gate[j] * a.B + b];
+}
+
 __global__ void grad_gather_kernel(GradReduceArgs a) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -509,8 +520,9 @@ cudaError_t launch_grad_reduce(const GradReduceArgs& a, cudaStream_t st) {
 
 cudaError_t launch_grad_gather(const GradReduceArgs& a, cudaStream_t st) {
   if (a.n_occ > 0 && a.B > 0) {
-    const int64_t warps = (int64_t)a.n_occ * a.B;
-    grad_gather_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
+    const int64_t rows = (int64_t)a.n_occ * a.B;
+    if (a.tiles_per_sample < 32) grad_gather_small_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(a);
+    else grad_gather_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(a);
     g_kernel_launches++;
   }
   return cudaGetLastError();

@@ -373,11 +373,12 @@ def test_c3_full_size_against_oracle(q, k):
 
 
 # ---------------------------------------------------------------- many tiles, every sample weighted
-@pytest.mark.parametrize("k,ckpt", [(10, 1), (9, 0)])
+@pytest.mark.parametrize("k,ckpt", [(10, 1), (9, 0), (6, 1)])
 def test_backward_many_tiles_all_samples(q, k, ckpt):
-    """Far more tiles than resident CTAs (4096 and 8192) and every sample weighted, so every tile's
-    gradient partials count: complex64 against the complex128 plan on every sample, and both against
-    the FP64 oracle's adjoint sweep on the first and last sample."""
+    """Far more tiles than resident CTAs (4096, 8192 and 65536) and every sample weighted, so every
+    tile's gradient partials count: complex64 against the complex128 plan on every sample, and both
+    against the FP64 oracle's adjoint sweep on the first and last sample. At k = 6 a tile has 2 threads
+    (4 in complex128), so 16 (8) tiles share a CTA."""
     wl = W.ring_workload("many-tiles", 14, 256, 4, "c64", 7)
     r = run(q, wl, "c64", "fused", k=k, checkpoint_passes=ckpt)
     assert r["plan"].info()["n_passes"] >= 2
