@@ -393,7 +393,7 @@ def run_ours(args, world, rank, local):
                            scalar_bwd=int(args.scalar_bwd), product_prefix=int(not args.no_product_prefix),
                            bwd_reg_bits=args.bwd_reg_bits, fwd_reg_bits=args.fwd_reg_bits,
                            split_diagonal=int(args.split_diagonal), max_regs=args.max_regs)
-        autotune = {"k_candidates": [11, 12, 13], "ms_per_fwd_bwd": ms, "chosen_k": k}
+        autotune = {"k_candidates": [11, 12, 13], "ms_per_fwd_bwd": ms[:3], "chosen_k": k}
     ckpt = args.checkpoint_passes if args.mode == "fused" else 0
     plan = q.Plan(wl.gates, wl.n, dtype="c64", mode=args.mode, k=k, contiguous_bits=args.contiguous_bits,
                   checkpoint_passes=ckpt, pauli_frame=(not args.no_pauli_frame) and args.mode == "fused",
@@ -651,7 +651,7 @@ def run_other(args, world, rank, local):
         c2_flops = B * (1 << wl.n) * 6 * n_rot
         name = f"C2: 12 qubits, batch 1024, c64, RX encoding + 6 x (RY,RZ + CNOT ring), forward only, {args.mode}"
         extra = {"passes": P, "mode": args.mode, "rotations_in_passes": n_rot, "rotations": n_rot_circuit,
-                 "autotune": {"candidates": ["2^5 with the frame", "2^4 with the frame", "2^5 without"], "ms": c2_ms,
+                 "autotune": {"candidates": ["2^5 with the frame", "2^4 with the frame", "2^5 without", "2^4 without"], "ms": c2_ms,
                               **tuned} if args.mode == "fused" else None,
                  "prefix_gates": sum(len(x) for x in desc.get("prefix", [])),
                  "l2": "32 MiB state per step stays in L2 and shared memory (ALU-bound, no flush)"}

@@ -348,11 +348,11 @@ void qsim_landscape_clear_cache(void);
  * does not depend on the values), and writes to opts->k the largest candidate whose time is within
  * 2 % of the fastest. n_qubits <= max_k: opts->k = n_qubits (one pass), and when opts leaves
  * fwd_reg_bits and bwd_reg_bits at 0 the candidates are the amplitudes per thread in the register phases
- * and the Pauli frame: 2^5 and 2^4 (2^4 and 2^3 for complex128) with opts->pauli_frame as given, and the
- * larger with the frame off when it was on (the smaller minus one when it was off); the backward's
- * phases follow the forward's when with_backward != 0. The fastest is written to opts->fwd_reg_bits
- * (/ bwd_reg_bits; left at 0 when the largest count wins) and opts->pauli_frame. h_ms: NULL or 3 floats,
- * mean ms per call of each candidate (-1 when not run). Synchronises `stream`. Errors: those of qsim_plan / qsim_forward /
+ * and the Pauli frame: 2^5 and 2^4 (2^4 and 2^3 for complex128) with the frame and then without it when
+ * opts->pauli_frame is 1, else 2^5, 2^4 and 2^3 without; the backward's phases follow the forward's
+ * when with_backward != 0. The fastest is written to opts->fwd_reg_bits (/ bwd_reg_bits; left at 0
+ * when the largest count wins) and opts->pauli_frame. h_ms: NULL or 4 floats, mean ms per call of each
+ * candidate in that order (-1 when not run; a circuit of several passes has 3 candidates). Synchronises `stream`. Errors: those of qsim_plan / qsim_forward /
  * qsim_backward, QSIM_ERR_OOM for scratch. In the paper the maximum group width is a fixed
  * argument of the greedy splitter (Sec. "Circuit Splitting", typically 3 to 6 qubits); here the
  * width is measured per circuit and batch. */

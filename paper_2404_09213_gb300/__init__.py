@@ -316,13 +316,14 @@ def _opts(dtype, **kw):
 
 def autotune(gates, n_qubits, batch, *, with_backward=True, reps=2, dtype="c64", stream=None, return_opts=False,
              **opts):
-    """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate]).
-    Plans are timed with the Pauli frame on unless ``pauli_frame=0`` is passed (as :class:`Plan`)."""
+    """Fastest fused-pass k for this circuit and batch (``qsim_autotune``) -> (k, [ms per candidate]):
+    four entries, -1 for a candidate not run (the fourth, for a circuit of several passes). Plans are
+    timed with the Pauli frame on unless ``pauli_frame=0`` is passed (as :class:`Plan`)."""
     opts.setdefault("pauli_frame", 1)
     opts.setdefault("product_prefix", 1)
     opts.setdefault("split_diagonal", 0)
     o = _opts(dtype, **opts)
-    ms = (ctypes.c_float * 3)()
+    ms = (ctypes.c_float * 4)()
     arr = gate_structs(gates)
     _lib.check(_lib.lib().qsim_autotune(arr, len(gates), int(n_qubits), int(batch), int(bool(with_backward)),
                                         int(reps), ctypes.byref(o), ms, _stream(stream)))

@@ -101,33 +101,35 @@ int autotune_upto(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, i
   if (opts->mode != QSIM_FUSED) return fail(QSIM_ERR_ARG, "autotune: fused mode only");
   if (opts->dtype != QSIM_C64 && opts->dtype != QSIM_C128) return fail(QSIM_ERR_ARG, "autotune: bad dtype");
   if (h_ms)
-    for (int i = 0; i < 3; i++) h_ms[i] = -1.f;
+    for (int i = 0; i < 4; i++) h_ms[i] = -1.f;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (n_qubits <= kmax) {
     // One pass holds the whole state, so k is n; what remains to choose is the amplitudes per thread of
-    // the register phases and the Pauli frame. Candidates: 2^5 and 2^4 (the frame as requested), and 2^5
-    // with the frame off when it was on (2^3 otherwise). Fewer amplitudes mean shorter unrolled code and
-    // more resident warps, more mean fewer shared-memory exchanges; the frame halves the code but adds
-    // a walk per sample and a fix-up of the returned states, which a single short pass may not repay.
-    // Single-circuit plans only.
+    // the register phases and the Pauli frame. Candidates: 2^5 and 2^4 with the frame and without it
+    // when it was requested, else 2^5, 2^4 and 2^3 without. Fewer amplitudes mean shorter unrolled code
+    // and more resident warps, more mean fewer shared-memory exchanges; the frame halves the code but
+    // adds a walk per sample and a fix-up of the returned states, which a single short pass may not
+    // repay. Single-circuit plans only.
     opts->k = n_qubits;
     if (kmax != qsim::max_k_for(opts->dtype) || opts->fwd_reg_bits != 0 || opts->bwd_reg_bits != 0) return QSIM_OK;
     const int top = qsim::fwd_R_for(16, opts->dtype);
     const bool frame = opts->pauli_frame == 1;
-    const int rb[3] = {top, top - 1, frame ? top : top - 2};
-    float ms[3];
+    const int nc = frame ? 4 : 3;
+    const int rb[4] = {top, top - 1, frame ? top : top - 2, top - 1};
+    const bool off[4] = {!frame, !frame, true, true};
+    float ms[4];
     int best = 0;
-    for (int i = 0; i < 3; i++) {
+    for (int i = 0; i < nc; i++) {
       qsim_plan_opts o = *opts;
       o.fwd_reg_bits = std::min(rb[i], n_qubits);
       if (with_backward) o.bwd_reg_bits = std::min(rb[i], n_qubits);
-      if (i == 2 && frame) o.pauli_frame = 0;
+      if (off[i]) o.pauli_frame = 0;
       const int rc = time_candidate(h_gates, n_gates, n_qubits, batch, with_backward, reps, o, st, ms[i]);
       if (rc) return rc;
       if (h_ms) h_ms[i] = ms[i];
       if (ms[i] < ms[best]) best = i;
     }
-    if (best == 2 && frame) opts->pauli_frame = 0;
+    if (off[best]) opts->pauli_frame = 0;
     if (rb[best] != top) {   // keep the library defaults (0) when the largest register count wins
       opts->fwd_reg_bits = std::min(rb[best], n_qubits);
       if (with_backward) opts->bwd_reg_bits = std::min(rb[best], n_qubits);

@@ -24,6 +24,8 @@ def test_autotune_times_three_candidates(q):
     wl = W.config(3, n=15, batch=4, layers=3)
     k, ms = q.autotune(wl.gates, wl.n, 4, reps=1)
     assert k in (11, 12, 13)
+    assert ms[3] == -1.0   # three tile sizes; the fourth slot is for single-pass circuits
+    ms = ms[:3]
     assert all(m > 0 for m in ms)
     # the largest k within 2 % of the fastest candidate
     assert ms[k - 11] <= 1.02 * min(ms)
@@ -31,17 +33,19 @@ def test_autotune_times_three_candidates(q):
 
 
 def test_autotune_single_pass_when_the_state_fits(q):
-    # one pass holds the whole state: k = n, and the three candidates are the register bits per thread;
-    # the tuned plan gives the default plan's results
+    # one pass holds the whole state: k = n, and the four candidates are 2^5 and 2^4 amplitudes per
+    # thread with the Pauli frame and without it; the fastest wins, and the tuned plan gives the default
+    # plan's results
     wl = W.config(2, batch=8)
     k, ms, tuned = q.autotune(wl.gates, wl.n, 8, reps=1, return_opts=True)
     assert k == wl.n and all(m > 0 for m in ms)
-    assert tuned["fwd_reg_bits"] in (0, 4) and tuned["bwd_reg_bits"] == tuned["fwd_reg_bits"]
-    assert tuned["pauli_frame"] or tuned["fwd_reg_bits"] == 0   # the frame-off candidate is 2^5
+    best = int(np.argmin(ms))
+    assert tuned["fwd_reg_bits"] == (0 if best in (0, 2) else 4) and tuned["bwd_reg_bits"] == tuned["fwd_reg_bits"]
+    assert tuned["pauli_frame"] == (best in (0, 1))
     p, x, g = tensors(wl)
     a = q.Plan(wl.gates, wl.n)
     b = q.Plan(wl.gates, wl.n, **tuned)
-    for fr, frame in ((4, True), (5, False)):   # every candidate, not only the one that won
+    for fr, frame in ((4, True), (5, False), (4, False)):   # every candidate, not only the one that won
         c = q.Plan(wl.gates, wl.n, fwd_reg_bits=fr, bwd_reg_bits=fr, pauli_frame=frame)
         _, zc = c.forward(p, x)
         _, za = a.forward(p, x)
@@ -53,7 +57,7 @@ def test_autotune_single_pass_when_the_state_fits(q):
     np.testing.assert_allclose(zb.cpu().numpy(), a.forward(p, x)[1].cpu().numpy(), atol=1e-5)
     # an explicit register choice is kept: nothing is timed
     k2, ms2 = q.autotune(wl.gates, wl.n, 8, fwd_reg_bits=4)
-    assert k2 == wl.n and ms2 == [-1.0, -1.0, -1.0]
+    assert k2 == wl.n and ms2 == [-1.0, -1.0, -1.0, -1.0]
 
 
 def test_autotuned_plan_matches_default_plan(q):
