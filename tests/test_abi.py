@@ -1,6 +1,7 @@
 """The C ABI library: it loads, exports every function that include/qsim.h declares, and its host-only
 entry points (planning, validation, schedule description, index maps) behave. No GPU needed."""
 import ctypes
+import random
 import os
 import re
 
@@ -97,6 +98,46 @@ def test_specialised_kernels_compile_on_host(q, gates, n, kw):
     p = q.Plan(gates, n, **kw)
     src = p.kernel_source()
     assert src.count('extern "C" __global__') >= 2
+    p.compile_kernels()
+
+
+@pytest.mark.parametrize("gates,n,kw", [
+    # packed backward with CZ runs: factor tables (with thread factors and CZ signs) next to in-register
+    # butterflies for runs wider than a tile's 8 threads, and 4 tiles per 32-thread CTA
+    (W.hea_cz_ansatz(10, 3), 10, {"k": 8}),
+    # complex128 tables (two values per entry) and the product prefix
+    (W.hea_cz_ansatz(9, 2), 9, {"k": 9, "dtype": "c128"}),
+    # 32-thread tiles: every run of the ring ansatz from a table
+    (W.ring_ansatz(12, 3), 12, {"k": 10}),
+])
+def test_diagonal_tables_and_grouped_tiles_compile_on_host(q, gates, n, kw):
+    p = q.Plan(gates, n, **kw)
+    src = p.kernel_source()
+    assert "build_tables" in src
+    p.compile_kernels()
+
+
+def test_diagonal_runs_with_thread_factors_compile_on_host(q):
+    # runs of RZ and CZ on thread and register bits: table entries times a thread-uniform factor and
+    # signed by register-thread CZs, and the in-register butterfly for the widest runs
+    rng = random.Random(0)
+    n = 10
+    gates = [W.gate(W.H, (i,)) for i in range(n)]
+    for _ in range(120):
+        r = rng.random()
+        if r < 0.5:
+            gates.append(W.gate(W.RZ, (rng.randrange(n),), param=rng.randrange(6)))
+        elif r < 0.7:
+            c, t = rng.sample(range(n), 2)
+            gates.append(W.gate(W.CZ, (t,), (c,)))
+        elif r < 0.85:
+            gates.append(W.gate(W.RY, (rng.randrange(n),), param=rng.randrange(6)))
+        else:
+            c, t = rng.sample(range(n), 2)
+            gates.append(W.gate(W.CNOT, (t,), (c,)))
+    p = q.Plan(gates, n, k=9)
+    src = p.kernel_source()
+    assert "qj::cmul(fr, fi, tr, ti)" in src and "fr = -fr" in src and "T dr[" in src
     p.compile_kernels()
 
 
