@@ -360,8 +360,8 @@ int qsim_autotune(const qsim_gate* h_gates, int32_t n_gates, int32_t n_qubits, i
                   int32_t with_backward, int32_t reps, qsim_plan_opts* opts, float* h_ms, void* stream);
 
 /* Per-circuit k for qsim_multi_plan: the qsim_autotune measurement (candidates up to the
- * multi-circuit maximum, max_k - 1) on the first circuit of every distinct qubit count (same batch,
- * opts as the base), the result copied to every circuit of that count.
+ * multi-circuit maximum: 11 qubits complex64, 10 complex128) on the first circuit of every distinct
+ * qubit count (same batch, opts as the base), the result copied to every circuit of that count.
  * h_k: n_circuits int32 (host, written). */
 int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n_gates, const int32_t* h_n_qubits,
                         int32_t n_circuits, int32_t batch, int32_t with_backward, int32_t reps,

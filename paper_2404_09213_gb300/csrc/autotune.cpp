@@ -184,7 +184,7 @@ int qsim_multi_autotune(const qsim_gate* const* h_gate_lists, const int32_t* h_n
   for (auto& kv : rep_of) {
     qsim_plan_opts o = base;
     const int c = kv.second;
-    // multi-circuit plans take tiles of at most max_k - 1 qubits (see multi.cpp)
+    // multi-circuit plans take tiles of at most multi_max_k_for qubits (see multi.cpp)
     const int rc = autotune_upto(h_gate_lists[c], h_n_gates[c], h_n_qubits[c], batch, with_backward, reps, &o,
                                  nullptr, stream, qsim::multi_max_k_for(o.dtype));
     if (rc) return rc;

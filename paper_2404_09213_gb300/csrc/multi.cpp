@@ -24,8 +24,8 @@ namespace {
 thread_local std::string m_err;
 int mfail(int code, const std::string& msg);
 
-// Queue kernel CTAs of 128 threads in both directions; with tiles of at most max_k - 1 qubits
-// (2^(k - R) <= 128 threads per tile) and at most 128 registers per thread (link option) four
+// Queue kernel CTAs of 128 threads in both directions; with tiles of at most 11 qubits (10 for
+// complex128; 2^(k - R) <= 128 threads per tile) and at most 128 registers per thread (link option) four
 // CTAs fit on an SM. Every pass structure of a direction lives in one kernel, so its registers and
 // shared memory are the maxima over them: larger tiles would cost every circuit occupancy.
 constexpr int kCtaF = 128, kCtaB = 128;
