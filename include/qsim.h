@@ -69,8 +69,8 @@ enum { QSIM_FUSED = 0, QSIM_PER_GATE = 1 };
 typedef struct {
   int32_t k;                 /* max qubits local to one fused pass (tile = 2^k amplitudes); 0 = default
                                 (12 complex64, 11 complex128); at most 13 for complex64, 11 for complex128,
-                                and at most 8 more than the
-                                register bits of either direction (256 threads per tile) */
+                                and at most 8 more than the register bits of either direction (256
+                                threads per tile) */
   int32_t dtype;             /* QSIM_C64 or QSIM_C128 */
   int32_t mode;              /* QSIM_FUSED (default) or QSIM_PER_GATE (one kernel per gate: the plain baseline) */
   int32_t contiguous_bits;   /* low index bits local in every pass (runs of 2^c amplitudes); 0 = default (4) */
